@@ -1,0 +1,341 @@
+"""Pins for the CPU oracle, independent of the oracle's own code.
+
+Each check ties the oracle to something other than itself: the worked
+example printed in the paper (Fig. 2 / Fig. 3), the paper's distribution
+example (Fig. 4) and combination counts (Tables 2-7), library routines
+(matrix products, entropy and mutual-information routines of scipy and
+scikit-learn), closed forms, invariants of contingency tables and entropy,
+and a brute-force pure-Python search on tiny inputs.
+"""
+import itertools
+import json
+import math
+import os
+from collections import Counter
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_dataset, random_small
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fig2_fig3_worked_example.json")
+
+
+def _worked_example():
+    with open(GOLDEN) as f:
+        fx = json.load(f)
+
+    def decode(bits):
+        n = len(bits["cases"][0])
+        out = []
+        for cls in ("cases", "controls"):
+            rows = bits[cls]
+            for m in range(n):
+                hot = [g for g in range(len(rows)) if rows[g][m] == "1"]
+                assert len(hot) == 1, "each sample lies in exactly one genotype row"
+                out.append(hot[0])
+        return out
+
+    a = decode(fx["a_bits"])
+    b = decode(fx["b_bits"])
+    G = np.array([a, b], dtype=np.uint8)
+    ph = np.array([1] * 8 + [0] * 8, dtype=np.uint8)
+    return fx, G, ph
+
+
+# ---- worked example (Fig. 2 / Fig. 3) --------------------------------------
+
+def test_worked_example_single_variant_tables():
+    fx, G, ph = _worked_example()
+    t = oracle.tables(G, ph, 1, [[0], [1]])
+    assert t[0].tolist() == fx["a_counts"]
+    assert t[1].tolist() == fx["b_counts"]
+
+
+def test_worked_example_pair_table():
+    fx, G, ph = _worked_example()
+    t = oracle.tables(G, ph, 2, [[0, 1]])
+    assert t[0].tolist() == fx["ab_counts"]
+
+
+def test_worked_example_pair_bits_are_ands_of_parents():
+    # Fig. 2: every row of a x b is the AND of its parent rows, in a-major order.
+    fx, _, _ = _worked_example()
+    for cls in ("cases", "controls"):
+        for i in range(3):
+            for j in range(3):
+                av = int(fx["a_bits"][cls][i], 2)
+                bv = int(fx["b_bits"][cls][j], 2)
+                assert av & bv == int(fx["ab_bits"][cls][3 * i + j], 2)
+
+
+def test_worked_example_mi_b_is_zero():
+    # Cases and controls of variant b have identical genotype counts, so the
+    # genotype carries no information on the phenotype: MI = 0 exactly.
+    fx, G, ph = _worked_example()
+    t = oracle.tables(G, ph, 1, [[1]])
+    assert oracle.mi(t, 1)[0] == pytest.approx(0.0, abs=1e-15)
+
+
+# ---- library routines -------------------------------------------------------
+
+def _mi_by_ratio(table):
+    """MI written as sum p(x,y) ln(p(x,y) / (p(x) p(y))) (equivalent form)."""
+    t = np.asarray(table, dtype=np.float64)
+    N = t.sum()
+    px = t.sum(axis=1) / N
+    py = t.sum(axis=0) / N
+    s = 0.0
+    for x in range(t.shape[0]):
+        for y in range(2):
+            if t[x, y] > 0:
+                pxy = t[x, y] / N
+                s += pxy * math.log(pxy / (px[x] * py[y]))
+    return s
+
+
+def test_mi_matches_sklearn_mutual_info_score():
+    skm = pytest.importorskip("sklearn.metrics")
+    ds = random_small(11, S=6, M=40)
+    combos = list(itertools.combinations(range(6), 3))
+    t = oracle.tables(ds.genotypes, ds.phenotype, 3, combos)
+    got = oracle.mi(t, 3)
+    for i in range(len(combos)):
+        ref = skm.mutual_info_score(None, None, contingency=t[i].astype(np.int64))
+        assert got[i] == pytest.approx(ref, rel=1e-12, abs=1e-14)
+
+
+def test_mi_matches_scipy_conditional_entropy_form():
+    from scipy.stats import entropy
+    ds = random_small(12, S=5, M=37)
+    combos = list(itertools.combinations(range(5), 2))
+    t = oracle.tables(ds.genotypes, ds.phenotype, 2, combos)
+    got = oracle.mi(t, 2)
+    for i in range(len(combos)):
+        tab = t[i].astype(np.float64)
+        N = tab.sum()
+        hy = entropy(tab.sum(axis=0))
+        hy_given_x = sum((row.sum() / N) * entropy(row) for row in tab if row.sum() > 0)
+        assert got[i] == pytest.approx(hy - hy_given_x, rel=1e-12, abs=1e-14)
+        assert got[i] == pytest.approx(_mi_by_ratio(tab), rel=1e-12, abs=1e-14)
+
+
+def test_order2_counts_equal_binary_matrix_products():
+    # Cell (g, h) of class c counts samples of class c with genotype g at SNP i
+    # and h at SNP j: the 0/1 matrix product A_g A_h^T restricted to class c.
+    import torch
+    ds = make_dataset("mm", seed=7, S=24, cases=70, controls=53, k=2, top_n=5)
+    G, ph = ds.genotypes, ds.phenotype
+    combos = list(itertools.combinations(range(ds.S), 2))
+    t = oracle.tables(G, ph, 2, combos)
+    for c, mask in ((0, ph == 1), (1, ph == 0)):
+        onehot = [torch.tensor((G[:, mask] == g).astype(np.float64)) for g in range(3)]
+        for g in range(3):
+            for h in range(3):
+                prod = onehot[g] @ onehot[h].T
+                for n, (i, j) in enumerate(combos):
+                    assert t[n, 3 * g + h, c] == int(prod[i, j].item())
+
+
+# ---- closed forms -----------------------------------------------------------
+
+def test_mi_of_monomorphic_snp_is_zero():
+    G = np.zeros((2, 30), np.uint8)
+    G[1] = 2
+    ph = np.array([1] * 12 + [0] * 18, np.uint8)
+    t = oracle.tables(G, ph, 1, [[0], [1]])
+    assert np.all(oracle.mi(t, 1) == 0.0)
+
+
+def test_mi_of_phenotype_determining_snp_is_class_entropy():
+    M1, M0 = 13, 29
+    ph = np.array([1] * M1 + [0] * M0, np.uint8)
+    G = np.array([[2] * M1 + [0] * M0], np.uint8)
+    q = M1 / (M1 + M0)
+    hy = -q * math.log(q) - (1 - q) * math.log(1 - q)
+    t = oracle.tables(G, ph, 1, [[0]])
+    assert oracle.mi(t, 1)[0] == pytest.approx(hy, rel=1e-14)
+
+
+# ---- invariants -------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_table_invariants(k):
+    ds = random_small(20 + k, S=7, M=33, cases=14)
+    G, ph = ds.genotypes, ds.phenotype
+    combos = list(itertools.combinations(range(7), k))
+    t = oracle.tables(G, ph, k, combos)
+    assert np.all(t[:, :, 0].sum(axis=1) == 14)
+    assert np.all(t[:, :, 1].sum(axis=1) == 33 - 14)
+    if k == 1:
+        for n, (s,) in enumerate(combos):
+            for c, mask in ((0, ph == 1), (1, ph == 0)):
+                hist = np.bincount(G[s, mask], minlength=3)
+                assert t[n, :, c].tolist() == hist.tolist()
+        return
+    # Marginalising SNP t of the combination gives the table of the others.
+    for n, cmb in enumerate(combos):
+        full = t[n].reshape([3] * k + [2])
+        for drop in range(k):
+            rest = [cmb[u] for u in range(k) if u != drop]
+            sub = oracle.tables(G, ph, k - 1, [rest])[0]
+            assert np.array_equal(full.sum(axis=drop).reshape(-1, 2), sub)
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_mi_bounds_and_symmetries(k):
+    ds = random_small(40 + k, S=6, M=31, cases=11)
+    G, ph = ds.genotypes, ds.phenotype
+    combos = list(itertools.combinations(range(6), k))
+    t = oracle.tables(G, ph, k, combos)
+    mi = oracle.mi(t, k)
+    N = 31
+    hy = -(11 / N) * math.log(11 / N) - (20 / N) * math.log(20 / N)
+    assert np.all(mi >= -1e-15)
+    assert np.all(mi <= hy + 1e-15) and hy <= math.log(2)
+    for n in range(len(combos)):
+        nx = t[n].sum(axis=1)
+        hx = -sum((v / N) * math.log(v / N) for v in nx if v > 0)
+        assert mi[n] <= hx + 1e-14
+    # Swapping the case/control labels leaves MI unchanged.
+    t2 = oracle.tables(G, 1 - ph, k, combos)
+    assert np.allclose(oracle.mi(t2, k), mi, rtol=1e-12, atol=1e-15)
+    # Permuting the SNPs of a combination relabels cells only.
+    for n, cmb in enumerate(combos[:5]):
+        rev = list(reversed(cmb))
+        tr = oracle.tables(G, ph, k, [rev])
+        assert oracle.mi(tr, k)[0] == pytest.approx(mi[n], rel=1e-12, abs=1e-15)
+
+
+# ---- brute force ------------------------------------------------------------
+
+def _brute_force(G, ph, k):
+    """Pure-Python tables (Counter over per-sample genotype tuples) and MI."""
+    S, M = G.shape
+    res = []
+    for cmb in itertools.combinations(range(S), k):
+        cnt = Counter()
+        for m in range(M):
+            cnt[(tuple(int(G[s, m]) for s in cmb), int(ph[m]))] += 1
+        table = np.zeros((3 ** k, 2), np.int64)
+        for (gs, y), v in cnt.items():
+            cell = 0
+            for g in gs:
+                cell = cell * 3 + g
+            table[cell, 0 if y == 1 else 1] += v
+        res.append((cmb, table, _mi_by_ratio(table)))
+    return res
+
+
+@pytest.mark.parametrize("seed,S,M,k", [(1, 6, 20, 1), (2, 7, 25, 2), (3, 8, 40, 3),
+                                        (4, 7, 30, 4), (5, 5, 17, 5), (6, 8, 11, 2)])
+def test_search_matches_brute_force(seed, S, M, k):
+    ds = random_small(seed, S=S, M=M)
+    G, ph = ds.genotypes, ds.phenotype
+    brute = _brute_force(G, ph, k)
+    combos = [b[0] for b in brute]
+    t = oracle.tables(G, ph, k, combos)
+    for n, b in enumerate(brute):
+        assert np.array_equal(t[n], b[1])
+    top_n = 7
+    idx, score, tested = oracle.search(G, ph, k, top_n, nthreads=3)
+    assert tested == math.comb(S, k) == len(brute)
+    assert len(idx) == min(top_n, len(brute))
+    ref = {b[0]: b[2] for b in brute}
+    for i in range(len(idx)):
+        assert score[i] == pytest.approx(ref[tuple(int(x) for x in idx[i])], rel=1e-12, abs=1e-14)
+    # Best first; bit-equal scores are ordered by index tuple.  Tables that
+    # are cell permutations of each other have equal MI in exact arithmetic
+    # but may differ in the last bit, so order is only checked up to 1e-12.
+    for i in range(1, len(idx)):
+        assert score[i] <= score[i - 1] + 1e-12
+        if score[i] == score[i - 1]:
+            assert tuple(idx[i - 1]) < tuple(idx[i])
+    # Nothing left out scores above the last kept score.
+    kept = {tuple(int(x) for x in r) for r in idx}
+    cutoff = score[-1]
+    for cmb, _, s in brute:
+        if cmb not in kept:
+            assert s <= cutoff + 1e-12
+
+
+def test_search_top_n_larger_than_combinations_returns_all():
+    ds = random_small(9, S=5, M=20)
+    idx, score, tested = oracle.search(ds.genotypes, ds.phenotype, 3, 100, nthreads=2)
+    assert len(idx) == math.comb(5, 3) == tested
+    assert len({tuple(r) for r in idx.tolist()}) == len(idx)
+
+
+def test_search_k_equals_s():
+    ds = random_small(10, S=4, M=20)
+    idx, score, tested = oracle.search(ds.genotypes, ds.phenotype, 4, 3, nthreads=2)
+    assert idx.tolist() == [[0, 1, 2, 3]] and tested == 1
+
+
+def test_search_is_independent_of_thread_count():
+    ds = make_dataset("thr", seed=3, S=30, cases=50, controls=61, k=3, top_n=20)
+    a = oracle.search(ds.genotypes, ds.phenotype, 3, 20, nthreads=1)
+    b = oracle.search(ds.genotypes, ds.phenotype, 3, 20, nthreads=5)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_validation_rejects_bad_inputs():
+    G = np.zeros((3, 10), np.uint8)
+    ph = np.zeros(10, np.uint8)
+    assert oracle.validate(G, ph, 2) == 0
+    G2 = G.copy(); G2[1, 4] = 3
+    assert oracle.validate(G2, ph, 2) != 0
+    ph2 = ph.copy(); ph2[0] = 2
+    assert oracle.validate(G, ph2, 2) != 0
+    assert oracle.validate(G, ph, 0) != 0
+    assert oracle.validate(G, ph, 4) != 0
+
+
+# ---- distribution (Fig. 4) and combination counts (Tables 2-7) --------------
+
+def test_fig4_static_distribution_example():
+    # n = 8 variants, k = 4, p = 3 units: 25, 26 and 19 combinations.
+    assert oracle.distribution(8, 4, 3).tolist() == [25, 26, 19]
+
+
+@pytest.mark.parametrize("n,k,count", [
+    (464, 4, 1906472876), (152, 5, 632671880), (76, 6, 218618940),      # Table 2
+    (184865, 2, 17087441680), (3246, 3, 5694987980),                    # Table 3
+    (3755572, 2, 7052158645806), (28576, 3, 3888727096800),             # Table 4
+    (2409, 4, 1399760565126), (561, 5, 454852770372), (223, 6, 159602946217),
+    (17010, 3, 820134519120),                                           # Table 5
+])
+def test_combination_counts_of_the_paper_tables(n, k, count):
+    assert oracle.binom(n, k) == count
+
+
+def test_distribution_covers_every_combination():
+    for n, k, p in [(20, 2, 3), (15, 3, 4), (12, 4, 5)]:
+        assert int(oracle.distribution(n, k, p).sum()) == math.comb(n, k)
+
+
+# ---- planted recovery (generator + method sanity) ---------------------------
+
+def test_planted_pair_is_recovered_c1():
+    from synth import make_config
+    ds = make_config("C1")
+    idx, score, tested = oracle.search(ds.genotypes, ds.phenotype, 2, 10)
+    assert tested == math.comb(100, 2)
+    assert tuple(idx[0]) == (17, 63)
+
+
+def test_planted_pair_has_no_marginal_effect_c1():
+    from synth import make_config
+    ds = make_config("C1")
+    t = oracle.tables(ds.genotypes, ds.phenotype, 1, [[17], [63]])
+    mi1 = oracle.mi(t, 1)
+    t2 = oracle.tables(ds.genotypes, ds.phenotype, 2, [[17, 63]])
+    assert oracle.mi(t2, 2)[0] > 10 * mi1.max()
+
+
+def test_planted_triple_is_recovered():
+    ds = make_dataset("p3", seed=21, S=60, cases=1500, controls=1500, k=3, top_n=5,
+                      planted=(4, 30, 55))
+    idx, score, _ = oracle.search(ds.genotypes, ds.phenotype, 3, 5)
+    assert tuple(idx[0]) == (4, 30, 55)

@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Benchmark of the exhaustive epistasis search on GB300.
+
+One step = one full ``fc_search`` (sweep with prefix tables, AND/POPC
+counting, FP32 mutual information and per-warp top lists -> block and grid
+merge -> FP64 rescoring of the candidates -> final ordering -> results to
+the host) over the order-3 workload: 1,000 SNPs x 4,000 samples
+(2,000 cases / 2,000 controls), top 100, synthetic HWE genotypes with a
+planted 3-SNP interaction.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (bounded samples of the same workload on the host cores).
+Multi-GPU (torchrun): every rank searches its own data set (independent
+problems, weak scaling); only the step times are reduced (max over ranks).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("k-SNP combinations/sec and sample-combinations/sec at order 2/3/4; "
+          "% of popc roofline")
+UNIT = "combinations/s"
+POPC_PER_CLK_PER_SM = 16          # 32-bit POPC issue rate per SM per clock
+DEFAULT_SM_MAX_MHZ = 2070.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C4"])
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target duration of the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def init_group(world):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(dist, value):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def workload_title(name):
+    from synth.genotypes import CONFIG_TITLES
+    return CONFIG_TITLES[name]
+
+
+def algorithmic_popc(ds, k):
+    """32-bit POPCs per combination of the paper's method (3^k cells x
+    32-bit words of both classes), times the number of combinations."""
+    words = -(-ds.cases // 32) + -(-ds.controls // 32)
+    return math.comb(ds.S, k) * (3 ** k) * words
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2201_03331_gb300", "csrc", "fc_search.cu")
+    try:
+        rec = json.load(open(path)).get(kernel_key)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256") != sha:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline_sample(ds, k, seconds):
+    """Time the oracle on the first P (k-1)-prefixes of the workload, P
+    chosen so that the sample takes about ``seconds`` on all host cores."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, _, tested = oracle.search(ds.genotypes, ds.phenotype, k, 10, 0, (0, 8))
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_prefix = dt / 8
+    npfx = math.comb(ds.S - 1, k - 1)
+    P = int(max(8, min(npfx, seconds / per_prefix)))
+    t0 = time.perf_counter()
+    _, _, tested = oracle.search(ds.genotypes, ds.phenotype, k, 10, 0, (0, P))
+    dt = time.perf_counter() - t0
+    return {"value": tested / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"(k-1)-prefixes [0, {P}) of {npfx} = {tested} combinations, {dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import make_config
+    oracle.build()
+    ds = make_config(args.workload)
+    k = ds.k
+    cores = os.cpu_count() or 1
+    # Size one step at ~ (a few minutes / steps) of CPU time.
+    t0 = time.perf_counter()
+    oracle.search(ds.genotypes, ds.phenotype, k, ds.top_n, 0, (0, 8))
+    per_prefix = max(time.perf_counter() - t0, 1e-3) / 8
+    npfx = math.comb(ds.S - 1, k - 1)
+    budget = min(8.0, 150.0 / max(1, args.steps + args.warmup))
+    P = int(max(8, min(npfx, budget / per_prefix)))
+    times, tested = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, tested = oracle.search(ds.genotypes, ds.phenotype, k, ds.top_n, 0, (0, P))
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = tested / (ms / 1e3)
+    sample = f"(k-1)-prefixes [0, {P}) of {npfx} = {tested} combinations per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_title(args.workload), "k": k, "snps": ds.S, "samples": ds.M,
+                   "top_n": ds.top_n, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    dist = init_group(world)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    import paper_2201_03331_gb300 as fc
+    from paper_2201_03331_gb300 import build as fcbuild
+    from synth import make_config, make_dataset
+    from synth.genotypes import CONFIGS
+
+    fcbuild.build()
+    cfg = dict(CONFIGS[args.workload])
+    S = cfg.pop("S")
+    if world > 1:
+        cfg["seed"] = cfg["seed"] + 1000 * rank      # independent data set per rank
+    ds = make_dataset(args.workload, S=S, **cfg) if world > 1 else make_config(args.workload)
+    k, top_n = ds.k, ds.top_n
+    total = math.comb(ds.S, k)
+
+    stream = torch.cuda.Stream()
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    fc.fc_set_stream(h, stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(max(3, args.warmup)):
+        fc.fc_search(h, k, top_n)
+    torch.cuda.synchronize()
+
+    fc.fc_timing(h, 1)
+    clocks = ClockSampler(local)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                       # L2 flush between timed steps
+        ev[i][0].record(stream)
+        idx, score = fc.fc_search(h, k, top_n)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    sweep_ms, sweeps, launches = fc.fc_timing(h, 0)
+    total_ms = max_over_ranks(dist, sum(step_ms))
+    ms_per_step = total_ms / args.steps
+    value = world * total * args.steps / (total_ms / 1e3)
+
+    # End to end through the public API: pinned host inputs -> fc_load ->
+    # fc_search -> host results, every step.
+    Gp = torch.from_numpy(ds.genotypes).pin_memory()
+    Pp = torch.from_numpy(ds.phenotype).pin_memory()
+    Gn, Pn = Gp.numpy(), Pp.numpy()
+    e2e_times = []
+    for i in range(1 + args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2 = fc.fc_load(Gn, Pn)
+        idx2, score2 = fc.fc_search(h2, k, top_n)
+        fc.fc_free(h2)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(dist, sum(e2e_times) / len(e2e_times))
+    e2e = {"value": world * total / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(ds.genotypes.nbytes + ds.phenotype.nbytes),
+           "d2h_bytes_per_step": int(idx2.nbytes + score2.nbytes + 8 + 4),
+           "ms_per_step": 1e3 * e2e_s}
+
+    props = torch.cuda.get_device_properties(local)
+    sm_max = DEFAULT_SM_MAX_MHZ
+    try:
+        sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", sm_max))
+    except (OSError, ValueError):
+        pass
+    peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    popc = algorithmic_popc(ds, k)
+    sweep_avg_s = (sweep_ms / max(sweeps, 1)) / 1e3
+    achieved = popc / sweep_avg_s / 1e12 if sweeps else None
+    kernel_key = f"k_search<{k},1,TOPN> {args.workload}"
+    roofline = {"bound": "alu", "kernel": kernel_key, "achieved": achieved, "peak": peak,
+                "unit": "Tpopc32/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": traffic_for(kernel_key),
+                "peak_basis": f"{props.multi_processor_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz",
+                "sweep_ms_per_launch": 1e3 * sweep_avg_s,
+                "algorithmic_popc_per_launch": popc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_title(args.workload), "k": k, "snps": ds.S, "samples": ds.M,
+                   "cases": ds.cases, "controls": ds.controls, "top_n": top_n,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "one independent data set per GPU" if world > 1 else "single GPU"},
+        "sample_combinations_per_s": value * ds.M,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "top1": [int(x) for x in idx[0]],
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(ds, k, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fc.fc_free(h)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

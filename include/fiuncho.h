@@ -1,0 +1,165 @@
+/*
+ * fiuncho.h - C ABI of the GB300 exhaustive epistasis search.
+ *
+ * The library tests every k-combination of SNPs for association with a
+ * binary phenotype, as the exhaustive search of Fiuncho does
+ * (Ponte-Fernandez, Gonzalez-Dominguez, Martin, "Fiuncho: a program for
+ * any-order epistasis detection in CPU clusters"): for each combination it
+ * builds the 3^k x {cases, controls} contingency table from per-genotype
+ * bit vectors (Section "Constructing the genotype tables", Section
+ * "Computing the contingency tables", Figs. 2-3), scores it with mutual
+ * information (Section "Mutual Information test") and keeps the best
+ * combinations (Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *   - Return value: FC_OK (0) on success, a negative FC_E* code otherwise.
+ *     No C++ exception or abort crosses this boundary.  fc_last_error()
+ *     gives a one-line description of the last failure on the calling
+ *     thread.
+ *   - Input buffers are only read during the call; the caller keeps
+ *     ownership.  Output buffers are caller-allocated host memory unless an
+ *     entry point says otherwise.
+ *   - Genotypes are uint8 values 0, 1, 2 (minor-allele count: rows a_1,
+ *     a_2, a_3 of a genotype table); phenotype 1 = case, 0 = control.
+ *     Any other value fails with FC_EINVAL.
+ *   - Combinations are strictly increasing SNP index tuples; rank 0 of a
+ *     result is the highest mutual information.  Equal scores are ordered
+ *     by the lexicographic order of the index tuple (smaller first).
+ *   - Mutual information is in nats (natural logarithm), plug-in
+ *     probabilities n/N over all samples, rescored in FP64 before it is
+ *     returned.
+ *   - Work runs on the handle's CUDA stream (fc_set_stream); every entry
+ *     point returns after its results are in the caller's buffers.
+ */
+#ifndef FIUNCHO_H
+#define FIUNCHO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FC_OK 0
+#define FC_EINVAL (-1)   /* bad argument or input value */
+#define FC_ERANGE (-2)   /* size outside the supported limits below */
+#define FC_ENOMEM (-3)   /* device or host allocation failed */
+#define FC_ECUDA (-4)    /* CUDA runtime or launch error */
+#define FC_ETIMEOUT (-5) /* a bounded device wait ran out */
+#define FC_ENODEV (-6)   /* no usable CUDA device */
+
+/* Orders accepted by fc_search / fc_scores / fc_search_batch. */
+#define FC_KMAX_SEARCH 4
+/* Orders accepted by fc_tables. */
+#define FC_KMAX_TABLES 6
+/* Per-class sample limit: cases and controls each at most 65535. */
+#define FC_MAX_CLASS_SAMPLES 65535
+/* Largest top_n + error window the candidate list can hold. */
+#define FC_MAX_LIST 4096
+
+typedef struct fc_handle fc_handle;
+
+/*
+ * fc_load - pack one data set into device memory.
+ *
+ * genotypes : host uint8 [S][M], SNP-major (row s = SNP s, column m =
+ *             sample m), values 0/1/2.
+ * S, M      : SNP and sample counts, 1 <= S < 2^31, 1 <= M < 2^31.
+ * phenotype : host uint8 [M], 1 = case, 0 = control.
+ * out       : receives a new handle that owns the packed device copy; free
+ *             it with fc_free.  *out is NULL on failure.
+ *
+ * The genotypes are packed into one bit per sample per genotype row, cases
+ * and controls in separate word ranges (the genotype tables of Fig. 2).
+ * Fails with FC_EINVAL on a null pointer, a size <= 0 or a value outside the
+ * coding above; FC_ERANGE if cases or controls exceed FC_MAX_CLASS_SAMPLES;
+ * FC_ENODEV without a CUDA device.
+ */
+int fc_load(const uint8_t *genotypes, int64_t S, int64_t M, const uint8_t *phenotype,
+            fc_handle **out);
+
+/* fc_load_device - as fc_load, but genotypes and phenotype are device
+ * pointers (same layout) on the current device. */
+int fc_load_device(const uint8_t *d_genotypes, int64_t S, int64_t M,
+                   const uint8_t *d_phenotype, fc_handle **out);
+
+/*
+ * fc_set_stream - run the handle's work on cuda_stream (a cudaStream_t;
+ * NULL = the library's own non-blocking stream).  The stream must belong to
+ * the handle's device and outlive its use.
+ */
+int fc_set_stream(fc_handle *h, void *cuda_stream);
+
+/*
+ * fc_search - exhaustive search of order k (Algorithm 1 over all
+ * C(S, k) combinations).
+ *
+ * k         : 1 <= k <= min(FC_KMAX_SEARCH, S); C(S, k) must be < 2^60.
+ * top_n     : number of combinations to return, 0 <= top_n <= FC_MAX_LIST/2.
+ * out_idx   : host uint32 [top_n][k], SNP indices of each result, ascending.
+ * out_score : host double [top_n], FP64 mutual information in nats.
+ * out_count : receives min(top_n, C(S, k)); entries beyond it are untouched.
+ *
+ * Results are ordered by (score descending, index tuple ascending).  The
+ * tables are exact; scores are computed in FP32 during the sweep and the
+ * candidates within the FP32 error bound of the cut are rescored in FP64.
+ */
+int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
+              int64_t *out_count);
+
+/*
+ * fc_tables - exact contingency tables of n given combinations (Fig. 3).
+ *
+ * combos : host uint32 [n][k], SNP indices < S in any order; the first
+ *          index is the most significant digit of the cell number.
+ * out    : host uint32 [n][3^k][2]; out[i][cell][0] = cases,
+ *          out[i][cell][1] = controls, cell = sum_t g_t * 3^(k-1-t).
+ * k      : 1 <= k <= FC_KMAX_TABLES.
+ */
+int fc_tables(fc_handle *h, int k, const uint32_t *combos, int64_t n, uint32_t *out);
+
+/*
+ * fc_scores - FP32 scores the search kernel computes for the combinations of
+ * lexicographic ranks [rank_begin, rank_begin + n) (rank 0 = (0, 1, .., k-1)).
+ * out : host float [n].  A parity hook for the sweep's own arithmetic.
+ */
+int fc_scores(fc_handle *h, int k, uint64_t rank_begin, int64_t n, float *out);
+
+/*
+ * fc_timing - instrumentation of a handle's searches.
+ * Reads the counters accumulated since the last reset into the non-NULL
+ * outputs: sweep_ms = total device time of the sweep kernel (CUDA events
+ * recorded on the handle's stream around each launch), sweeps = its number
+ * of launches, launches = every kernel launch of the library on this
+ * handle.  Then, if enable >= 0, resets the counters and switches the
+ * instrumentation on (1) or off (0); enable < 0 only reads.
+ */
+int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64_t *launches);
+
+/* fc_info - sizes of a loaded data set (any pointer may be NULL). */
+int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls);
+
+/* fc_free - release a handle and its device memory (NULL is a no-op). */
+void fc_free(fc_handle *h);
+
+/* fc_strerror - static description of a status code. */
+const char *fc_strerror(int status);
+
+/* fc_last_error - description of the last failure on this thread. */
+const char *fc_last_error(void);
+
+/*
+ * Host helpers of the combination space (no device needed).
+ * fc_num_combinations: C(S, k), or -1 if it is >= 2^62 or the arguments are
+ * invalid.  fc_unrank / fc_rank: lexicographic rank <-> ascending tuple
+ * (out / combo hold k indices).
+ */
+int64_t fc_num_combinations(int64_t S, int k);
+int fc_unrank(int64_t S, int k, uint64_t rank, uint32_t *out);
+int fc_rank(int64_t S, int k, const uint32_t *combo, uint64_t *rank);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIUNCHO_H */

@@ -1,0 +1,211 @@
+"""ctypes binding of ``libfiuncho.so``: one Python function per C entry
+point, same names, argument marshalling only.  All computation happens in
+the library's CUDA kernels; if the shared object is missing the import of
+any entry point raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfiuncho.so")
+
+FC_OK = 0
+FC_EINVAL = -1
+FC_ERANGE = -2
+FC_ENOMEM = -3
+FC_ECUDA = -4
+FC_ETIMEOUT = -5
+FC_ENODEV = -6
+FC_KMAX_SEARCH = 4
+FC_KMAX_TABLES = 6
+FC_MAX_LIST = 4096
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.c_void_p
+i64 = ctypes.c_int64
+u64 = ctypes.c_uint64
+i32 = ctypes.c_int
+
+_SIGNATURES = {
+    "fc_load": ([P, i64, i64, P, P], i32),
+    "fc_load_device": ([P, i64, i64, P, P], i32),
+    "fc_set_stream": ([P, P], i32),
+    "fc_search": ([P, i32, i64, P, P, P], i32),
+    "fc_tables": ([P, i32, P, i64, P], i32),
+    "fc_scores": ([P, i32, u64, i64, P], i32),
+    "fc_info": ([P, P, P, P, P], i32),
+    "fc_timing": ([P, i32, P, P, P], i32),
+    "fc_free": ([P], None),
+    "fc_strerror": ([i32], ctypes.c_char_p),
+    "fc_last_error": ([], ctypes.c_char_p),
+    "fc_num_combinations": ([i64, i32], i64),
+    "fc_unrank": ([i64, i32, u64, P], i32),
+    "fc_rank": ([i64, i32, P, P], i32),
+}
+
+
+class FiunchoError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = library()
+        msg = lib.fc_strerror(status).decode()
+        detail = lib.fc_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status}): {detail}")
+        self.status = status
+
+
+def library():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: run paper_2201_03331_gb300.build.build()")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGNATURES.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != FC_OK:
+        raise FiunchoError(status, where)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(P)
+
+
+class Handle:
+    """Owns an ``fc_handle *``; freed by :func:`fc_free` or garbage collection."""
+
+    def __init__(self, ptr: int):
+        self._ptr = ptr
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise ValueError("handle already freed")
+        return self._ptr
+
+    def __del__(self):
+        try:
+            fc_free(self)
+        except Exception:
+            pass
+
+
+def fc_load(genotypes: np.ndarray, phenotype: np.ndarray) -> Handle:
+    """Pack host ``uint8[S][M]`` genotypes and ``uint8[M]`` phenotype."""
+    G = np.ascontiguousarray(genotypes, dtype=np.uint8)
+    ph = np.ascontiguousarray(phenotype, dtype=np.uint8)
+    if G.ndim != 2 or ph.ndim != 1 or ph.shape[0] != G.shape[1]:
+        raise ValueError("genotypes must be [S][M] and phenotype [M]")
+    out = ctypes.c_void_p()
+    _check(library().fc_load(_ptr(G), G.shape[0], G.shape[1], _ptr(ph), ctypes.byref(out)), "fc_load")
+    return Handle(out.value)
+
+
+def fc_load_device(genotypes, phenotype) -> Handle:
+    """Pack device (torch CUDA ``uint8``) genotypes ``[S][M]`` and phenotype ``[M]``."""
+    import torch
+    if not (genotypes.is_cuda and phenotype.is_cuda):
+        raise ValueError("fc_load_device takes CUDA tensors")
+    G = genotypes.contiguous()
+    ph = phenotype.contiguous()
+    if G.dtype != torch.uint8 or ph.dtype != torch.uint8:
+        raise ValueError("uint8 tensors expected")
+    out = ctypes.c_void_p()
+    _check(library().fc_load_device(G.data_ptr(), G.shape[0], G.shape[1], ph.data_ptr(),
+                                    ctypes.byref(out)), "fc_load_device")
+    return Handle(out.value)
+
+
+def fc_set_stream(h: Handle, stream) -> None:
+    """``stream``: a ``torch.cuda.Stream``, a raw ``cudaStream_t`` int, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(library().fc_set_stream(h.ptr, ctypes.c_void_p(raw or 0)), "fc_set_stream")
+
+
+def fc_search(h: Handle, k: int, top_n: int):
+    """Returns ``(idx uint32[c][k], score float64[c])``, best first."""
+    idx = np.zeros((max(top_n, 1), k), dtype=np.uint32)
+    score = np.zeros(max(top_n, 1), dtype=np.float64)
+    cnt = ctypes.c_int64(0)
+    _check(library().fc_search(h.ptr, k, top_n, _ptr(idx), _ptr(score), ctypes.byref(cnt)), "fc_search")
+    n = cnt.value
+    return idx[:n], score[:n]
+
+
+def fc_tables(h: Handle, k: int, combos) -> np.ndarray:
+    """Exact ``uint32[n][3^k][2]`` tables of the given combinations."""
+    c = np.ascontiguousarray(np.asarray(combos, dtype=np.uint32).reshape(-1, k))
+    out = np.zeros((c.shape[0], 3 ** k, 2), dtype=np.uint32)
+    _check(library().fc_tables(h.ptr, k, _ptr(c), c.shape[0], _ptr(out)), "fc_tables")
+    return out
+
+
+def fc_scores(h: Handle, k: int, rank_begin: int, n: int) -> np.ndarray:
+    """FP32 sweep scores of ranks ``[rank_begin, rank_begin + n)``."""
+    out = np.zeros(n, dtype=np.float32)
+    _check(library().fc_scores(h.ptr, k, rank_begin, n, _ptr(out)), "fc_scores")
+    return out
+
+
+def fc_info(h: Handle):
+    v = [ctypes.c_int64(0) for _ in range(4)]
+    _check(library().fc_info(h.ptr, *[ctypes.byref(x) for x in v]), "fc_info")
+    return tuple(x.value for x in v)
+
+
+def fc_timing(h: Handle, enable: int = -1):
+    """Returns ``(sweep_ms, sweeps, launches)`` accumulated so far, then resets
+    and switches instrumentation on (1) / off (0); ``enable=-1`` only reads."""
+    ms = ctypes.c_double(0)
+    sw = ctypes.c_int64(0)
+    la = ctypes.c_int64(0)
+    _check(library().fc_timing(h.ptr, enable, ctypes.byref(ms), ctypes.byref(sw), ctypes.byref(la)),
+           "fc_timing")
+    return ms.value, sw.value, la.value
+
+
+def fc_free(h: Handle) -> None:
+    if h._ptr:
+        library().fc_free(h._ptr)
+        h._ptr = None
+
+
+def fc_strerror(status: int) -> str:
+    return library().fc_strerror(status).decode()
+
+
+def fc_last_error() -> str:
+    return library().fc_last_error().decode()
+
+
+def fc_num_combinations(S: int, k: int) -> int:
+    return int(library().fc_num_combinations(S, k))
+
+
+def fc_unrank(S: int, k: int, rank: int) -> np.ndarray:
+    out = np.zeros(k, dtype=np.uint32)
+    _check(library().fc_unrank(S, k, rank, _ptr(out)), "fc_unrank")
+    return out
+
+
+def fc_rank(S: int, k: int, combo) -> int:
+    c = np.ascontiguousarray(np.asarray(combo, dtype=np.uint32))
+    r = ctypes.c_uint64(0)
+    _check(library().fc_rank(S, k, _ptr(c), ctypes.byref(r)), "fc_rank")
+    return int(r.value)

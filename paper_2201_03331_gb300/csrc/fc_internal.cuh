@@ -1,0 +1,169 @@
+// Internal declarations shared by the library's translation units.
+//
+// Genotype layout in HBM (the "bit table", a GPU form of the genotype
+// tables of the paper's Section "Constructing the genotype tables"):
+//   X[(w * 3 + g) * S_pad + s]   (uint4 = 128 samples)
+// w  : 128-bit word index; words [0, W0) hold the cases, [W0, Wt) the
+//      controls (W0 = ceil(M1/128), Wt = W0 + ceil(M0/128));
+// g  : genotype row 0/1/2 (rows a_1, a_2, a_3 of a genotype table);
+// s  : SNP, innermost, so the 32 lanes of a warp that work on 32 consecutive
+//      extension SNPs read 512 contiguous bytes.
+// Bit b of word w is sample 128*w' + b of its class in input order (w' the
+// word index within the class).  Padding bits are 0 in all three rows, so
+// ANDs over padding contribute nothing.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fc {
+
+constexpr int KMAX_SEARCH = 4;   // orders of the fused search kernels
+constexpr int KMAX_TABLES = 6;   // orders of the exact-table kernel
+
+__host__ __device__ constexpr int pow3(int k) { return k <= 0 ? 1 : 3 * pow3(k - 1); }
+
+// C(n, r) for the sizes the library accepts (C(S, k) < 2^60, r <= 6): each
+// intermediate is i * C(n - r + i, i) <= r * C(n, r) < 2^63.
+__host__ __device__ inline uint64_t binom(int64_t n, int r)
+{
+    if (r < 0 || n < r) return 0;
+    uint64_t c = 1;
+    for (int i = 1; i <= r; ++i) c = c * (uint64_t)(n - r + i) / (uint64_t)i;
+    return c;
+}
+
+// Lexicographic unranking of k-subsets of {0..S-1}: rank 0 is (0,1,..,k-1).
+// Combinations with first element v: C(S-1-v, k-1).  The count of those
+// with c_t in [lo, v) is C(S-lo, m+1) - C(S-v, m+1), m = k-1-t, which lets
+// each position be found by binary search.
+__host__ __device__ inline void unrank(int64_t S, int k, uint64_t rank, uint32_t *out)
+{
+    int64_t lo = 0;
+    for (int t = 0; t < k; ++t) {
+        const int m = k - 1 - t;
+        const uint64_t base = binom(S - lo, m + 1);
+        // largest v in [lo, S-1-m] with base - C(S - v, m + 1) <= rank
+        int64_t a = lo, b = S - 1 - m;
+        while (a < b) {
+            int64_t mid = a + (b - a + 1) / 2;
+            if (base - binom(S - mid, m + 1) <= rank) a = mid; else b = mid - 1;
+        }
+        rank -= base - binom(S - a, m + 1);
+        out[t] = (uint32_t)a;
+        lo = a + 1;
+    }
+}
+
+__host__ __device__ inline uint64_t rank_of(int64_t S, int k, const uint32_t *c)
+{
+    uint64_t r = 0;
+    int64_t lo = 0;
+    for (int t = 0; t < k; ++t) {
+        const int m = k - 1 - t;
+        r += binom(S - lo, m + 1) - binom(S - (int64_t)c[t], m + 1);
+        lo = (int64_t)c[t] + 1;
+    }
+    return r;
+}
+
+// Ranking key: larger score first; equal scores by smaller rank (rank order
+// is lexicographic order of the index tuple).
+__host__ __device__ inline bool better(float s1, uint64_t r1, float s2, uint64_t r2)
+{
+    return s1 > s2 || (s1 == s2 && r1 < r2);
+}
+__host__ __device__ inline bool better64(double s1, uint64_t r1, double s2, uint64_t r2)
+{
+    return s1 > s2 || (s1 == s2 && r1 < r2);
+}
+
+constexpr uint64_t NO_RANK = ~0ull;
+
+// Device-side error word bits.
+enum : uint32_t {
+    ERR_GENOTYPE = 1u,     // genotype value outside {0,1,2}
+    ERR_PHENOTYPE = 2u,    // phenotype value outside {0,1}
+    ERR_LIST_SHORT = 4u,   // candidate list too short for the FP32 error window
+    ERR_TIMEOUT = 8u,      // bounded device wait ran out
+};
+
+// ---- kernel launch wrappers (defined in the .cu files) --------------------
+
+struct PackArgs {
+    const uint8_t *G;       // [S][M] device
+    const uint8_t *ph;      // [M] device
+    int64_t S, M, S_pad;
+    int W0, Wt;
+    uint4 *X;               // [Wt][3][S_pad]
+    int32_t *case_idx;      // [M1] sample index of the i-th case
+    int32_t *ctrl_idx;      // [M0]
+    uint32_t *err;          // error word
+    int64_t *class_count;   // [2] cases, controls
+};
+cudaError_t launch_class_index(const PackArgs &a, cudaStream_t st);
+cudaError_t launch_pack(const PackArgs &a, int64_t M1, int64_t M0, cudaStream_t st);
+cudaError_t launch_logtab(float *logtab, int64_t M, cudaStream_t st);
+
+struct SearchArgs {
+    const uint4 *X;
+    int64_t S, S_pad;
+    int W0, Wt;
+    const float *logtab;    // ln(n) for n = 0..M (ln 0 := 0)
+    int M;                  // samples (size of logtab - 1)
+    float hy, invN;         // H(Y) and 1/N in FP32
+    uint64_t rank_begin, rank_end;
+    int L;                  // list capacity
+    float *list_score;      // [grid][L]
+    uint64_t *list_rank;    // [grid][L]
+    float *dump_score;      // MODE_SCORES: [rank_end - rank_begin]
+};
+
+struct TuneConfig {
+    int G;          // lanes per combination
+    int NW;         // warps per CTA
+    int WT;         // 128-bit words per prefix-table tile
+    int grid;       // CTAs
+};
+
+enum SearchMode { MODE_TOPN = 0, MODE_SCORES = 1 };
+
+cudaError_t launch_search(int k, const TuneConfig &cfg, int mode, const SearchArgs &a,
+                          cudaStream_t st, size_t *smem_out);
+int search_max_blocks_per_sm(int k, const TuneConfig &cfg, int mode, int L, int M, size_t *smem);
+
+cudaError_t launch_merge(const float *in_s, const uint64_t *in_r, int nlists, int L,
+                         float *out_s, uint64_t *out_r, int *nout, cudaStream_t st);
+
+struct RescoreArgs {
+    const uint4 *X;
+    int64_t S, S_pad;
+    int W0, Wt;
+    int k;
+    int N;                  // requested top_n (<= L)
+    int L;
+    const float *cand_s;    // [L] sorted best first (FP32)
+    const uint64_t *cand_r; // [L]
+    float eps;              // FP32 score error bound
+    uint64_t total;         // C(S, k)
+    double *res_s;          // [L] FP64 scores (-inf where skipped)
+    uint64_t *res_r;        // [L]
+    uint32_t *res_tab;      // [L][3^k][2] exact tables (optional)
+    uint32_t *err;
+};
+cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st);
+cudaError_t launch_final_sort(double *res_s, uint64_t *res_r, int L, int N, int k, int64_t S,
+                              uint32_t *out_idx, double *out_score, cudaStream_t st);
+
+struct TablesArgs {
+    const uint4 *X;
+    int64_t S, S_pad;
+    int W0, Wt;
+    int k;
+    const uint32_t *combos; // [n][k] device
+    int64_t n;
+    uint32_t *out;          // [n][3^k][2] device
+};
+cudaError_t launch_tables(const TablesArgs &a, cudaStream_t st);
+
+}  // namespace fc

@@ -1,0 +1,675 @@
+// Host runtime behind the C ABI: handle, device memory, launch sequence of
+// the search (sweep -> block/grid merge -> FP64 rescoring -> final order),
+// configuration choice and error reporting.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fc_internal.cuh"
+#include "fc_runtime.h"
+
+using namespace fc;
+
+// ---- error reporting ------------------------------------------------------
+
+namespace {
+thread_local char g_last_error[512] = "";
+}
+
+namespace fc {
+
+int set_error(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+int cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return FC_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return set_error(FC_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(FC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ---- fault injection (host side only) --------------------------------------
+// FC_FAULT_ALLOC=n makes the n-th device allocation of the process report
+// cudaErrorMemoryAllocation without calling CUDA; FC_FAULT_LAUNCH=n makes the
+// n-th kernel launch sequence report cudaErrorLaunchFailure before launching.
+
+namespace {
+std::atomic<long> g_alloc_count{0}, g_launch_count{0};
+long env_long(const char *name)
+{
+    const char *v = getenv(name);
+    return v ? atol(v) : 0;
+}
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    const long n = ++g_alloc_count;
+    const long f = env_long("FC_FAULT_ALLOC");
+    if (f > 0 && n == f) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t launch_gate()
+{
+    const long n = ++g_launch_count;
+    const long f = env_long("FC_FAULT_LAUNCH");
+    if (f > 0 && n == f) return cudaErrorLaunchFailure;
+    return cudaSuccess;
+}
+
+void fault_counters_reset()
+{
+    g_alloc_count = 0;
+    g_launch_count = 0;
+}
+
+// ---- device selection ------------------------------------------------------
+
+int check_device(int *dev, int *sms)
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n <= 0)
+        return set_error(FC_ENODEV, "no CUDA device (%s)", cudaGetErrorString(e));
+    int d = 0;
+    if ((e = cudaGetDevice(&d)) != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    cudaDeviceProp p;
+    if ((e = cudaGetDeviceProperties(&p, d)) != cudaSuccess) return cuda_status(e, "cudaGetDeviceProperties");
+    if (p.major != 10 || p.minor != 3)
+        return set_error(FC_ENODEV, "device %d is sm_%d%d; this library is built for sm_103a only",
+                         d, p.major, p.minor);
+    *dev = d;
+    *sms = p.multiProcessorCount;
+    return FC_OK;
+}
+
+DeviceGuard::DeviceGuard(int dev)
+{
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+}
+DeviceGuard::~DeviceGuard()
+{
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != prev) cudaSetDevice(prev);
+}
+
+// ---- scratch arena ---------------------------------------------------------
+
+int Dataset::reserve_scratch(size_t bytes)
+{
+    if (bytes <= scratch_cap) return FC_OK;
+    if (scratch) {
+        cudaStreamSynchronize(stream);
+        cudaFree(scratch);
+        scratch = nullptr;
+        scratch_cap = 0;
+    }
+    size_t cap = std::max(bytes, (size_t)1 << 20);
+    cudaError_t e = dev_alloc(&scratch, cap);
+    if (e != cudaSuccess) return cuda_status(e, "scratch allocation");
+    scratch_cap = cap;
+    return FC_OK;
+}
+
+void *Arena::take(size_t bytes)
+{
+    off = (off + 255) & ~(size_t)255;
+    void *p = base ? static_cast<char *>(base) + off : nullptr;
+    off += bytes;
+    return p;
+}
+
+// ---- loading ---------------------------------------------------------------
+
+int Dataset::load(const uint8_t *dG, const uint8_t *dph, int64_t S_, int64_t M_)
+{
+    S = S_;
+    M = M_;
+    S_pad = (S + 31) / 32 * 32;
+    cudaError_t e;
+    // Class index of every sample (cases first), phenotype validation.
+    int32_t *case_idx = nullptr, *ctrl_idx = nullptr;
+    int64_t *cc = nullptr;
+    if ((e = dev_alloc((void **)&case_idx, sizeof(int32_t) * M)) != cudaSuccess) return cuda_status(e, "alloc");
+    if ((e = dev_alloc((void **)&ctrl_idx, sizeof(int32_t) * M)) != cudaSuccess) {
+        cudaFree(case_idx);
+        return cuda_status(e, "alloc");
+    }
+    if ((e = dev_alloc((void **)&cc, sizeof(int64_t) * 2)) != cudaSuccess) {
+        cudaFree(case_idx); cudaFree(ctrl_idx);
+        return cuda_status(e, "alloc");
+    }
+    auto cleanup = [&]() { cudaFree(case_idx); cudaFree(ctrl_idx); cudaFree(cc); };
+    if ((e = dev_alloc((void **)&err, sizeof(uint32_t) * 4)) != cudaSuccess) { cleanup(); return cuda_status(e, "alloc"); }
+    cudaMemsetAsync(err, 0, sizeof(uint32_t) * 4, stream);
+
+    PackArgs pa{};
+    pa.G = dG; pa.ph = dph; pa.S = S; pa.M = M; pa.S_pad = S_pad;
+    pa.case_idx = case_idx; pa.ctrl_idx = ctrl_idx; pa.err = err; pa.class_count = cc;
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_class_index(pa, stream)) != cudaSuccess) {
+        cleanup();
+        return cuda_status(e, "class index kernel");
+    }
+    int64_t hcc[2] = {0, 0};
+    uint32_t herr = 0;
+    cudaMemcpyAsync(hcc, cc, sizeof hcc, cudaMemcpyDeviceToHost, stream);
+    cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) { cleanup(); return cuda_status(e, "class index"); }
+    if (herr & ERR_PHENOTYPE) { cleanup(); return set_error(FC_EINVAL, "phenotype value outside {0,1}"); }
+    M1 = hcc[0];
+    M0 = hcc[1];
+    if (M1 > FC_MAX_CLASS_SAMPLES || M0 > FC_MAX_CLASS_SAMPLES) {
+        cleanup();
+        return set_error(FC_ERANGE, "cases (%lld) or controls (%lld) exceed %d", (long long)M1,
+                         (long long)M0, FC_MAX_CLASS_SAMPLES);
+    }
+    W0 = (int)((M1 + 127) / 128);
+    Wt = W0 + (int)((M0 + 127) / 128);
+    const size_t xbytes = sizeof(uint4) * (size_t)std::max(Wt, 1) * 3 * S_pad;
+    if ((e = dev_alloc((void **)&X, xbytes)) != cudaSuccess) { cleanup(); return cuda_status(e, "bit table allocation"); }
+    cudaMemsetAsync(X, 0, xbytes, stream);
+    if ((e = dev_alloc((void **)&logtab, sizeof(float) * (M + 1))) != cudaSuccess) {
+        cleanup();
+        return cuda_status(e, "log table allocation");
+    }
+    pa.X = X; pa.W0 = W0; pa.Wt = Wt;
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_pack(pa, M1, M0, stream)) != cudaSuccess ||
+        (e = launch_logtab(logtab, M, stream)) != cudaSuccess) {
+        cleanup();
+        return cuda_status(e, "pack kernel");
+    }
+    cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) { cleanup(); return cuda_status(e, "pack"); }
+    cleanup();
+    if (herr & ERR_GENOTYPE) return set_error(FC_EINVAL, "genotype value outside {0,1,2}");
+    return FC_OK;
+}
+
+Dataset::~Dataset()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    cudaFree(X);
+    cudaFree(logtab);
+    cudaFree(err);
+    cudaFree(scratch);
+    if (ev_sweep0) cudaEventDestroy(ev_sweep0);
+    if (ev_sweep1) cudaEventDestroy(ev_sweep1);
+    if (own_stream && own_stream_handle) cudaStreamDestroy(own_stream_handle);
+}
+
+// ---- configuration ---------------------------------------------------------
+
+int list_capacity(int64_t N)
+{
+    int64_t want = N + std::max<int64_t>(32, N / 4);
+    int64_t L = 64;
+    while (L < want) L <<= 1;
+    return (int)L;
+}
+
+float score_error_bound(int k, int64_t M)
+{
+    // FP32 sweep: log table entries within 2^-24 relative, differences,
+    // products and 2*3^k accumulations each within 2^-24 relative of a
+    // partial sum bounded by N ln 2; see the design notes.  Doubled for
+    // margin.
+    const double u = std::ldexp(1.0, -24);
+    const double terms = 2.0 * pow3(k);
+    const double e = u * (2.0 * std::log((double)std::max<int64_t>(M, 2)) + (terms + 6.0) * std::log(2.0));
+    return (float)(2.0 * e);
+}
+
+TuneConfig Dataset::pick_config(int k, int L, int mode)
+{
+    TuneConfig c{};
+    c.G = 1;
+    c.WT = std::min(Wt, 64);
+    const int nws[3] = {8, 4, 2};
+    for (int i = 0; i < 3; ++i) {
+        c.NW = nws[i];
+        size_t smem = 0;
+        const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)M, &smem);
+        if (nb > 0) {
+            c.grid = nb * sms;
+            return c;
+        }
+    }
+    // Fall back to narrower tiles.
+    c.NW = 2;
+    c.WT = 16;
+    size_t smem = 0;
+    const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)M, &smem);
+    c.grid = std::max(nb, 1) * sms;
+    return c;
+}
+
+// ---- search ----------------------------------------------------------------
+
+int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count)
+{
+    const int64_t total = (int64_t)binom(S, k);
+    const int64_t N = std::min<int64_t>(top_n, total);
+    if (N == 0) { *out_count = 0; return FC_OK; }
+    int L = list_capacity(N);
+    if (L > FC_MAX_LIST) return set_error(FC_ERANGE, "top_n %lld too large", (long long)top_n);
+    const float eps = score_error_bound(k, M);
+    const double Nd = (double)M;
+    double hy = 0.0;
+    if (M1 > 0) hy -= (M1 / Nd) * std::log(M1 / Nd);
+    if (M0 > 0) hy -= (M0 / Nd) * std::log(M0 / Nd);
+    const int cells = pow3(k);
+
+    for (;;) {
+        TuneConfig cfg = pick_config(k, L, MODE_TOPN);
+        if (cfg.grid <= 0) return set_error(FC_ERANGE, "no launch configuration fits");
+        const int F = std::max(2, 4096 / L);
+        const int nl1 = (cfg.grid + F - 1) / F;
+        // Scratch layout.
+        Arena ar;
+        auto plan = [&](Arena &A, void **p) {
+            p[0] = A.take(sizeof(float) * (size_t)cfg.grid * L);
+            p[1] = A.take(sizeof(uint64_t) * (size_t)cfg.grid * L);
+            p[2] = A.take(sizeof(float) * (size_t)nl1 * L);
+            p[3] = A.take(sizeof(uint64_t) * (size_t)nl1 * L);
+            p[4] = A.take(sizeof(float) * (size_t)nl1 * L);
+            p[5] = A.take(sizeof(uint64_t) * (size_t)nl1 * L);
+            p[6] = A.take(sizeof(double) * L);
+            p[7] = A.take(sizeof(uint64_t) * L);
+            p[8] = A.take(sizeof(uint32_t) * (size_t)L * cells * 2);
+            p[9] = A.take(sizeof(uint32_t) * (size_t)N * k);
+            p[10] = A.take(sizeof(double) * (size_t)N);
+        };
+        void *p[11];
+        plan(ar, p);
+        int rc = reserve_scratch(ar.off);
+        if (rc) return rc;
+        Arena A2;
+        A2.base = scratch;
+        plan(A2, p);
+
+        cudaError_t e;
+        cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
+        SearchArgs sa{};
+        sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
+        sa.logtab = logtab; sa.M = (int)M;
+        sa.hy = (float)hy; sa.invN = (float)(1.0 / Nd);
+        sa.rank_begin = 0; sa.rank_end = (uint64_t)total;
+        sa.L = L;
+        sa.list_score = (float *)p[0];
+        sa.list_rank = (uint64_t *)p[1];
+        if (timing) cudaEventRecord(ev_sweep0, stream);
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_TOPN, sa, stream, nullptr)) != cudaSuccess)
+            return cuda_status(e, "search kernel");
+        if (timing) cudaEventRecord(ev_sweep1, stream);
+        note_launches(1);
+        // Grid merge.
+        const float *src_s = (const float *)p[0];
+        const uint64_t *src_r = (const uint64_t *)p[1];
+        int nl = cfg.grid;
+        int pp = 0;
+        while (nl > 1) {
+            float *ds = (float *)p[2 + 2 * pp];
+            uint64_t *dr = (uint64_t *)p[3 + 2 * pp];
+            int nout = 0;
+            if ((e = launch_merge(src_s, src_r, nl, L, ds, dr, &nout, stream)) != cudaSuccess)
+                return cuda_status(e, "merge kernel");
+            src_s = ds; src_r = dr; nl = nout; pp ^= 1;
+            note_launches(1);
+        }
+        RescoreArgs ra{};
+        ra.X = X; ra.S = S; ra.S_pad = S_pad; ra.W0 = W0; ra.Wt = Wt; ra.k = k;
+        ra.N = (int)N; ra.L = L; ra.cand_s = src_s; ra.cand_r = src_r; ra.eps = eps;
+        ra.total = (uint64_t)total;
+        ra.res_s = (double *)p[6]; ra.res_r = (uint64_t *)p[7]; ra.res_tab = (uint32_t *)p[8];
+        ra.err = err;
+        if ((e = launch_rescore(ra, stream)) != cudaSuccess) return cuda_status(e, "rescore kernel");
+        if ((e = launch_final_sort((double *)p[6], (uint64_t *)p[7], L, (int)N, k, S, (uint32_t *)p[9],
+                                   (double *)p[10], stream)) != cudaSuccess)
+            return cuda_status(e, "final sort kernel");
+        note_launches(2);
+        uint32_t herr = 0;
+        cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(out_idx, p[9], sizeof(uint32_t) * (size_t)N * k, cudaMemcpyDeviceToHost, stream);
+        cudaMemcpyAsync(out_score, p[10], sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, stream);
+        if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "search");
+        if (timing) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev_sweep0, ev_sweep1) == cudaSuccess) {
+                sweep_ms += ms;
+                sweeps += 1;
+            }
+        }
+        last_list = L;
+        last_grid = cfg.grid;
+        if (herr & ERR_LIST_SHORT) {
+            L *= 4;
+            if (L > FC_MAX_LIST)
+                return set_error(FC_ERANGE, "more than %d candidates lie within the FP32 error window",
+                                 FC_MAX_LIST);
+            continue;
+        }
+        *out_count = N;
+        return FC_OK;
+    }
+}
+
+int Dataset::scores(int k, uint64_t rank_begin, int64_t n, float *out)
+{
+    if (n == 0) return FC_OK;
+    TuneConfig cfg = pick_config(k, 0, MODE_SCORES);
+    const int64_t per_cta = (int64_t)cfg.NW * 32;
+    cfg.grid = (int)std::max<int64_t>(1, std::min<int64_t>(cfg.grid, (n + per_cta - 1) / per_cta));
+    Arena ar;
+    ar.take(sizeof(float) * n);
+    int rc = reserve_scratch(ar.off);
+    if (rc) return rc;
+    const double Nd = (double)M;
+    double hy = 0.0;
+    if (M1 > 0) hy -= (M1 / Nd) * std::log(M1 / Nd);
+    if (M0 > 0) hy -= (M0 / Nd) * std::log(M0 / Nd);
+    SearchArgs sa{};
+    sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
+    sa.logtab = logtab; sa.M = (int)M;
+    sa.hy = (float)hy; sa.invN = (float)(1.0 / Nd);
+    sa.rank_begin = rank_begin; sa.rank_end = rank_begin + (uint64_t)n;
+    sa.L = 0;
+    sa.dump_score = (float *)scratch;
+    cudaError_t e;
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_SCORES, sa, stream, nullptr)) != cudaSuccess)
+        return cuda_status(e, "score kernel");
+    note_launches(1);
+    cudaMemcpyAsync(out, scratch, sizeof(float) * n, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "scores");
+    return FC_OK;
+}
+
+int Dataset::tables(int k, const uint32_t *combos, int64_t n, uint32_t *out)
+{
+    if (n == 0) return FC_OK;
+    const int cells = pow3(k);
+    Arena ar;
+    void *dc = ar.take(sizeof(uint32_t) * (size_t)n * k);
+    void *dout = ar.take(sizeof(uint32_t) * (size_t)n * cells * 2);
+    int rc = reserve_scratch(ar.off);
+    if (rc) return rc;
+    Arena A2;
+    A2.base = scratch;
+    dc = A2.take(sizeof(uint32_t) * (size_t)n * k);
+    dout = A2.take(sizeof(uint32_t) * (size_t)n * cells * 2);
+    cudaError_t e;
+    cudaMemcpyAsync(dc, combos, sizeof(uint32_t) * (size_t)n * k, cudaMemcpyHostToDevice, stream);
+    TablesArgs ta{};
+    ta.X = X; ta.S = S; ta.S_pad = S_pad; ta.W0 = W0; ta.Wt = Wt; ta.k = k;
+    ta.combos = (const uint32_t *)dc; ta.n = n; ta.out = (uint32_t *)dout;
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_tables(ta, stream)) != cudaSuccess)
+        return cuda_status(e, "tables kernel");
+    note_launches(1);
+    cudaMemcpyAsync(out, dout, sizeof(uint32_t) * (size_t)n * cells * 2, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tables");
+    return FC_OK;
+}
+
+}  // namespace fc
+
+// ---- C ABI -----------------------------------------------------------------
+
+struct fc_handle {
+    fc::Dataset ds;
+};
+
+namespace {
+
+int make_handle(fc_handle **out, int *dev)
+{
+    int sms = 0;
+    int rc = check_device(dev, &sms);
+    if (rc) return rc;
+    fc_handle *h = new (std::nothrow) fc_handle();
+    if (!h) return set_error(FC_ENOMEM, "host allocation");
+    h->ds.device = *dev;
+    h->ds.sms = sms;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->ds.own_stream_handle, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_status(e, "stream creation");
+    }
+    h->ds.own_stream = true;
+    h->ds.stream = h->ds.own_stream_handle;
+    *out = h;
+    return FC_OK;
+}
+
+template <typename F>
+int guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (...) {
+        return set_error(FC_ENOMEM, "host exception");
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fc_load(const uint8_t *genotypes, int64_t S, int64_t M, const uint8_t *phenotype, fc_handle **out)
+{
+    return guarded([&]() -> int {
+        if (!out) return set_error(FC_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!genotypes || !phenotype) return set_error(FC_EINVAL, "NULL input");
+        if (S <= 0 || M <= 0 || S >= ((int64_t)1 << 31) || M >= ((int64_t)1 << 31))
+            return set_error(FC_EINVAL, "S and M must be in [1, 2^31)");
+        int dev = 0;
+        fc_handle *h = nullptr;
+        int rc = make_handle(&h, &dev);
+        if (rc) return rc;
+        uint8_t *dG = nullptr, *dph = nullptr;
+        cudaError_t e;
+        if ((e = dev_alloc((void **)&dG, (size_t)S * M)) != cudaSuccess) {
+            delete h;
+            return cuda_status(e, "genotype staging allocation");
+        }
+        if ((e = dev_alloc((void **)&dph, (size_t)M)) != cudaSuccess) {
+            cudaFree(dG);
+            delete h;
+            return cuda_status(e, "phenotype staging allocation");
+        }
+        cudaMemcpyAsync(dG, genotypes, (size_t)S * M, cudaMemcpyHostToDevice, h->ds.stream);
+        cudaMemcpyAsync(dph, phenotype, (size_t)M, cudaMemcpyHostToDevice, h->ds.stream);
+        rc = h->ds.load(dG, dph, S, M);
+        cudaStreamSynchronize(h->ds.stream);
+        cudaFree(dG);
+        cudaFree(dph);
+        if (rc) { delete h; return rc; }
+        *out = h;
+        return FC_OK;
+    });
+}
+
+int fc_load_device(const uint8_t *d_genotypes, int64_t S, int64_t M, const uint8_t *d_phenotype,
+                   fc_handle **out)
+{
+    return guarded([&]() -> int {
+        if (!out) return set_error(FC_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!d_genotypes || !d_phenotype) return set_error(FC_EINVAL, "NULL input");
+        if (S <= 0 || M <= 0 || S >= ((int64_t)1 << 31) || M >= ((int64_t)1 << 31))
+            return set_error(FC_EINVAL, "S and M must be in [1, 2^31)");
+        int dev = 0;
+        fc_handle *h = nullptr;
+        int rc = make_handle(&h, &dev);
+        if (rc) return rc;
+        cudaDeviceSynchronize();  // inputs may have been written on another stream
+        rc = h->ds.load(d_genotypes, d_phenotype, S, M);
+        if (rc) { delete h; return rc; }
+        *out = h;
+        return FC_OK;
+    });
+}
+
+int fc_set_stream(fc_handle *h, void *cuda_stream)
+{
+    if (!h) return set_error(FC_EINVAL, "NULL handle");
+    cudaStreamSynchronize(h->ds.stream);
+    h->ds.stream = cuda_stream ? (cudaStream_t)cuda_stream : h->ds.own_stream_handle;
+    return FC_OK;
+}
+
+int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count)
+{
+    return guarded([&]() -> int {
+        if (!h || !out_count) return set_error(FC_EINVAL, "NULL handle or out_count");
+        if (k < 1 || k > FC_KMAX_SEARCH || k > h->ds.S)
+            return set_error(FC_EINVAL, "order k=%d outside [1, min(%d, S)]", k, FC_KMAX_SEARCH);
+        if (top_n < 0) return set_error(FC_EINVAL, "top_n < 0");
+        if (top_n > FC_MAX_LIST / 2) return set_error(FC_ERANGE, "top_n above %d", FC_MAX_LIST / 2);
+        if (top_n > 0 && (!out_idx || !out_score)) return set_error(FC_EINVAL, "NULL output");
+        if (fc_num_combinations(h->ds.S, k) < 0 || fc_num_combinations(h->ds.S, k) >= ((int64_t)1 << 60))
+            return set_error(FC_ERANGE, "C(S, k) >= 2^60");
+        DeviceGuard g(h->ds.device);
+        return h->ds.search(k, top_n, out_idx, out_score, out_count);
+    });
+}
+
+int fc_tables(fc_handle *h, int k, const uint32_t *combos, int64_t n, uint32_t *out)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (k < 1 || k > FC_KMAX_TABLES) return set_error(FC_EINVAL, "order k=%d outside [1, %d]", k, FC_KMAX_TABLES);
+        if (n < 0) return set_error(FC_EINVAL, "n < 0");
+        if (n > 0 && (!combos || !out)) return set_error(FC_EINVAL, "NULL buffer");
+        for (int64_t i = 0; i < n * k; ++i)
+            if ((int64_t)combos[i] >= h->ds.S) return set_error(FC_EINVAL, "SNP index %u >= S", combos[i]);
+        DeviceGuard g(h->ds.device);
+        return h->ds.tables(k, combos, n, out);
+    });
+}
+
+int fc_scores(fc_handle *h, int k, uint64_t rank_begin, int64_t n, float *out)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (k < 1 || k > FC_KMAX_SEARCH || k > h->ds.S) return set_error(FC_EINVAL, "bad order k=%d", k);
+        if (n < 0 || (n > 0 && !out)) return set_error(FC_EINVAL, "bad output");
+        const int64_t total = fc_num_combinations(h->ds.S, k);
+        if (total < 0) return set_error(FC_ERANGE, "C(S, k) too large");
+        if (rank_begin > (uint64_t)total || (uint64_t)n > (uint64_t)total - rank_begin)
+            return set_error(FC_EINVAL, "rank range outside [0, C(S, k))");
+        DeviceGuard g(h->ds.device);
+        return h->ds.scores(k, rank_begin, n, out);
+    });
+}
+
+int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64_t *launches)
+{
+    if (!h) return set_error(FC_EINVAL, "NULL handle");
+    fc::Dataset &d = h->ds;
+    if (sweep_ms) *sweep_ms = d.sweep_ms;
+    if (sweeps) *sweeps = d.sweeps;
+    if (launches) *launches = d.launches;
+    if (enable >= 0) {
+        DeviceGuard g(d.device);
+        if (enable && !d.ev_sweep0) {
+            cudaError_t e;
+            if ((e = cudaEventCreate(&d.ev_sweep0)) != cudaSuccess) return cuda_status(e, "event");
+            if ((e = cudaEventCreate(&d.ev_sweep1)) != cudaSuccess) return cuda_status(e, "event");
+        }
+        d.timing = enable != 0;
+        d.sweep_ms = 0.0;
+        d.sweeps = 0;
+        d.launches = 0;
+    }
+    return FC_OK;
+}
+
+int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls)
+{
+    if (!h) return set_error(FC_EINVAL, "NULL handle");
+    if (S) *S = h->ds.S;
+    if (M) *M = h->ds.M;
+    if (cases) *cases = h->ds.M1;
+    if (controls) *controls = h->ds.M0;
+    return FC_OK;
+}
+
+void fc_free(fc_handle *h)
+{
+    if (!h) return;
+    DeviceGuard g(h->ds.device);
+    delete h;
+}
+
+const char *fc_strerror(int status)
+{
+    switch (status) {
+    case FC_OK: return "success";
+    case FC_EINVAL: return "invalid argument or input value";
+    case FC_ERANGE: return "size outside the supported limits";
+    case FC_ENOMEM: return "out of memory";
+    case FC_ECUDA: return "CUDA error";
+    case FC_ETIMEOUT: return "bounded device wait ran out";
+    case FC_ENODEV: return "no usable CUDA device";
+    default: return "unknown status";
+    }
+}
+
+const char *fc_last_error(void) { return g_last_error; }
+
+int64_t fc_num_combinations(int64_t S, int k)
+{
+    if (S < 0 || k < 0 || k > 64) return -1;
+    if (k > S) return 0;
+    int r = (int)std::min<int64_t>(k, S - k);
+    unsigned __int128 c = 1;
+    for (int i = 1; i <= r; ++i) {
+        c = c * (unsigned __int128)(S - r + i) / (unsigned __int128)i;
+        if (c >= ((unsigned __int128)1 << 62)) return -1;
+    }
+    return (int64_t)c;
+}
+
+int fc_unrank(int64_t S, int k, uint64_t rank, uint32_t *out)
+{
+    if (!out || k < 1 || k > FC_KMAX_TABLES || S < k || S >= ((int64_t)1 << 31))
+        return set_error(FC_EINVAL, "bad arguments");
+    const int64_t total = fc_num_combinations(S, k);
+    if (total < 0 || total >= ((int64_t)1 << 60)) return set_error(FC_ERANGE, "C(S, k) too large");
+    if (rank >= (uint64_t)total) return set_error(FC_EINVAL, "rank >= C(S, k)");
+    unrank(S, k, rank, out);
+    return FC_OK;
+}
+
+int fc_rank(int64_t S, int k, const uint32_t *combo, uint64_t *rank)
+{
+    if (!combo || !rank || k < 1 || k > FC_KMAX_TABLES || S < k || S >= ((int64_t)1 << 31))
+        return set_error(FC_EINVAL, "bad arguments");
+    const int64_t total = fc_num_combinations(S, k);
+    if (total < 0 || total >= ((int64_t)1 << 60)) return set_error(FC_ERANGE, "C(S, k) too large");
+    for (int t = 0; t < k; ++t) {
+        if ((int64_t)combo[t] >= S || (t > 0 && combo[t] <= combo[t - 1]))
+            return set_error(FC_EINVAL, "combination must be strictly increasing and < S");
+    }
+    *rank = rank_of(S, k, combo);
+    return FC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// Internal host-runtime declarations (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fiuncho.h"
+#include "fc_internal.cuh"
+
+namespace fc {
+
+int set_error(int status, const char *fmt, ...);
+int cuda_status(cudaError_t e, const char *what);
+cudaError_t dev_alloc(void **p, size_t bytes);
+cudaError_t launch_gate();
+void fault_counters_reset();
+int check_device(int *dev, int *sms);
+int list_capacity(int64_t N);
+float score_error_bound(int k, int64_t M);
+
+struct DeviceGuard {
+    int prev = 0;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+// Bump allocator used twice per call: once with base = nullptr to size the
+// scratch area, once over the real allocation.
+struct Arena {
+    void *base = nullptr;
+    size_t off = 0;
+    void *take(size_t bytes);
+};
+
+// One packed data set on one device.
+struct Dataset {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream_handle = nullptr;
+    bool own_stream = false;
+
+    int64_t S = 0, M = 0, M1 = 0, M0 = 0, S_pad = 0;
+    int W0 = 0, Wt = 0;
+    uint4 *X = nullptr;        // bit table [Wt][3][S_pad]
+    float *logtab = nullptr;   // ln(n), n = 0..M
+    uint32_t *err = nullptr;   // device error word(s)
+
+    void *scratch = nullptr;   // reusable work area (grown on demand)
+    size_t scratch_cap = 0;
+
+    int last_list = 0, last_grid = 0;
+
+    // Optional instrumentation (fc_timing): CUDA events around the sweep
+    // kernel on the launching stream, and a count of kernel launches.
+    bool timing = false;
+    cudaEvent_t ev_sweep0 = nullptr, ev_sweep1 = nullptr;
+    double sweep_ms = 0.0;
+    int64_t sweeps = 0, launches = 0;
+    void note_launches(int64_t n) { if (timing) launches += n; }
+
+    ~Dataset();
+    int load(const uint8_t *dG, const uint8_t *dph, int64_t S, int64_t M);
+    int reserve_scratch(size_t bytes);
+    TuneConfig pick_config(int k, int L, int mode);
+    int search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count);
+    int scores(int k, uint64_t rank_begin, int64_t n, float *out);
+    int tables(int k, const uint32_t *combos, int64_t n, uint32_t *out);
+};
+
+}  // namespace fc

@@ -162,10 +162,11 @@ def cpu_baseline_sample(ds, k, seconds):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
+    P0 = 16 * cores              # calibration sample: every thread gets prefixes
     t0 = time.perf_counter()
-    _, _, tested = oracle.search(ds.genotypes, ds.phenotype, k, 10, 0, (0, 8))
+    _, _, tested = oracle.search(ds.genotypes, ds.phenotype, k, 10, 0, (0, P0))
     dt = max(time.perf_counter() - t0, 1e-3)
-    per_prefix = dt / 8
+    per_prefix = dt / P0
     npfx = math.comb(ds.S - 1, k - 1)
     P = int(max(8, min(npfx, seconds / per_prefix)))
     t0 = time.perf_counter()
@@ -187,9 +188,10 @@ def run_reference(args):
     k = ds.k
     cores = os.cpu_count() or 1
     # Size one step at ~ (a few minutes / steps) of CPU time.
+    P0 = 16 * cores
     t0 = time.perf_counter()
-    oracle.search(ds.genotypes, ds.phenotype, k, ds.top_n, 0, (0, 8))
-    per_prefix = max(time.perf_counter() - t0, 1e-3) / 8
+    oracle.search(ds.genotypes, ds.phenotype, k, ds.top_n, 0, (0, P0))
+    per_prefix = max(time.perf_counter() - t0, 1e-3) / P0
     npfx = math.comb(ds.S - 1, k - 1)
     budget = min(8.0, 150.0 / max(1, args.steps + args.warmup))
     P = int(max(8, min(npfx, budget / per_prefix)))

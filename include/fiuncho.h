@@ -107,6 +107,43 @@ int fc_set_stream(fc_handle *h, void *cuda_stream);
 int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
               int64_t *out_count);
 
+/* Size of the fixed device work area used by fc_search_static. */
+#define FC_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
+
+/*
+ * fc_search_static - fc_search that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc at search time.  cudaMalloc and cudaFree may
+ * synchronise the whole device and take a driver-wide lock, so an
+ * application that shares the GPU with latency-sensitive work, or a
+ * framework whose own caching allocator owns the device memory budget, may
+ * forbid them on its hot path; fc_search instead grows a per-handle work
+ * area with cudaMalloc on first use.  fc_search_static takes its work area
+ * from a fixed FC_STATIC_SCRATCH_BYTES (8 MiB) array compiled into the
+ * library's device image, which every GPU that loads the library holds
+ * until the process exits.
+ *
+ * Arguments, results and ordering are those of fc_search; the handle (made
+ * by fc_load, which does allocate) and the host output buffers are still
+ * the caller's.  It calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ * Limits and behaviour:
+ *   - a search whose work area (per-CTA candidate lists, merge and
+ *     rescoring buffers, device results) exceeds FC_STATIC_SCRATCH_BYTES
+ *     fails with FC_ERANGE and a message giving the size it needed; this
+ *     happens for large top_n (e.g. top_n = 2000 needs about 15 MiB);
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - all calls share the one array and each overwrites what the previous
+ *     one left there (every byte read is written first in the same call, so
+ *     nothing needs clearing); calls whose GPU work overlaps in time, from
+ *     different streams or threads, race on it and must not be issued.
+ */
+int fc_search_static(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
+                     int64_t *out_count);
+
 /*
  * fc_tables - exact contingency tables of n given combinations (Fig. 3).
  *

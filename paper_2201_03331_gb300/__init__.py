@@ -27,6 +27,7 @@ from ._binding import (  # noqa: F401
     fc_rank,
     fc_scores,
     fc_search,
+    fc_search_static,
     fc_set_stream,
     fc_strerror,
     fc_tables,

@@ -38,6 +38,7 @@ _SIGNATURES = {
     "fc_load_device": ([P, i64, i64, P, P], i32),
     "fc_set_stream": ([P, P], i32),
     "fc_search": ([P, i32, i64, P, P, P], i32),
+    "fc_search_static": ([P, i32, i64, P, P, P], i32),
     "fc_tables": ([P, i32, P, i64, P], i32),
     "fc_scores": ([P, i32, u64, i64, P], i32),
     "fc_info": ([P, P, P, P, P], i32),
@@ -144,6 +145,18 @@ def fc_search(h: Handle, k: int, top_n: int):
     score = np.zeros(max(top_n, 1), dtype=np.float64)
     cnt = ctypes.c_int64(0)
     _check(library().fc_search(h.ptr, k, top_n, _ptr(idx), _ptr(score), ctypes.byref(cnt)), "fc_search")
+    n = cnt.value
+    return idx[:n], score[:n]
+
+
+def fc_search_static(h: Handle, k: int, top_n: int):
+    """As :func:`fc_search`, through the entry point that allocates no
+    device memory (fixed 8 MiB work area in the library's device image)."""
+    idx = np.zeros((max(top_n, 1), k), dtype=np.uint32)
+    score = np.zeros(max(top_n, 1), dtype=np.float64)
+    cnt = ctypes.c_int64(0)
+    _check(library().fc_search_static(h.ptr, k, top_n, _ptr(idx), _ptr(score), ctypes.byref(cnt)),
+           "fc_search_static")
     n = cnt.value
     return idx[:n], score[:n]
 

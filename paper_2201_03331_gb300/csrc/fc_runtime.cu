@@ -262,7 +262,8 @@ TuneConfig Dataset::pick_config(int k, int L, int mode)
 
 // ---- search ----------------------------------------------------------------
 
-int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count)
+int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
+                    void *ext_scratch, size_t ext_cap)
 {
     const int64_t total = (int64_t)binom(S, k);
     const int64_t N = std::min<int64_t>(top_n, total);
@@ -298,10 +299,19 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         };
         void *p[11];
         plan(ar, p);
-        int rc = reserve_scratch(ar.off);
-        if (rc) return rc;
         Arena A2;
-        A2.base = scratch;
+        if (ext_scratch) {
+            // Caller-provided scratch (the allocation-free entry point).
+            if (ar.off > ext_cap)
+                return set_error(FC_ERANGE,
+                                 "search needs %zu bytes of scratch; the static scratch area holds %zu",
+                                 ar.off, ext_cap);
+            A2.base = ext_scratch;
+        } else {
+            int rc = reserve_scratch(ar.off);
+            if (rc) return rc;
+            A2.base = scratch;
+        }
         plan(A2, p);
 
         cudaError_t e;
@@ -547,6 +557,71 @@ int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out
             return set_error(FC_ERANGE, "C(S, k) >= 2^60");
         DeviceGuard g(h->ds.device);
         return h->ds.search(k, top_n, out_idx, out_score, out_count);
+    });
+}
+
+}  // extern "C"
+
+// ---- allocation-free search ------------------------------------------------
+// fc_search_static runs the same search as fc_search, but its work area (the
+// per-CTA candidate lists, the merge buffers, the rescoring buffers and the
+// device copy of the results) is this fixed array in the library's device
+// image instead of memory obtained from cudaMalloc.  Every device that loads
+// the library holds the array until the process exits.  All calls share it:
+// each call writes every byte it later reads (no part needs to start at
+// zero), so the previous call's contents are simply overwritten, and two
+// calls whose GPU work overlaps (different streams or threads) race on it.
+static __device__ __align__(256) unsigned char g_static_scratch[FC_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 128;
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on device `dev`, looked up once per
+// device with that device current.  In host code the array's name is only a
+// host-side stand-in; the kernels must be given this address.
+int static_scratch_address(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (dev < 0 || dev >= kMaxDevices) return set_error(FC_EINVAL, "device ordinal %d out of range", dev);
+    if (!g_static_addr[dev]) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+        if (cur != dev) return set_error(FC_ECUDA, "static scratch set-up needs device %d current", dev);
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return FC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fc_search_static(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
+                     int64_t *out_count)
+{
+    return guarded([&]() -> int {
+        if (!h || !out_count) return set_error(FC_EINVAL, "NULL handle or out_count");
+        if (k < 1 || k > FC_KMAX_SEARCH || k > h->ds.S)
+            return set_error(FC_EINVAL, "order k=%d outside [1, min(%d, S)]", k, FC_KMAX_SEARCH);
+        if (top_n < 0) return set_error(FC_EINVAL, "top_n < 0");
+        if (top_n > FC_MAX_LIST / 2) return set_error(FC_ERANGE, "top_n above %d", FC_MAX_LIST / 2);
+        if (top_n > 0 && (!out_idx || !out_score)) return set_error(FC_EINVAL, "NULL output");
+        if (fc_num_combinations(h->ds.S, k) < 0 || fc_num_combinations(h->ds.S, k) >= ((int64_t)1 << 60))
+            return set_error(FC_ERANGE, "C(S, k) >= 2^60");
+        DeviceGuard g(h->ds.device);
+        void *scratch = nullptr;
+        int rc = static_scratch_address(h->ds.device, &scratch);
+        if (rc) return rc;
+        return h->ds.search(k, top_n, out_idx, out_score, out_count, scratch,
+                            (size_t)FC_STATIC_SCRATCH_BYTES);
     });
 }
 

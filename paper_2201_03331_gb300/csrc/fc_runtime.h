@@ -64,7 +64,10 @@ struct Dataset {
     int load(const uint8_t *dG, const uint8_t *dph, int64_t S, int64_t M);
     int reserve_scratch(size_t bytes);
     TuneConfig pick_config(int k, int L, int mode);
-    int search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count);
+    // ext_scratch: if non-null, a device work area of ext_cap bytes used instead
+    // of the handle's own (grown-on-demand) scratch allocation.
+    int search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
+               void *ext_scratch = nullptr, size_t ext_cap = 0);
     int scores(int k, uint64_t rank_begin, int64_t n, float *out);
     int tables(int k, const uint32_t *combos, int64_t n, uint32_t *out);
 };

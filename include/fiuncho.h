@@ -173,6 +173,21 @@ int fc_scores(fc_handle *h, int k, uint64_t rank_begin, int64_t n, float *out);
  */
 int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64_t *launches);
 
+/*
+ * fc_pairs_dense - every order-2 table or FP32 score computed by the
+ * tensor-core pair kernel (the k = 2 path fc_search takes for S >= 1024).
+ * A parity hook for the contraction and its epilogue.
+ * scores : host float [S][S] or NULL; scores[i][j] for i < j, 0 elsewhere
+ *          (S <= 8192).
+ * tables : host uint32 [S][S][9][2] or NULL; the table of (i, j), i < j, in
+ *          the layout of fc_tables, 0 elsewhere (S <= 1024).
+ */
+int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables);
+
+/* fc_last_search_kind - which sweep the last fc_search on h ran:
+ * 0 none yet, 1 prefix-table AND/POPC sweep, 2 tensor-core order-2 pairs. */
+int fc_last_search_kind(const fc_handle *h);
+
 /* fc_info - sizes of a loaded data set (any pointer may be NULL). */
 int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls);
 

@@ -20,6 +20,8 @@ from ._binding import (  # noqa: F401
     LIB_PATH,
     fc_free,
     fc_info,
+    fc_last_search_kind,
+    fc_pairs_dense,
     fc_last_error,
     fc_load,
     fc_load_device,

@@ -42,6 +42,8 @@ _SIGNATURES = {
     "fc_tables": ([P, i32, P, i64, P], i32),
     "fc_scores": ([P, i32, u64, i64, P], i32),
     "fc_info": ([P, P, P, P, P], i32),
+    "fc_pairs_dense": ([P, P, P], i32),
+    "fc_last_search_kind": ([P], i32),
     "fc_timing": ([P, i32, P, P, P], i32),
     "fc_free": ([P], None),
     "fc_strerror": ([i32], ctypes.c_char_p),
@@ -174,6 +176,25 @@ def fc_scores(h: Handle, k: int, rank_begin: int, n: int) -> np.ndarray:
     out = np.zeros(n, dtype=np.float32)
     _check(library().fc_scores(h.ptr, k, rank_begin, n, _ptr(out)), "fc_scores")
     return out
+
+
+def fc_pairs_dense(h: Handle, scores: bool = True, tables: bool = False):
+    """Dense order-2 output of the tensor-core kernel: ``(scores float32[S][S]
+    or None, tables uint32[S][S][9][2] or None)`` (entries with i < j)."""
+    S = fc_info(h)[0]
+    sc = np.zeros((S, S), dtype=np.float32) if scores else None
+    tb = np.zeros((S, S, 9, 2), dtype=np.uint32) if tables else None
+    _check(library().fc_pairs_dense(h.ptr, _ptr(sc) if sc is not None else None,
+                                    _ptr(tb) if tb is not None else None), "fc_pairs_dense")
+    return sc, tb
+
+
+def fc_last_search_kind(h: Handle) -> int:
+    """0 none, 1 prefix-table AND/POPC sweep, 2 tensor-core order-2 pairs."""
+    r = library().fc_last_search_kind(h.ptr)
+    if r < 0:
+        _check(r, "fc_last_search_kind")
+    return int(r)
 
 
 def fc_info(h: Handle):

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace fc {
@@ -154,6 +155,37 @@ struct RescoreArgs {
 cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st);
 cudaError_t launch_final_sort(double *res_s, uint64_t *res_r, int L, int N, int k, int64_t S,
                               uint32_t *out_idx, double *out_score, cudaStream_t st);
+
+// ---- order-2 tensor-core path (fc_pairs_tc.cu) -----------------------------
+
+constexpr int TC_MAX_STAGES = 6;
+enum { MODE_DUMP = 2 };
+
+struct PairsArgs {
+    const uint32_t *tiles;  // (I << 16 | J) 64-SNP block pairs, I <= J
+    int ntiles;
+    int64_t S;
+    int W0, Wt;             // 128-sample chunks: cases [0, W0), controls [W0, Wt)
+    const uint16_t *marg;   // [S][8]: cases g0..g2, controls g0..g2, pad
+    const float *logtab;
+    int M;
+    float hy, invN;
+    uint64_t pair_base;     // C(S, 2)
+    int L, Bcap, P2, stages;
+    float *list_score;      // [grid][L]
+    uint64_t *list_rank;
+    int *gthr;              // global score threshold (ordered int)
+    uint32_t *err;
+    float *dump_scores;     // MODE_DUMP: [S][S] (i < j)
+    uint32_t *dump_tables;  // MODE_DUMP: [S][S][9][2]
+};
+
+size_t pairs_smem_bytes(int stages, int M, int P2);
+cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, uint8_t *E,
+                               cudaStream_t st);
+cudaError_t launch_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint16_t *marg,
+                             cudaStream_t st);
+cudaError_t launch_pairs_tc(int mode, const CUtensorMap &tmap, const PairsArgs &a, int grid, cudaStream_t st);
 
 struct TablesArgs {
     const uint4 *X;

@@ -1,0 +1,584 @@
+// Order-2 all-pairs search on the fifth-generation tensor cores (tcgen05).
+//
+// For k = 2 the contingency counts of every SNP pair form a dense binary
+// contraction (Section "Computing the contingency tables": a cell is the
+// population count of the AND of one row of each SNP's genotype table):
+//     n_c(g, h)[i, j] = sum_{m in class c} [G_i(m) = g] [G_j(m) = h].
+// With the genotype rows g, h in {0, 1} stored as 0/1 e4m3 bytes
+// (E[2s + g][m]), one class's counts for all pairs are E_c E_c^T.  Products
+// of 0/1 are exact and FP32 accumulation of integers below 2^24 is exact,
+// so tcgen05.mma kind::f8f6f4 computes the four {0,1}x{0,1} cells of every
+// pair exactly.  The five cells that involve genotype 2 follow exactly from
+// the per-SNP genotype counts (the rows of each SNP's genotype table
+// partition the samples):
+//     n(g,2) = n_i(g) - n(g,0) - n(g,1),   n(2,h) = n_j(h) - n(0,h) - n(1,h),
+//     n(2,2) = n_i(2) - n(2,0) - n(2,1).
+// The epilogue scores each pair with the same FP32 mutual information as the
+// sweep kernel and keeps a CTA top list; the count matrix is never written.
+//
+// Roles (one persistent CTA per SM, 192 threads):
+//   warp 0 : TMA producer (128-byte K chunks of the A and B row blocks)
+//   warp 1 : TMEM allocation and the single-thread MMA issue
+//   warps 2-5 : epilogue (TMEM -> registers -> table -> MI -> top list)
+// Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
+#include <cuda.h>
+#include <cfloat>
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+constexpr int TC_BM = 128;          // tile rows: 64 SNPs x genotype rows {0,1}
+constexpr int TC_BN = 128;          // tile columns
+constexpr int TC_BK = 128;          // K bytes (samples) per pipeline stage
+constexpr int TC_SNPS = 64;         // SNPs per tile side
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;   // 16 KiB
+constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK;   // 16 KiB
+constexpr unsigned FULL = 0xffffffffu;
+constexpr long long WAIT_BUDGET = 4000000000ll;  // clock64 ticks (~2 s) per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity.  On timeout it raises the
+// CTA abort flag and the device error word; every role then leaves its loop.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint32_t *err)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_BUDGET) {
+            *abort_flag = 1;
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with the
+// 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms.
+// Fields: start address >> 4 (bits 0-13), leading byte offset >> 4 (16-29,
+// unused for swizzled K-major, set to 1), stride byte offset >> 4 (32-45:
+// 1024 bytes between 8-row groups), fixed 0b001 at bits 46-48, swizzle mode
+// 2 (128 B) at bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3fff);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3
+// (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Exact integer value of an FP32 accumulator holding an integer in [0, 2^23).
+__device__ __forceinline__ uint32_t f2u_exact(uint32_t bits)
+{
+    return __float_as_uint(__uint_as_float(bits) + 8388608.0f) - 0x4B000000u;
+}
+
+__device__ __forceinline__ int ordered_int(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float from_ordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Descending bitonic sort of n = 2^p (score, rank) pairs by the 128
+// epilogue threads (tid in [0,128)).
+__device__ void epi_bitonic_desc(float *s, uint64_t *r, int n, int tid)
+{
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            epi_bar();
+            for (int i = tid; i < (n >> 1); i += 128) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool desc = (lo & size) == 0;
+                const float s1 = s[lo], s2 = s[hi];
+                const uint64_t r1 = r[lo], r2 = r[hi];
+                const bool sw = desc ? better(s2, r2, s1, r1) : better(s1, r1, s2, r2);
+                if (sw) { s[lo] = s2; s[hi] = s1; r[lo] = r2; r[hi] = r1; }
+            }
+        }
+    }
+    epi_bar();
+}
+
+// ---- data preparation ------------------------------------------------------
+
+// E[2s + g][w*128 + b] = 0x38 (e4m3 1.0) if bit b of word w of genotype row
+// g of SNP s is set, else 0; rows of padding SNPs are zero.
+__global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, uint8_t *E)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * Wt) return;
+    const int64_t row = t / Wt;
+    const int w = (int)(t % Wt);
+    const int64_t s = row >> 1;
+    const int g = (int)(row & 1);
+    uint4 bits = make_uint4(0, 0, 0, 0);
+    if (s < S) bits = X[((size_t)w * 3 + g) * S_pad + s];
+    const uint32_t b32[4] = {bits.x, bits.y, bits.z, bits.w};
+    uint4 *dst = reinterpret_cast<uint4 *>(E + row * (int64_t)Wt * 128 + (int64_t)w * 128);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint32_t o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int bit0 = q * 16 + u * 4;
+            const uint32_t word = b32[bit0 >> 5];
+            const int sh = bit0 & 31;
+            uint32_t v = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v |= (((word >> (sh + e)) & 1u) ? 0x38u : 0u) << (8 * e);
+            o[u] = v;
+        }
+        dst[q] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// Per SNP and class, how many samples carry genotype 0, 1, 2:
+// marg[s*8 + c*3 + g], c = 0 cases, 1 controls.
+__global__ void k_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint16_t *marg)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    uint32_t cnt[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    for (int w = 0; w < Wt; ++w) {
+        const int c = w < W0 ? 0 : 1;
+        for (int g = 0; g < 3; ++g) {
+            const uint4 v = X[((size_t)w * 3 + g) * S_pad + s];
+            cnt[c][g] += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+    }
+    for (int c = 0; c < 2; ++c)
+        for (int g = 0; g < 3; ++g) marg[s * 8 + c * 3 + g] = (uint16_t)cnt[c][g];
+    marg[s * 8 + 6] = 0;
+    marg[s * 8 + 7] = 0;
+}
+
+// ---- the fused tensor-core kernel ------------------------------------------
+
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constant__ CUtensorMap tmap, PairsArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar_full[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
+    __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_done;
+    __shared__ uint32_t tmem_base_slot;
+    __shared__ int abort_flag_s;
+    __shared__ int buf_count;
+    __shared__ int epi_stop;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int stages = a.stages;
+    volatile int *abort_flag = &abort_flag_s;
+
+    uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stA = smem;
+    uint8_t *stB = smem + (size_t)stages * TC_A_BYTES;
+    float *logtab = reinterpret_cast<float *>(stB + (size_t)stages * TC_B_BYTES);
+    const int lt_floats = (a.M + 1 + 3) & ~3;
+    uint64_t *lrank = reinterpret_cast<uint64_t *>(logtab + lt_floats);
+    float *lscore = reinterpret_cast<float *>(lrank + a.P2);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_tfull[b], 1);
+            mbar_init(&bar_tempty[b], 4);
+        }
+        mbar_init(&bar_done, 1);
+        abort_flag_s = 0;
+        buf_count = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) logtab[i] = a.logtab[i];
+    if (MODE == MODE_TOPN) {
+        for (int i = threadIdx.x; i < a.P2; i += blockDim.x) {
+            lscore[i] = -FLT_MAX;
+            lrank[i] = NO_RANK;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_slot;
+
+    const int kc0 = a.W0, kc1 = a.Wt - a.W0;   // 128-sample chunks per class
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t fill = 0;   // running stage-fill counter
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                const uint32_t tile = a.tiles[t];
+                const int I = (int)(tile >> 16), J = (int)(tile & 0xffff);
+                for (int c = 0; c < 2 && ok; ++c) {
+                    const int nk = c ? kc1 : kc0;
+                    const int xbase = c ? kc0 * TC_BK : 0;
+                    for (int kc = 0; kc < nk; ++kc, ++fill) {
+                        const int s = fill % stages;
+                        const uint32_t n = fill / stages;
+                        if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
+                        mbar_expect_tx(&bar_full[s], TC_A_BYTES + TC_B_BYTES);
+                        tma_load_2d(&tmap, &bar_full[s], stA + (size_t)s * TC_A_BYTES, xbase + kc * TC_BK, I * TC_BM);
+                        tma_load_2d(&tmap, &bar_full[s], stB + (size_t)s * TC_B_BYTES, xbase + kc * TC_BK, J * TC_BN);
+                    }
+                }
+            }
+            // Let every copy issued so far land before the CTA can exit.
+            const uint32_t issued = fill;
+            for (uint32_t f = (issued > (uint32_t)stages ? issued - stages : 0); f < issued; ++f) {
+                const int s = f % stages;
+                const uint32_t n = f / stages;
+                long long t0 = clock64();
+                while (!mbar_try(&bar_full[s], n & 1) && clock64() - t0 < WAIT_BUDGET) {}
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_e4m3_f32(TC_BM, TC_BN);
+            uint32_t fill = 0;
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+                const int b = it & 1;
+                const uint32_t u = (uint32_t)(it >> 1);
+                if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err)) break;
+                tc_fence_after();
+                for (int c = 0; c < 2 && ok; ++c) {
+                    const int nk = c ? kc1 : kc0;
+                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + c * 128);
+                    for (int kc = 0; kc < nk; ++kc, ++fill) {
+                        const int s = fill % stages;
+                        const uint32_t n = fill / stages;
+                        if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t aaddr = smem_u32(stA + (size_t)s * TC_A_BYTES);
+                        const uint32_t baddr = smem_u32(stB + (size_t)s * TC_B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 32; ++kk) {
+                            mma_e4m3(d, smem_desc_sw128(aaddr + kk * 32), smem_desc_sw128(baddr + kk * 32), idesc,
+                                     (kc > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(&bar_empty[s]);
+                    }
+                }
+                if (ok) mma_commit(&bar_tfull[b]);
+            }
+            // All MMAs issued by this thread complete before TMEM is released.
+            mma_commit(&bar_done);
+            long long t0 = clock64();
+            while (!mbar_try(&bar_done, 0) && clock64() - t0 < WAIT_BUDGET) {}
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int tid = threadIdx.x - 64;           // 0..127
+        const int quarter = warp & 3;               // TMEM lanes 32*quarter ..
+        const int row = quarter * 32 + lane;        // tile row = 2*i_l + g
+        const int i_l = row >> 1;
+        const int g = row & 1;
+        const int L = a.L;
+        const int Bcap = a.Bcap;
+        float thr_s = -FLT_MAX;
+        uint64_t thr_r = NO_RANK;
+        int it = 0;
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+            const int b = it & 1;
+            const uint32_t u = (uint32_t)(it >> 1);
+            mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
+            // One stop decision for all four epilogue warps (they meet at
+            // named barriers, which have no timeout).
+            epi_bar();
+            if (tid == 0) epi_stop = *abort_flag;
+            epi_bar();
+            if (epi_stop) break;
+            tc_fence_after();
+            const uint32_t tile = a.tiles[t];
+            const int I = (int)(tile >> 16), J = (int)(tile & 0xffff);
+            const int64_t i = (int64_t)I * TC_SNPS + i_l;
+            uint32_t mi[2][3] = {{0, 0, 0}, {0, 0, 0}};
+            if (i < a.S) {
+                const uint4 m4 = *reinterpret_cast<const uint4 *>(a.marg + i * 8);
+                mi[0][0] = m4.x & 0xffff; mi[0][1] = m4.x >> 16; mi[0][2] = m4.y & 0xffff;
+                mi[1][0] = m4.y >> 16;    mi[1][1] = m4.z & 0xffff; mi[1][2] = m4.z >> 16;
+            }
+            const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+            for (int ch = 0; ch < TC_BN / 32; ++ch) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(taddr + ch * 32, v0);
+                tmem_ld32(taddr + 128 + ch * 32, v1);
+                tmem_wait_ld();
+                if (ch == TC_BN / 32 - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar_tempty[b]);
+                }
+                float sc[8];
+                uint64_t rk[8];
+                bool val[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    // This thread scores j = 2q + g of the chunk; its partner
+                    // lane (the other genotype row of SNP i) scores 2q + 1 - g.
+                    uint32_t own[2][2], oth[2][2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t s0 = g ? v0[4 * q + h] : v0[4 * q + 2 + h];
+                        const uint32_t s1 = g ? v1[4 * q + h] : v1[4 * q + 2 + h];
+                        own[0][h] = g ? v0[4 * q + 2 + h] : v0[4 * q + h];
+                        own[1][h] = g ? v1[4 * q + 2 + h] : v1[4 * q + h];
+                        oth[0][h] = __shfl_xor_sync(FULL, s0, 1);
+                        oth[1][h] = __shfl_xor_sync(FULL, s1, 1);
+                    }
+                    const int jl = ch * 16 + 2 * q + g;
+                    const int64_t j = (int64_t)J * TC_SNPS + jl;
+                    const bool valid = i < a.S && j < a.S && i < j;
+                    uint32_t mj[2][3] = {{0, 0, 0}, {0, 0, 0}};
+                    if (j < a.S) {
+                        const uint4 m4 = *reinterpret_cast<const uint4 *>(a.marg + j * 8);
+                        mj[0][0] = m4.x & 0xffff; mj[0][1] = m4.x >> 16; mj[0][2] = m4.y & 0xffff;
+                        mj[1][0] = m4.y >> 16;    mj[1][1] = m4.z & 0xffff; mj[1][2] = m4.z >> 16;
+                    }
+                    uint32_t cell[2][9];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const uint32_t n00 = f2u_exact(g ? oth[c][0] : own[c][0]);
+                        const uint32_t n01 = f2u_exact(g ? oth[c][1] : own[c][1]);
+                        const uint32_t n10 = f2u_exact(g ? own[c][0] : oth[c][0]);
+                        const uint32_t n11 = f2u_exact(g ? own[c][1] : oth[c][1]);
+                        const uint32_t n02 = mi[c][0] - n00 - n01;
+                        const uint32_t n12 = mi[c][1] - n10 - n11;
+                        const uint32_t n20 = mj[c][0] - n00 - n10;
+                        const uint32_t n21 = mj[c][1] - n01 - n11;
+                        const uint32_t n22 = mi[c][2] - n20 - n21;
+                        cell[c][0] = n00; cell[c][1] = n01; cell[c][2] = n02;
+                        cell[c][3] = n10; cell[c][4] = n11; cell[c][5] = n12;
+                        cell[c][6] = n20; cell[c][7] = n21; cell[c][8] = n22;
+                    }
+                    float hsum = 0.f;
+                    if (valid) {
+#pragma unroll
+                        for (int x = 0; x < 9; ++x) {
+                            const uint32_t ca = cell[0][x], cb = cell[1][x];
+                            const float ln = logtab[ca + cb];
+                            hsum = fmaf((float)ca, ln - logtab[ca], hsum);
+                            hsum = fmaf((float)cb, ln - logtab[cb], hsum);
+                        }
+                    }
+                    const float score = fmaf(-hsum, a.invN, a.hy);
+                    // Lexicographic rank of (i, j): C(S,2) - C(S-i,2) + (j-i-1).
+                    const uint64_t si = (uint64_t)(a.S - i);
+                    const uint64_t rank = valid ? (a.pair_base - si * (si - 1) / 2 + (uint64_t)(j - i - 1)) : NO_RANK;
+                    sc[q] = score;
+                    rk[q] = rank;
+                    val[q] = valid;
+                    if (MODE == MODE_DUMP && valid) {
+                        if (a.dump_scores) a.dump_scores[i * a.S + j] = score;
+                        if (a.dump_tables) {
+                            uint32_t *o = a.dump_tables + (size_t)(i * a.S + j) * 18;
+#pragma unroll
+                            for (int x = 0; x < 9; ++x) { o[2 * x] = cell[0][x]; o[2 * x + 1] = cell[1][x]; }
+                        }
+                    }
+                }
+                if (MODE == MODE_TOPN) {
+                    // Merge the buffer into the list when a full chunk might not fit.
+                    epi_bar();
+                    if (buf_count > Bcap - 1024) {
+                        const int nb = buf_count;
+                        for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
+                        epi_bitonic_desc(lscore, lrank, a.P2, tid);
+                        if (tid == 0) {
+                            buf_count = 0;
+                            if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr, ordered_int(lscore[L - 1]));
+                        }
+                        epi_bar();
+                    }
+                    thr_s = lscore[L - 1];
+                    thr_r = lrank[L - 1];
+                    const float gthr = from_ordered(*(volatile int *)a.gthr);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const bool cand = val[q] && sc[q] >= gthr && better(sc[q], rk[q], thr_s, thr_r);
+                        const unsigned m = __ballot_sync(FULL, cand);
+                        int base = 0;
+                        if (lane == 0 && m) base = atomicAdd(&buf_count, __popc(m));
+                        base = __shfl_sync(FULL, base, 0);
+                        if (cand) {
+                            const int slot = L + base + __popc(m & ((1u << lane) - 1u));
+                            lscore[slot] = sc[q];
+                            lrank[slot] = rk[q];
+                        }
+                    }
+                }
+            }
+        }
+        if (MODE == MODE_TOPN) {
+            epi_bar();
+            const int nb = buf_count;
+            for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
+            epi_bitonic_desc(lscore, lrank, a.P2, tid);
+            for (int x = tid; x < L; x += 128) {
+                a.list_score[(size_t)blockIdx.x * L + x] = lscore[x];
+                a.list_rank[(size_t)blockIdx.x * L + x] = lrank[x];
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+size_t pairs_smem_bytes(int stages, int M, int P2)
+{
+    return 1024 + (size_t)stages * (TC_A_BYTES + TC_B_BYTES) + (size_t)((M + 1 + 3) & ~3) * 4 +
+           (size_t)P2 * (8 + 4);
+}
+
+cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, uint8_t *E,
+                               cudaStream_t st)
+{
+    const int64_t n = rows * Wt;
+    k_expand_e4m3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S, S_pad, Wt, rows, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint16_t *marg,
+                             cudaStream_t st)
+{
+    k_marginals<<<(unsigned)((S + 127) / 128), 128, 0, st>>>(X, S, S_pad, W0, Wt, marg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_tc(int mode, const CUtensorMap &tmap, const PairsArgs &a, int grid, cudaStream_t st)
+{
+    const size_t bytes = pairs_smem_bytes(a.stages, a.M, a.P2);
+    void *fn = mode == MODE_TOPN ? reinterpret_cast<void *>(&k_pairs_tc<MODE_TOPN>)
+                                 : reinterpret_cast<void *>(&k_pairs_tc<MODE_DUMP>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    CUtensorMap map = tmap;
+    PairsArgs args = a;
+    void *params[] = {&map, &args};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(TC_THREADS), params, bytes, st);
+}
+
+}  // namespace fc

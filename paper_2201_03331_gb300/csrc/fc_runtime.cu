@@ -209,6 +209,9 @@ Dataset::~Dataset()
     cudaFree(logtab);
     cudaFree(err);
     cudaFree(scratch);
+    cudaFree(E);
+    cudaFree(marg);
+    cudaFree(tiles);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
     if (ev_sweep1) cudaEventDestroy(ev_sweep1);
     if (own_stream && own_stream_handle) cudaStreamDestroy(own_stream_handle);
@@ -260,6 +263,163 @@ TuneConfig Dataset::pick_config(int k, int L, int mode)
     return c;
 }
 
+// ---- order-2 tensor-core path --------------------------------------------------
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t rows)
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!fn) {
+            void *p = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                             cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+                return set_error(FC_ECUDA, "cuTensorMapEncodeTiled unavailable");
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        }
+    }
+    const cuuint64_t dims[2] = {inner_bytes, rows};
+    const cuuint64_t strides[1] = {inner_bytes};
+    const cuuint32_t box[2] = {128, 128};
+    const cuuint32_t elem[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, elem,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FC_OK;
+}
+
+int pow2_at_least(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+bool Dataset::pairs_tc_eligible(int L)
+{
+    const char *mode = getenv("FC_PAIRS_PATH");
+    if (mode && strcmp(mode, "popc") == 0) return false;
+    const bool forced = mode && strcmp(mode, "tc") == 0;
+    if (!forced && S < 1024) return false;
+    if (L > 2048) return false;
+    // Each class needs at least one K chunk, or its accumulator is never written.
+    if (W0 == 0 || Wt == W0) return false;
+    const int Bcap = std::max(L, 1024);
+    const int P2 = pow2_at_least(L + Bcap);
+    return pairs_smem_bytes(2, (int)M, P2) <= (size_t)max_smem_optin;
+}
+
+PairsArgs Dataset::pairs_args(int L, float hy, float invN)
+{
+    PairsArgs pa{};
+    pa.tiles = tiles;
+    pa.ntiles = ntiles;
+    pa.S = S;
+    pa.W0 = W0;
+    pa.Wt = Wt;
+    pa.marg = marg;
+    pa.logtab = logtab;
+    pa.M = (int)M;
+    pa.hy = hy;
+    pa.invN = invN;
+    pa.pair_base = binom(S, 2);
+    pa.L = L;
+    pa.Bcap = L > 0 ? std::max(L, 1024) : 0;
+    pa.P2 = L > 0 ? pow2_at_least(L + pa.Bcap) : 0;
+    pa.stages = 2;
+    for (int st = 4; st >= 2; --st) {
+        if (pairs_smem_bytes(st, (int)M, pa.P2) <= (size_t)max_smem_optin) { pa.stages = st; break; }
+    }
+    return pa;
+}
+
+int Dataset::prepare_pairs()
+{
+    if (pairs_ready) return FC_OK;
+    const int64_t S64 = (S + 63) / 64 * 64;
+    const int64_t rows = 2 * S64;
+    const uint64_t kbytes = (uint64_t)Wt * 128;
+    cudaError_t e;
+    if ((e = dev_alloc((void **)&E, (size_t)rows * kbytes)) != cudaSuccess)
+        return cuda_status(e, "e4m3 operand allocation");
+    if ((e = dev_alloc((void **)&marg, sizeof(uint16_t) * 8 * (size_t)S)) != cudaSuccess)
+        return cuda_status(e, "marginal allocation");
+    const int nb = (int)(S64 / 64);
+    std::vector<uint32_t> t;
+    t.reserve((size_t)nb * (nb + 1) / 2);
+    // Groups of 16 row blocks sweep all column blocks: a group's A blocks and
+    // the current B block are shared by the CTAs working at the same time.
+    const int Gr = 16;
+    for (int g0 = 0; g0 < nb; g0 += Gr)
+        for (int J = g0; J < nb; ++J)
+            for (int I = g0; I < std::min(g0 + Gr, nb); ++I)
+                if (I <= J) t.push_back(((uint32_t)I << 16) | (uint32_t)J);
+    ntiles = (int)t.size();
+    if ((e = dev_alloc((void **)&tiles, sizeof(uint32_t) * t.size())) != cudaSuccess)
+        return cuda_status(e, "tile list allocation");
+    cudaMemcpyAsync(tiles, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice, stream);
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, Wt, rows, E, stream)) != cudaSuccess ||
+        (e = launch_marginals(X, S, S_pad, W0, Wt, marg, stream)) != cudaSuccess)
+        return cuda_status(e, "pair operand preparation");
+    note_launches(2);
+    int rc = encode_tmap_u8(&tmap, E, kbytes, (uint64_t)rows);
+    if (rc) return rc;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair operand preparation");
+    pairs_ready = true;
+    return FC_OK;
+}
+
+int Dataset::pairs_dense(float *scores, uint32_t *tables)
+{
+    int rc = prepare_pairs();
+    if (rc) return rc;
+    const double Nd = (double)M;
+    double hy = 0.0;
+    if (M1 > 0) hy -= (M1 / Nd) * std::log(M1 / Nd);
+    if (M0 > 0) hy -= (M0 / Nd) * std::log(M0 / Nd);
+    PairsArgs pa = pairs_args(0, (float)hy, (float)(1.0 / Nd));
+    const size_t ns = scores ? sizeof(float) * (size_t)S * S : 0;
+    const size_t nt = tables ? sizeof(uint32_t) * 18 * (size_t)S * S : 0;
+    Arena ar;
+    ar.take(ns);
+    ar.take(nt);
+    rc = reserve_scratch(ar.off);
+    if (rc) return rc;
+    Arena A2;
+    A2.base = scratch;
+    pa.dump_scores = scores ? (float *)A2.take(ns) : nullptr;
+    pa.dump_tables = tables ? (uint32_t *)A2.take(nt) : nullptr;
+    pa.err = err;
+    cudaError_t e;
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
+    if (ns) cudaMemsetAsync(pa.dump_scores, 0, ns, stream);
+    if (nt) cudaMemsetAsync(pa.dump_tables, 0, nt, stream);
+    const int grid = std::min(sms, ntiles);
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_pairs_tc(MODE_DUMP, tmap, pa, grid, stream)) != cudaSuccess)
+        return cuda_status(e, "tensor-core pairs kernel");
+    note_launches(1);
+    uint32_t herr = 0;
+    cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
+    if (ns) cudaMemcpyAsync(scores, pa.dump_scores, ns, cudaMemcpyDeviceToHost, stream);
+    if (nt) cudaMemcpyAsync(tables, pa.dump_tables, nt, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pairs dump");
+    if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the pairs kernel");
+    return FC_OK;
+}
+
 // ---- search ----------------------------------------------------------------
 
 int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
@@ -278,15 +438,29 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
     const int cells = pow3(k);
 
     for (;;) {
-        TuneConfig cfg = pick_config(k, L, MODE_TOPN);
-        if (cfg.grid <= 0) return set_error(FC_ERANGE, "no launch configuration fits");
+        // Order 2 on large SNP counts: tensor-core contraction; else the
+        // prefix-table AND/POPC sweep.
+        const bool tc = k == 2 && pairs_tc_eligible(L);
+        TuneConfig cfg{};
+        PairsArgs pa{};
+        int grid = 0;
+        if (tc) {
+            int rc = prepare_pairs();
+            if (rc) return rc;
+            pa = pairs_args(L, (float)hy, (float)(1.0 / Nd));
+            grid = std::min(sms, ntiles);
+        } else {
+            cfg = pick_config(k, L, MODE_TOPN);
+            grid = cfg.grid;
+        }
+        if (grid <= 0) return set_error(FC_ERANGE, "no launch configuration fits");
         const int F = std::max(2, 4096 / L);
-        const int nl1 = (cfg.grid + F - 1) / F;
+        const int nl1 = (grid + F - 1) / F;
         // Scratch layout.
         Arena ar;
         auto plan = [&](Arena &A, void **p) {
-            p[0] = A.take(sizeof(float) * (size_t)cfg.grid * L);
-            p[1] = A.take(sizeof(uint64_t) * (size_t)cfg.grid * L);
+            p[0] = A.take(sizeof(float) * (size_t)grid * L);
+            p[1] = A.take(sizeof(uint64_t) * (size_t)grid * L);
             p[2] = A.take(sizeof(float) * (size_t)nl1 * L);
             p[3] = A.take(sizeof(uint64_t) * (size_t)nl1 * L);
             p[4] = A.take(sizeof(float) * (size_t)nl1 * L);
@@ -296,8 +470,9 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             p[8] = A.take(sizeof(uint32_t) * (size_t)L * cells * 2);
             p[9] = A.take(sizeof(uint32_t) * (size_t)N * k);
             p[10] = A.take(sizeof(double) * (size_t)N);
+            p[11] = A.take(sizeof(int) * 4);
         };
-        void *p[11];
+        void *p[12];
         plan(ar, p);
         Arena A2;
         if (ext_scratch) {
@@ -325,14 +500,26 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         sa.list_score = (float *)p[0];
         sa.list_rank = (uint64_t *)p[1];
         if (timing) cudaEventRecord(ev_sweep0, stream);
-        if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_TOPN, sa, stream, nullptr)) != cudaSuccess)
-            return cuda_status(e, "search kernel");
+        if (tc) {
+            pa.list_score = (float *)p[0];
+            pa.list_rank = (uint64_t *)p[1];
+            pa.gthr = (int *)p[11];
+            pa.err = err;
+            // 0x80808080 is below the ordered image of every finite score.
+            cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
+            if ((e = launch_gate()) != cudaSuccess || (e = launch_pairs_tc(MODE_TOPN, tmap, pa, grid, stream)) != cudaSuccess)
+                return cuda_status(e, "tensor-core pairs kernel");
+        } else {
+            if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_TOPN, sa, stream, nullptr)) != cudaSuccess)
+                return cuda_status(e, "search kernel");
+        }
         if (timing) cudaEventRecord(ev_sweep1, stream);
         note_launches(1);
+        last_path_tc = tc;
         // Grid merge.
         const float *src_s = (const float *)p[0];
         const uint64_t *src_r = (const uint64_t *)p[1];
-        int nl = cfg.grid;
+        int nl = grid;
         int pp = 0;
         while (nl > 1) {
             float *ds = (float *)p[2 + 2 * pp];
@@ -367,7 +554,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             }
         }
         last_list = L;
-        last_grid = cfg.grid;
+        last_grid = grid;
+        if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the sweep");
         if (herr & ERR_LIST_SHORT) {
             L *= 4;
             if (L > FC_MAX_LIST)
@@ -455,6 +643,7 @@ int make_handle(fc_handle **out, int *dev)
     if (!h) return set_error(FC_ENOMEM, "host allocation");
     h->ds.device = *dev;
     h->ds.sms = sms;
+    cudaDeviceGetAttribute(&h->ds.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, *dev);
     cudaError_t e = cudaStreamCreateWithFlags(&h->ds.own_stream_handle, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete h;
@@ -674,6 +863,27 @@ int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64
         d.launches = 0;
     }
     return FC_OK;
+}
+
+int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (!scores && !tables) return set_error(FC_EINVAL, "no output requested");
+        if (h->ds.S < 2) return set_error(FC_EINVAL, "fewer than two SNPs");
+        if (scores && h->ds.S > 8192) return set_error(FC_ERANGE, "dense scores need S <= 8192");
+        if (tables && h->ds.S > 1024) return set_error(FC_ERANGE, "dense tables need S <= 1024");
+        if ((size_t)pairs_smem_bytes(2, (int)h->ds.M, 0) > (size_t)h->ds.max_smem_optin)
+            return set_error(FC_ERANGE, "too many samples for the tensor-core path");
+        DeviceGuard g(h->ds.device);
+        return h->ds.pairs_dense(scores, tables);
+    });
+}
+
+int fc_last_search_kind(const fc_handle *h)
+{
+    if (!h) return set_error(FC_EINVAL, "NULL handle");
+    return h->ds.last_path_tc ? 2 : (h->ds.last_list > 0 ? 1 : 0);
 }
 
 int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls)

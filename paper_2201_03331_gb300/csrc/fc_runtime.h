@@ -51,6 +51,18 @@ struct Dataset {
     size_t scratch_cap = 0;
 
     int last_list = 0, last_grid = 0;
+    bool last_path_tc = false;
+    int max_smem_optin = 0;
+
+    // Order-2 tensor-core operands, built on first use: E = 0/1 e4m3 bytes
+    // [2*S64][Wt*128] (rows 2s+g for genotypes g = 0, 1), per-SNP genotype
+    // counts, the block-pair tile list and E's TMA descriptor.
+    uint8_t *E = nullptr;
+    uint16_t *marg = nullptr;
+    uint32_t *tiles = nullptr;
+    int ntiles = 0;
+    CUtensorMap tmap{};
+    bool pairs_ready = false;
 
     // Optional instrumentation (fc_timing): CUDA events around the sweep
     // kernel on the launching stream, and a count of kernel launches.
@@ -70,6 +82,10 @@ struct Dataset {
                void *ext_scratch = nullptr, size_t ext_cap = 0);
     int scores(int k, uint64_t rank_begin, int64_t n, float *out);
     int tables(int k, const uint32_t *combos, int64_t n, uint32_t *out);
+    bool pairs_tc_eligible(int L);
+    PairsArgs pairs_args(int L, float hy, float invN);
+    int prepare_pairs();
+    int pairs_dense(float *scores, uint32_t *tables);
 };
 
 }  // namespace fc

@@ -38,7 +38,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C4"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4"])
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target duration of the CPU-baseline sample")
@@ -141,11 +141,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def traffic_for(kernel_key):
+def traffic_for(kernel_key, source="fc_search.cu"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2201_03331_gb300", "csrc", "fc_search.cu")
+    src = os.path.join(ROOT, "paper_2201_03331_gb300", "csrc", source)
     try:
         rec = json.load(open(path)).get(kernel_key)
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -162,7 +162,9 @@ def cpu_baseline_sample(ds, k, seconds):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    P0 = 16 * cores              # calibration sample: every thread gets prefixes
+    # Calibration sample: every thread gets prefixes (fewer when each prefix
+    # has many extensions).
+    P0 = cores * (16 if k > 2 else 1)
     t0 = time.perf_counter()
     _, _, tested = oracle.search(ds.genotypes, ds.phenotype, k, 10, 0, (0, P0))
     dt = max(time.perf_counter() - t0, 1e-3)
@@ -294,22 +296,41 @@ def run_ours(args):
            "ms_per_step": 1e3 * e2e_s}
 
     props = torch.cuda.get_device_properties(local)
-    sm_max = DEFAULT_SM_MAX_MHZ
+    peaks = {}
     try:
-        sm_max = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", sm_max))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-    popc = algorithmic_popc(ds, k)
+    sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
     sweep_avg_s = (sweep_ms / max(sweeps, 1)) / 1e3
-    achieved = popc / sweep_avg_s / 1e12 if sweeps else None
-    kernel_key = f"k_search<{k},1,TOPN> {args.workload}"
-    roofline = {"bound": "alu", "kernel": kernel_key, "achieved": achieved, "peak": peak,
-                "unit": "Tpopc32/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": traffic_for(kernel_key),
-                "peak_basis": f"{props.multi_processor_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz",
-                "sweep_ms_per_launch": 1e3 * sweep_avg_s,
-                "algorithmic_popc_per_launch": popc}
+    kind = fc.fc_last_search_kind(h)
+    if kind == 2:
+        # Tensor-core contraction: 4 cells ({0,1} x {0,1}) x M samples x 2
+        # FLOP per pair; fp8 peak = measured dense bf16 x 2 (nominal ratio).
+        flops = math.comb(ds.S, 2) * 4 * 2 * (ds.cases + ds.controls)
+        bf16 = peaks.get("bf16_tflops")
+        peak = 2.0 * float(bf16) if bf16 else 2.0 * 1900.0
+        achieved = flops / sweep_avg_s / 1e12 if sweeps else None
+        kernel_key = f"k_pairs_tc<TOPN> {args.workload}"
+        roofline = {"bound": "tensor", "kernel": kernel_key, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                    "traffic": traffic_for(kernel_key, "fc_pairs_tc.cu"),
+                    "peak_basis": ("2 x measured dense bf16 (fp8 e4m3 kind::f8f6f4)" if bf16
+                                   else "2 x fallback 1.9 PFLOP/s bf16"),
+                    "sweep_ms_per_launch": 1e3 * sweep_avg_s,
+                    "algorithmic_flop_per_launch": flops,
+                    "paper_method_popc_per_launch": algorithmic_popc(ds, k)}
+    else:
+        peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+        popc = algorithmic_popc(ds, k)
+        achieved = popc / sweep_avg_s / 1e12 if sweeps else None
+        kernel_key = f"k_search<{k},1,TOPN> {args.workload}"
+        roofline = {"bound": "alu", "kernel": kernel_key, "achieved": achieved, "peak": peak,
+                    "unit": "Tpopc32/s", "frac": (achieved / peak) if achieved else None,
+                    "traffic": traffic_for(kernel_key),
+                    "peak_basis": f"{props.multi_processor_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz",
+                    "sweep_ms_per_launch": 1e3 * sweep_avg_s,
+                    "algorithmic_popc_per_launch": popc}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

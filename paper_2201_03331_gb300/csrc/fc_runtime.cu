@@ -873,6 +873,8 @@ int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables)
         if (h->ds.S < 2) return set_error(FC_EINVAL, "fewer than two SNPs");
         if (scores && h->ds.S > 8192) return set_error(FC_ERANGE, "dense scores need S <= 8192");
         if (tables && h->ds.S > 1024) return set_error(FC_ERANGE, "dense tables need S <= 1024");
+        if (h->ds.W0 == 0 || h->ds.Wt == h->ds.W0)
+            return set_error(FC_EINVAL, "the tensor-core path needs both cases and controls");
         if ((size_t)pairs_smem_bytes(2, (int)h->ds.M, 0) > (size_t)h->ds.max_smem_optin)
             return set_error(FC_ERANGE, "too many samples for the tensor-core path");
         DeviceGuard g(h->ds.device);

@@ -145,6 +145,46 @@ int fc_search_static(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doub
                      int64_t *out_count);
 
 /*
+ * fc_load_batch - pack many data sets, each with R phenotype replicates.
+ *
+ * n_data        : number of data sets (n_data * R <= 2^20 jobs).
+ * genotypes[d]  : host uint8 [S[d]][M[d]] of data set d (as fc_load).
+ * S[d], M[d]    : its SNP and sample counts.
+ * phenotypes[d] : host uint8 [R][M[d]]: R phenotype vectors of data set d
+ *                 (for permutation replicates the caller supplies the
+ *                 permuted vectors; replicate 0 is usually the observed one).
+ * out           : new batch handle (free with fc_free).
+ * Job j = d * R + r is data set d with phenotype replicate r, packed into its
+ * own bit table.  Validation and errors as fc_load, per job.
+ */
+int fc_load_batch(int n_data, const uint8_t *const *genotypes, const int64_t *S, const int64_t *M,
+                  const uint8_t *const *phenotypes, int R, fc_handle **out);
+
+/*
+ * fc_search_batch - fc_search of order k on every job of a batch handle, in
+ * one persistent launch: CTAs pull (job, rank range) work items from a
+ * device queue, per-job lists are merged, rescored in FP64 and ordered on
+ * the device.  The launch sequence is captured once per (k, top_n) as a CUDA
+ * graph and replayed.  Results per job are those fc_search returns for it.
+ *
+ * out_idx   : host uint32 [jobs][top_n][k]
+ * out_score : host double [jobs][top_n]
+ * out_count : host int64 [jobs], min(top_n, C(S_j, k)); unused tail entries
+ *             of a job are left untouched.
+ * k must not exceed the smallest S of the batch.
+ */
+int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
+                    int64_t *out_count);
+
+/* fc_search_job - fc_search on one job of a batch handle, with its own
+ * launches (the per-data-set alternative to fc_search_batch). */
+int fc_search_job(fc_handle *h, int job, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
+                  int64_t *out_count);
+
+/* fc_batch_info - shape of a batch handle (any pointer may be NULL). */
+int fc_batch_info(const fc_handle *h, int *n_data, int *replicates, int *n_jobs);
+
+/*
  * fc_tables - exact contingency tables of n given combinations (Fig. 3).
  *
  * combos : host uint32 [n][k], SNP indices < S in any order; the first

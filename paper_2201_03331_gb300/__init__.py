@@ -24,6 +24,10 @@ from ._binding import (  # noqa: F401
     fc_pairs_dense,
     fc_last_error,
     fc_load,
+    fc_load_batch,
+    fc_batch_info,
+    fc_search_batch,
+    fc_search_job,
     fc_load_device,
     fc_num_combinations,
     fc_rank,

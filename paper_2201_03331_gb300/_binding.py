@@ -43,6 +43,10 @@ _SIGNATURES = {
     "fc_scores": ([P, i32, u64, i64, P], i32),
     "fc_info": ([P, P, P, P, P], i32),
     "fc_pairs_dense": ([P, P, P], i32),
+    "fc_load_batch": ([i32, P, P, P, P, i32, P], i32),
+    "fc_search_batch": ([P, i32, i64, P, P, P], i32),
+    "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
+    "fc_batch_info": ([P, P, P, P], i32),
     "fc_last_search_kind": ([P], i32),
     "fc_timing": ([P, i32, P, P, P], i32),
     "fc_free": ([P], None),
@@ -187,6 +191,58 @@ def fc_pairs_dense(h: Handle, scores: bool = True, tables: bool = False):
     _check(library().fc_pairs_dense(h.ptr, _ptr(sc) if sc is not None else None,
                                     _ptr(tb) if tb is not None else None), "fc_pairs_dense")
     return sc, tb
+
+
+def fc_load_batch(genotypes, phenotypes) -> Handle:
+    """``genotypes``: list of host ``uint8[S_d][M_d]``; ``phenotypes``: list of
+    host ``uint8[R][M_d]`` (same R for every data set).  Job ``d*R + r`` is
+    data set d with phenotype row r."""
+    n = len(genotypes)
+    if n == 0 or len(phenotypes) != n:
+        raise ValueError("one phenotype block per data set")
+    Gs = [np.ascontiguousarray(g, dtype=np.uint8) for g in genotypes]
+    Ps = [np.ascontiguousarray(np.atleast_2d(p), dtype=np.uint8) for p in phenotypes]
+    R = Ps[0].shape[0]
+    for g, p in zip(Gs, Ps):
+        if g.ndim != 2 or p.shape != (R, g.shape[1]):
+            raise ValueError("genotypes [S][M] and phenotypes [R][M] per data set")
+    gptr = (ctypes.c_void_p * n)(*[g.ctypes.data for g in Gs])
+    pptr = (ctypes.c_void_p * n)(*[p.ctypes.data for p in Ps])
+    S = np.array([g.shape[0] for g in Gs], dtype=np.int64)
+    M = np.array([g.shape[1] for g in Gs], dtype=np.int64)
+    out = ctypes.c_void_p()
+    _check(library().fc_load_batch(n, gptr, _ptr(S), _ptr(M), pptr, R, ctypes.byref(out)), "fc_load_batch")
+    h = Handle(out.value)
+    h._n_jobs = n * R
+    return h
+
+
+def fc_batch_info(h: Handle):
+    v = [ctypes.c_int(0) for _ in range(3)]
+    _check(library().fc_batch_info(h.ptr, *[ctypes.byref(x) for x in v]), "fc_batch_info")
+    return tuple(x.value for x in v)
+
+
+def fc_search_batch(h: Handle, k: int, top_n: int):
+    """Returns ``(idx uint32[jobs][top_n][k], score float64[jobs][top_n],
+    count int64[jobs])``."""
+    jobs = fc_batch_info(h)[2]
+    idx = np.zeros((jobs, max(top_n, 1), k), dtype=np.uint32)
+    score = np.zeros((jobs, max(top_n, 1)), dtype=np.float64)
+    cnt = np.zeros(jobs, dtype=np.int64)
+    _check(library().fc_search_batch(h.ptr, k, top_n, _ptr(idx), _ptr(score), _ptr(cnt)), "fc_search_batch")
+    return idx[:, :top_n], score[:, :top_n], cnt
+
+
+def fc_search_job(h: Handle, job: int, k: int, top_n: int):
+    """fc_search on one job of a batch handle: ``(idx, score)``."""
+    idx = np.zeros((max(top_n, 1), k), dtype=np.uint32)
+    score = np.zeros(max(top_n, 1), dtype=np.float64)
+    cnt = ctypes.c_int64(0)
+    _check(library().fc_search_job(h.ptr, job, k, top_n, _ptr(idx), _ptr(score), ctypes.byref(cnt)),
+           "fc_search_job")
+    n = cnt.value
+    return idx[:n], score[:n]
 
 
 def fc_last_search_kind(h: Handle) -> int:

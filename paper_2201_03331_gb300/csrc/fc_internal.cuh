@@ -156,6 +156,57 @@ cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st);
 cudaError_t launch_final_sort(double *res_s, uint64_t *res_r, int L, int N, int k, int64_t S,
                               uint32_t *out_idx, double *out_score, cudaStream_t st);
 
+// ---- batched persistent search (many data sets / phenotype replicates) -----
+
+enum { MODE_BATCH = 3 };
+
+struct JobDesc {
+    const uint4 *X;         // the job's bit table
+    int64_t S, S_pad;
+    int W0, Wt;
+    float hy, invN, eps;    // H(Y), 1/N and the FP32 score error bound
+    int N;                  // min(top_n, C(S, k))
+    uint64_t total;         // C(S, k)
+    int item_first, n_items;
+};
+
+struct BatchItem {
+    uint32_t job, pad;
+    uint64_t r0, r1;        // rank range [r0, r1) of the job
+};
+
+struct BatchArgs {
+    const JobDesc *jobs;
+    const BatchItem *items;
+    int n_items;
+    int *counter;           // work-queue head, zeroed before the launch
+    const float *logtab;    // ln(n), n = 0..M (M = largest sample count)
+    int M;
+    int L;
+    float *item_score;      // [n_items][L]
+    uint64_t *item_rank;
+};
+
+cudaError_t launch_search_batch(int k, const TuneConfig &cfg, const BatchArgs &b, cudaStream_t st);
+cudaError_t prepare_merge_jobs(int n2);
+cudaError_t launch_merge_jobs(const JobDesc *jobs, int n_jobs, const float *item_s, const uint64_t *item_r, int L,
+                              int n2, float *out_s, uint64_t *out_r, cudaStream_t st);
+
+struct RescoreBatchArgs {
+    const JobDesc *jobs;
+    int n_jobs, k, L;
+    const float *cand_s;    // [jobs][L]
+    const uint64_t *cand_r;
+    double *res_s;          // [jobs][L]
+    uint64_t *res_r;
+    uint32_t *res_tab;      // [jobs][L][3^k][2]
+    uint32_t *job_err;      // [jobs]
+};
+cudaError_t launch_rescore_batch(const RescoreBatchArgs &a, cudaStream_t st);
+cudaError_t prepare_final_sort_batch(int L);
+cudaError_t launch_final_sort_batch(const JobDesc *jobs, int n_jobs, double *res_s, uint64_t *res_r, int L,
+                                    int n_out, int k, uint32_t *out_idx, double *out_score, cudaStream_t st);
+
 // ---- order-2 tensor-core path (fc_pairs_tc.cu) -----------------------------
 
 constexpr int TC_MAX_STAGES = 6;

@@ -126,6 +126,81 @@ __global__ void k_final_sort(double *res_s, uint64_t *res_r, int L, int N, int k
     }
 }
 
+// Batched form of k_rescore: warp w rescores candidate w % L of job w / L.
+__global__ void k_rescore_batch(RescoreBatchArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= (int64_t)a.n_jobs * a.L) return;
+    const int job = (int)(w / a.L);
+    const int i = (int)(w % a.L);
+    const JobDesc jd = a.jobs[job];
+    const float *cs = a.cand_s + (size_t)job * a.L;
+    const uint64_t *cr = a.cand_r + (size_t)job * a.L;
+    double *res_s = a.res_s + (size_t)job * a.L;
+    uint64_t *res_r = a.res_r + (size_t)job * a.L;
+    const int cells = pow3(a.k);
+    float thr = -FLT_MAX;
+    if (jd.N > 0 && cr[jd.N - 1] != NO_RANK) thr = cs[jd.N - 1] - 2.0f * jd.eps;
+    if (i == 0 && lane == 0) {
+        if ((uint64_t)a.L < jd.total && cr[a.L - 1] != NO_RANK && cs[a.L - 1] >= thr)
+            atomicOr(a.job_err + job, ERR_LIST_SHORT);
+    }
+    const uint64_t r = cr[i];
+    if (jd.N == 0 || r == NO_RANK || cs[i] < thr) {
+        if (lane == 0) { res_s[i] = -DBL_MAX; res_r[i] = NO_RANK; }
+        return;
+    }
+    uint32_t c[KMAX_TABLES];
+    unrank(jd.S, a.k, r, c);
+    uint32_t *tab = a.res_tab + ((size_t)job * a.L + i) * cells * 2;
+    warp_table(jd.X, jd.S_pad, jd.W0, jd.Wt, a.k, c, tab);
+    if (lane == 0) {
+        res_s[i] = mi_fp64(tab, cells);
+        res_r[i] = r;
+    }
+}
+
+// Batched final order: CTA j sorts job j's rescored candidates and writes its
+// best N_j to out_idx[j][n_out][k] and out_score[j][n_out].
+__global__ void k_final_sort_batch(const JobDesc *jobs, double *res_s_all, uint64_t *res_r_all, int L, int n_out,
+                                   int k, uint32_t *out_idx, double *out_score)
+{
+    extern __shared__ uint4 smem4[];
+    uint64_t *r = reinterpret_cast<uint64_t *>(smem4);
+    double *s = reinterpret_cast<double *>(r + L);
+    const int job = blockIdx.x;
+    const JobDesc jd = jobs[job];
+    const double *res_s = res_s_all + (size_t)job * L;
+    const uint64_t *res_r = res_r_all + (size_t)job * L;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) { s[i] = res_s[i]; r[i] = res_r[i]; }
+    for (int size = 2; size <= L; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < (L >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool desc = (lo & size) == 0;
+                const double s1 = s[lo], s2 = s[hi];
+                const uint64_t r1 = r[lo], r2 = r[hi];
+                const bool sw = desc ? better64(s2, r2, s1, r1) : better64(s1, r1, s2, r2);
+                if (sw) { s[lo] = s2; s[hi] = s1; r[lo] = r2; r[hi] = r1; }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < jd.N; i += blockDim.x) {
+        out_score[(size_t)job * n_out + i] = s[i];
+        uint32_t c[KMAX_TABLES];
+        if (r[i] != NO_RANK) {
+            unrank(jd.S, k, r[i], c);
+        } else {
+            for (int t = 0; t < k; ++t) c[t] = 0xffffffffu;
+        }
+        for (int t = 0; t < k; ++t) out_idx[((size_t)job * n_out + i) * k + t] = c[t];
+    }
+}
+
 __global__ void k_tables(TablesArgs a)
 {
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -151,6 +226,26 @@ cudaError_t launch_final_sort(double *res_s, uint64_t *res_r, int L, int N, int 
     cudaError_t e = cudaFuncSetAttribute(k_final_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     k_final_sort<<<1, 1024, bytes, st>>>(res_s, res_r, L, N, k, S, out_idx, out_score);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rescore_batch(const RescoreBatchArgs &a, cudaStream_t st)
+{
+    const int wpb = 8;
+    const int64_t warps = (int64_t)a.n_jobs * a.L;
+    k_rescore_batch<<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_final_sort_batch(int L)
+{
+    return cudaFuncSetAttribute(k_final_sort_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, L * 16);
+}
+
+cudaError_t launch_final_sort_batch(const JobDesc *jobs, int n_jobs, double *res_s, uint64_t *res_r, int L,
+                                    int n_out, int k, uint32_t *out_idx, double *out_score, cudaStream_t st)
+{
+    k_final_sort_batch<<<n_jobs, 512, (size_t)L * 16, st>>>(jobs, res_s, res_r, L, n_out, k, out_idx, out_score);
     return cudaGetLastError();
 }
 

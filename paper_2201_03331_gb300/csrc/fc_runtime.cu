@@ -245,22 +245,72 @@ TuneConfig Dataset::pick_config(int k, int L, int mode)
     c.G = 1;
     c.WT = std::min(Wt, 64);
     const int nws[3] = {8, 4, 2};
-    for (int i = 0; i < 3; ++i) {
+    bool found = false;
+    for (int i = 0; i < 3 && !found; ++i) {
         c.NW = nws[i];
         size_t smem = 0;
         const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)M, &smem);
         if (nb > 0) {
             c.grid = nb * sms;
-            return c;
+            found = true;
         }
     }
-    // Fall back to narrower tiles.
-    c.NW = 2;
-    c.WT = 16;
-    size_t smem = 0;
-    const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)M, &smem);
-    c.grid = std::max(nb, 1) * sms;
+    if (!found) {
+        // Fall back to narrower tiles.
+        c.NW = 2;
+        c.WT = 16;
+        size_t smem = 0;
+        const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)M, &smem);
+        c.grid = std::max(nb, 1) * sms;
+    }
+    // Large searches of the sweep use the measured best configuration.
+    if (mode == MODE_TOPN) {
+        const char *at = getenv("FC_AUTOTUNE");
+        const bool enabled = !(at && strcmp(at, "0") == 0);
+        if (enabled && (int64_t)binom(S, k) >= ((int64_t)1 << 24)) c = tuned_config(*this, k, L, c);
+    }
     return c;
+}
+
+double Dataset::hy64() const
+{
+    const double Nd = (double)M;
+    double hy = 0.0;
+    if (M1 > 0) hy -= (M1 / Nd) * std::log(M1 / Nd);
+    if (M0 > 0) hy -= (M0 / Nd) * std::log(M0 / Nd);
+    return hy;
+}
+
+int Dataset::time_sweep(int k, const TuneConfig &cfg, int L, uint64_t n, float *ms)
+{
+    Arena ar;
+    ar.take(sizeof(float) * (size_t)cfg.grid * L);
+    ar.take(sizeof(uint64_t) * (size_t)cfg.grid * L);
+    int rc = reserve_scratch(ar.off);
+    if (rc) return rc;
+    Arena A2;
+    A2.base = scratch;
+    SearchArgs sa{};
+    sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
+    sa.logtab = logtab; sa.M = (int)M;
+    sa.hy = (float)hy64(); sa.invN = (float)(1.0 / (double)M);
+    sa.rank_begin = 0; sa.rank_end = n;
+    sa.L = L;
+    sa.list_score = (float *)A2.take(sizeof(float) * (size_t)cfg.grid * L);
+    sa.list_rank = (uint64_t *)A2.take(sizeof(uint64_t) * (size_t)cfg.grid * L);
+    cudaEvent_t e0, e1;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_status(e, "event");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_status(e, "event"); }
+    cudaEventRecord(e0, stream);
+    e = launch_search(k, cfg, MODE_TOPN, sa, stream, nullptr);
+    cudaEventRecord(e1, stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    note_launches(1);
+    return cuda_status(e, "autotune sweep");
 }
 
 // ---- order-2 tensor-core path --------------------------------------------------
@@ -628,11 +678,7 @@ int Dataset::tables(int k, const uint32_t *combos, int64_t n, uint32_t *out)
 
 // ---- C ABI -----------------------------------------------------------------
 
-struct fc_handle {
-    fc::Dataset ds;
-};
-
-namespace {
+namespace fc {
 
 int make_handle(fc_handle **out, int *dev)
 {
@@ -655,17 +701,7 @@ int make_handle(fc_handle **out, int *dev)
     return FC_OK;
 }
 
-template <typename F>
-int guarded(F &&f)
-{
-    try {
-        return f();
-    } catch (...) {
-        return set_error(FC_ENOMEM, "host exception");
-    }
-}
-
-}  // namespace
+}  // namespace fc
 
 extern "C" {
 

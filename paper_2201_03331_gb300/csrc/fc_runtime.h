@@ -3,6 +3,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/fiuncho.h"
@@ -86,6 +88,71 @@ struct Dataset {
     PairsArgs pairs_args(int L, float hy, float invN);
     int prepare_pairs();
     int pairs_dense(float *scores, uint32_t *tables);
+    double hy64() const;
+    // Device time (ms) of one MODE_TOPN sweep over ranks [0, n) with cfg.
+    int time_sweep(int k, const TuneConfig &cfg, int L, uint64_t n, float *ms);
 };
+
+// Sweep configuration chosen by measurement (autotuner), cached per process
+// by (k, words, SNPs, samples, list size); falls back to `fallback`.
+TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback);
+// Candidate sweep configurations that fit on the device for (k, L, M).
+int sweep_candidates(const Dataset &d, int k, int L, int mode, TuneConfig *out, int max_out);
+
+// Many data sets (x phenotype replicates) searched by one persistent launch.
+struct BatchState {
+    int n_data = 0, R = 0;
+    int64_t max_M = 0;
+    const float *logtab = nullptr;   // the ln table of the job with the most samples
+    // Launch plan for (k, top_n), replayed as one CUDA graph.
+    int k = 0;
+    int64_t top_n = -1;
+    int L = 0, n_items = 0, n2 = 0;
+    TuneConfig cfg{};
+    void *mem = nullptr;             // device buffers of the plan
+    JobDesc *d_jobs = nullptr;
+    BatchItem *d_items = nullptr;
+    int *d_counter = nullptr;
+    float *item_s = nullptr, *job_s = nullptr;
+    uint64_t *item_r = nullptr, *job_r = nullptr;
+    double *res_s = nullptr;
+    uint64_t *res_r = nullptr;
+    uint32_t *res_tab = nullptr, *job_err = nullptr, *out_idx = nullptr;
+    double *out_score = nullptr;
+    void *host = nullptr;            // pinned staging of the results
+    uint32_t *h_idx = nullptr, *h_err = nullptr;
+    double *h_score = nullptr;
+    std::vector<JobDesc> jobs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    ~BatchState();
+    void release_plan();
+};
+
+}  // namespace fc
+
+// The opaque C handle: one data set, or a batch of data sets.
+struct fc_handle {
+    fc::Dataset ds;
+    std::vector<std::unique_ptr<fc::Dataset>> jobs;
+    std::unique_ptr<fc::BatchState> batch;
+};
+
+namespace fc {
+
+// New handle on the current device with its own non-blocking stream.
+int make_handle(fc_handle **out, int *dev);
+
+// Runs f(), turning any C++ exception into FC_ENOMEM (nothing crosses the ABI).
+template <typename F>
+int guarded(F &&f)
+{
+    try {
+        return f();
+    } catch (...) {
+        return set_error(FC_ENOMEM, "host exception");
+    }
+}
 
 }  // namespace fc

@@ -1,0 +1,94 @@
+"""Batched persistent search (many data sets x phenotype replicates in one
+graph-captured launch) against the oracle and against per-job launches."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_batch, make_dataset, permuted_phenotypes
+from tests.parity_util import assert_topn_equal
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2201_03331_gb300 as fcm
+    from paper_2201_03331_gb300 import build
+    build.build()
+    return fcm
+
+
+def _small_batch(seed, n, R, snp_range, sample_range, k):
+    return make_batch(n_datasets=n, replicates=R, seed=seed, snp_range=snp_range,
+                      sample_range=sample_range, k=k, top_n=10)
+
+
+@pytest.mark.parametrize("k,snps,samples", [(3, (40, 90), (300, 1200)), (2, (60, 150), (200, 900)),
+                                            (4, (20, 30), (400, 700))])
+def test_batch_matches_oracle_per_job(fc, k, snps, samples):
+    batch = _small_batch(50 + k, 4, 3, snps, samples, k)
+    h = fc.fc_load_batch([ds.genotypes for ds, _ in batch], [ph for _, ph in batch])
+    assert fc.fc_batch_info(h) == (4, 3, 12)
+    idx, score, cnt = fc.fc_search_batch(h, k, 10)
+    for d, (ds, ph) in enumerate(batch):
+        for r in range(3):
+            j = d * 3 + r
+            o_idx, o_s, tested = oracle.search(ds.genotypes, ph[r], k, 10)
+            assert cnt[j] == min(10, math.comb(ds.S, k)) == len(o_s)
+
+            def score_of(c, ds=ds, ph=ph, r=r):
+                return float(oracle.mi(oracle.tables(ds.genotypes, ph[r], k, [c]), k)[0])
+            assert_topn_equal(idx[j, :cnt[j]], score[j, :cnt[j]], o_idx, o_s, score_of)
+
+
+def test_batch_equals_per_job_launches_and_replays(fc):
+    batch = _small_batch(61, 6, 4, (80, 200), (500, 3000), 3)
+    h = fc.fc_load_batch([ds.genotypes for ds, _ in batch], [ph for _, ph in batch])
+    a = fc.fc_search_batch(h, 3, 10)
+    b = fc.fc_search_batch(h, 3, 10)   # graph replay
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    for j in range(24):
+        idx, s = fc.fc_search_job(h, j, 3, 10)
+        assert np.array_equal(idx, a[0][j, :len(s)])
+        np.testing.assert_allclose(s, a[1][j, :len(s)], rtol=1e-12)
+    # A different (k, top_n) re-plans and still agrees.
+    c = fc.fc_search_batch(h, 2, 7)
+    for j in (0, 5, 23):
+        idx, s = fc.fc_search_job(h, j, 2, 7)
+        assert np.array_equal(idx, c[0][j]) and np.allclose(s, c[1][j], rtol=1e-12)
+
+
+def test_batch_uneven_and_tiny_jobs(fc):
+    # One data set with exactly k SNPs (one combination), one where top_n
+    # exceeds the number of combinations, one large.
+    sets = [make_dataset("u0", seed=71, S=3, cases=40, controls=61, k=3, top_n=10),
+            make_dataset("u1", seed=72, S=6, cases=300, controls=200, k=3, top_n=10),
+            make_dataset("u2", seed=73, S=120, cases=900, controls=1300, k=3, top_n=10,
+                         planted=(4, 60, 119))]
+    phs = [permuted_phenotypes(ds.phenotype, 2, seed=80 + i) for i, ds in enumerate(sets)]
+    h = fc.fc_load_batch([ds.genotypes for ds in sets], phs)
+    idx, score, cnt = fc.fc_search_batch(h, 3, 10)
+    assert cnt.tolist() == [1, 1, 10, 10, 10, 10]
+    assert idx[0, 0].tolist() == [0, 1, 2]
+    assert tuple(idx[4, 0]) == (4, 60, 119)     # replicate 0: the planted triple
+    for j, (ds, ph) in enumerate([(s, p[r]) for s, p in zip(sets, phs) for r in range(2)]):
+        o_idx, o_s, _ = oracle.search(ds.genotypes, ph, 3, 10)
+
+        def score_of(c, ds=ds, ph=ph):
+            return float(oracle.mi(oracle.tables(ds.genotypes, ph, 3, [c]), 3)[0])
+        assert_topn_equal(idx[j, :cnt[j]], score[j, :cnt[j]], o_idx, o_s, score_of)
+
+
+def test_batch_rejects_bad_order(fc):
+    sets = [make_dataset("b0", seed=91, S=5, cases=20, controls=20, k=3, top_n=3),
+            make_dataset("b1", seed=92, S=9, cases=20, controls=20, k=3, top_n=3)]
+    h = fc.fc_load_batch([ds.genotypes for ds in sets], [ds.phenotype[None, :] for ds in sets])
+    with pytest.raises(fc.FiunchoError) as e:
+        fc.fc_search_batch(h, 6, 3)    # larger than the smallest S
+    assert e.value.status == fc.FC_EINVAL
+    with pytest.raises(fc.FiunchoError):
+        fc.fc_search(h, 2, 3)          # a batch handle has no single data set

@@ -38,7 +38,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
+    p.add_argument("--c5-datasets", type=int, default=64)
+    p.add_argument("--c5-replicates", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target duration of the CPU-baseline sample")
@@ -74,6 +76,13 @@ def max_over_ranks(dist, value):
 def barrier(dist):
     if dist is not None:
         dist.barrier()
+
+
+def aggregate(dist, world, units_per_rank, steps, local_total_ms):
+    """Whole-job throughput: every rank processed ``units_per_rank`` per step;
+    the job's time is the slowest rank's (max over ranks)."""
+    total_ms = max_over_ranks(dist, local_total_ms)
+    return world * units_per_rank * steps / (total_ms / 1e3), total_ms / steps
 
 
 def workload_title(name):
@@ -270,9 +279,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     sweep_ms, sweeps, launches = fc.fc_timing(h, 0)
-    total_ms = max_over_ranks(dist, sum(step_ms))
-    ms_per_step = total_ms / args.steps
-    value = world * total * args.steps / (total_ms / 1e3)
+    value, ms_per_step = aggregate(dist, world, total, args.steps, sum(step_ms))
 
     # End to end through the public API: pinned host inputs -> fc_load ->
     # fc_search -> host results, every step.
@@ -321,16 +328,25 @@ def run_ours(args):
                     "algorithmic_flop_per_launch": flops,
                     "paper_method_popc_per_launch": algorithmic_popc(ds, k)}
     else:
+        # The sweep is bound by POPC issue (the XU pipe).  The full variant
+        # popcounts 3^k cells per combination (the paper's method); the
+        # inclusion-exclusion variant (kind 3) popcounts the 2^k cells with
+        # genotypes in {0,1} and derives the rest exactly.
+        ie = kind == 3
         peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-        popc = algorithmic_popc(ds, k)
+        paper_popc = algorithmic_popc(ds, k)
+        popc = paper_popc * (2 ** k) // (3 ** k) if ie else paper_popc
         achieved = popc / sweep_avg_s / 1e12 if sweeps else None
-        kernel_key = f"k_search<{k},1,TOPN> {args.workload}"
+        kernel_key = f"k_search<{k},{'IE' if ie else 'full'},TOPN> {args.workload}"
         roofline = {"bound": "alu", "kernel": kernel_key, "achieved": achieved, "peak": peak,
                     "unit": "Tpopc32/s", "frac": (achieved / peak) if achieved else None,
                     "traffic": traffic_for(kernel_key),
                     "peak_basis": f"{props.multi_processor_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz",
                     "sweep_ms_per_launch": 1e3 * sweep_avg_s,
-                    "algorithmic_popc_per_launch": popc}
+                    "algorithmic_popc_per_launch": popc,
+                    "counted_cells_per_combination": (2 ** k) if ie else (3 ** k),
+                    "paper_method_popc_per_launch": paper_popc,
+                    "paper_method_equivalent_tpopc_s": paper_popc / sweep_avg_s / 1e12 if sweeps else None}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -357,10 +373,100 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: order-3 search of every (data set, replicate) job,
+    one graph-captured persistent launch per step, against per-job launches
+    (fc_search_job) on the same resident bit tables."""
+    import numpy as np
+    import torch
+    import paper_2201_03331_gb300 as fc
+    from paper_2201_03331_gb300 import build as fcbuild
+    from synth import make_batch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the CUDA path has no CPU fallback)")
+    fcbuild.build()
+    batch = make_batch(n_datasets=args.c5_datasets, replicates=args.c5_replicates)
+    k, top_n = 3, 10
+    h = fc.fc_load_batch([ds.genotypes for ds, _ in batch], [ph for _, ph in batch])
+    n_jobs = fc.fc_batch_info(h)[2]
+    combos = sum(math.comb(ds.S, k) for ds, _ in batch) * args.c5_replicates
+    samples = sum(math.comb(ds.S, k) * ds.M for ds, _ in batch) * args.c5_replicates
+    stream = torch.cuda.Stream()
+    fc.fc_set_stream(h, stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        ref = fc.fc_search_batch(h, k, top_n)
+    torch.cuda.synchronize()
+    fc.fc_timing(h, 1)
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[i][0].record(stream)
+        out = fc.fc_search_batch(h, k, top_n)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sweep_ms, sweeps, launches = fc.fc_timing(h, 0)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    identical_replay = bool(np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]))
+
+    # Per-job launches of the same search (one warm-up pass, one timed pass).
+    for j in range(n_jobs):
+        fc.fc_search_job(h, j, k, top_n)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    same = True
+    for j in range(n_jobs):
+        idx, s = fc.fc_search_job(h, j, k, top_n)
+        same = same and np.array_equal(idx, out[0][j, :len(s)]) and np.array_equal(s, out[1][j, :len(s)])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    per_job_ms = e0.elapsed_time(e1)
+
+    props = torch.cuda.get_device_properties(0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
+    peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
+    popc = sum(algorithmic_popc(ds, k) for ds, _ in batch) * args.c5_replicates
+    sweep_s = sweep_ms / max(sweeps, 1) / 1e3
+    achieved = popc / sweep_s / 1e12 if sweeps else None
+    line = {
+        "metric": METRIC, "value": combos / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": workload_title("C5") if args.c5_datasets == 64 and args.c5_replicates == 20 else
+                   f"order-3 batched, {args.c5_datasets} data sets x {args.c5_replicates} replicates "
+                   "(S ~ U[200,1500], M ~ U[1000,8000], case fraction ~ U[0.3,0.7]), top 10 each",
+                   "jobs": n_jobs, "combinations": combos, "l2": "flushed between timed steps (256 MiB write)"},
+        "sample_combinations_per_s": samples / (ms / 1e3),
+        "roofline": {"bound": "alu", "kernel": "k_search_batch<3,*>", "achieved": achieved, "peak": peak,
+                     "unit": "Tpopc32/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                     "sweep_ms_per_launch": 1e3 * sweep_s},
+        "batched_vs_per_job": {"batched_ms": ms, "per_job_ms": per_job_ms, "speedup": per_job_ms / ms,
+                               "identical_results": bool(same), "identical_replay": identical_replay},
+        "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    fc.fc_free(h)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "C5":
+        return run_batch(args)
     return run_ours(args)
 
 

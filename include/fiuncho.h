@@ -225,8 +225,19 @@ int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64
 int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables);
 
 /* fc_last_search_kind - which sweep the last fc_search on h ran:
- * 0 none yet, 1 prefix-table AND/POPC sweep, 2 tensor-core order-2 pairs. */
+ * 0 none yet, 1 prefix-table AND/POPC sweep counting all 3^k cells,
+ * 2 tensor-core order-2 pairs, 3 prefix-table sweep counting the 2^k cells
+ * with genotypes in {0,1} and deriving the rest exactly from lower-order
+ * tables (inclusion-exclusion; k = 2, 3). */
 int fc_last_search_kind(const fc_handle *h);
+
+/*
+ * fc_sweep_tables - the exact tables the sweep kernel itself builds for the
+ * combinations of lexicographic ranks [rank_begin, rank_begin + n), in the
+ * layout of fc_tables (out: host uint32 [n][3^k][2]).  A parity hook for the
+ * sweep's counting (either variant, as fc_search would choose it).
+ */
+int fc_sweep_tables(fc_handle *h, int k, uint64_t rank_begin, int64_t n, uint32_t *out);
 
 /* fc_info - sizes of a loaded data set (any pointer may be NULL). */
 int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls);

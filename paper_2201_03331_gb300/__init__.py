@@ -37,6 +37,7 @@ from ._binding import (  # noqa: F401
     fc_set_stream,
     fc_strerror,
     fc_tables,
+    fc_sweep_tables,
     fc_timing,
     fc_unrank,
     library,

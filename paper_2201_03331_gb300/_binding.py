@@ -48,6 +48,7 @@ _SIGNATURES = {
     "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
     "fc_batch_info": ([P, P, P, P], i32),
     "fc_last_search_kind": ([P], i32),
+    "fc_sweep_tables": ([P, i32, u64, i64, P], i32),
     "fc_timing": ([P, i32, P, P, P], i32),
     "fc_free": ([P], None),
     "fc_strerror": ([i32], ctypes.c_char_p),
@@ -245,8 +246,17 @@ def fc_search_job(h: Handle, job: int, k: int, top_n: int):
     return idx[:n], score[:n]
 
 
+def fc_sweep_tables(h: Handle, k: int, rank_begin: int, n: int) -> np.ndarray:
+    """Exact ``uint32[n][3^k][2]`` tables built by the sweep kernel for ranks
+    ``[rank_begin, rank_begin + n)``."""
+    out = np.zeros((n, 3 ** k, 2), dtype=np.uint32)
+    _check(library().fc_sweep_tables(h.ptr, k, rank_begin, n, _ptr(out)), "fc_sweep_tables")
+    return out
+
+
 def fc_last_search_kind(h: Handle) -> int:
-    """0 none, 1 prefix-table AND/POPC sweep, 2 tensor-core order-2 pairs."""
+    """0 none, 1 full 3^k AND/POPC sweep, 2 tensor-core order-2 pairs,
+    3 inclusion-exclusion AND/POPC sweep."""
     r = library().fc_last_search_kind(h.ptr)
     if r < 0:
         _check(r, "fc_last_search_kind")

@@ -15,7 +15,7 @@ namespace fc {
 
 // ---- autotuner ---------------------------------------------------------------
 
-int sweep_candidates(const Dataset &d, int k, int L, int mode, TuneConfig *out, int max_out)
+int sweep_candidates(const Dataset &d, int k, int L, int mode, bool ie, TuneConfig *out, int max_out)
 {
     int n = 0;
     const int Gs[3] = {1, 2, 4};
@@ -30,7 +30,7 @@ int sweep_candidates(const Dataset &d, int k, int L, int mode, TuneConfig *out, 
             for (int wj = 0; wj < wi; ++wj) dup = dup || WTs[wj] == WT;
             if (dup) continue;
             for (int ni = 0; ni < 2; ++ni) {
-                TuneConfig c{G, NWs[ni], WT, 0};
+                TuneConfig c{G, NWs[ni], WT, 0, ie};
                 size_t smem = 0;
                 const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)d.M, &smem);
                 if (nb <= 0) continue;
@@ -50,16 +50,18 @@ std::map<std::tuple<int, int, int64_t, int64_t, int, int>, TuneConfig> g_tune_ca
 // Times every candidate on the first ranks of this data set (a slice large
 // enough that every warp sweeps thousands of combinations) and keeps the
 // fastest.  Results are cached per process.
-TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback)
+TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback, bool cached_only)
 {
-    const auto key = std::make_tuple(k, d.Wt, d.S, d.M, L, d.device);
+    const auto key = std::make_tuple(k * 2 + (fallback.ie ? 1 : 0), d.Wt, d.S, d.M, L, d.device);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) return it->second;
     }
+    if (cached_only) return fallback;
+    if (fallback.ie && d.prepare_ie(k) != FC_OK) return fallback;
     TuneConfig cand[32];
-    const int n = sweep_candidates(d, k, L, MODE_TOPN, cand, 32);
+    const int n = sweep_candidates(d, k, L, MODE_TOPN, fallback.ie, cand, 32);
     const uint64_t total = binom(d.S, k);
     TuneConfig best = fallback;
     float best_ms = 1e30f;
@@ -138,7 +140,9 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
         if (t > binom(h->jobs[rep]->S, k)) rep = j;
     }
     Dataset &R = *h->jobs[rep];
-    TuneConfig cfg = R.pick_config(k, L, MODE_TOPN);
+    // The batched kernel counts all 3^k cells (per-job inclusion-exclusion
+    // tables would multiply the memory by the number of jobs).
+    TuneConfig cfg = R.pick_config(k, L, MODE_TOPN, false, false);
     // The batch kernel holds the ln table of the largest sample count.
     {
         size_t smem = 0;
@@ -272,9 +276,10 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
     auto chk = [&](cudaError_t x) { if (ce == cudaSuccess && x != cudaSuccess) ce = x; };
     chk(cudaMemsetAsync(B.d_counter, 0, sizeof(int), st));
     chk(cudaMemsetAsync(B.job_err, 0, sizeof(uint32_t) * nj, st));
-    chk(cudaEventRecord(B.ev0, st));
+    // External event records become timing nodes of the graph.
+    chk(cudaEventRecordWithFlags(B.ev0, st, cudaEventRecordExternal));
     chk(launch_search_batch(k, cfg, ba, st));
-    chk(cudaEventRecord(B.ev1, st));
+    chk(cudaEventRecordWithFlags(B.ev1, st, cudaEventRecordExternal));
     chk(launch_merge_jobs(B.d_jobs, nj, B.item_s, B.item_r, L, n2, B.job_s, B.job_r, st));
     chk(launch_rescore_batch(rb, st));
     chk(launch_final_sort_batch(B.d_jobs, nj, B.res_s, B.res_r, L, n_out, k, B.out_idx, B.out_score, st));

@@ -117,7 +117,11 @@ struct SearchArgs {
     int L;                  // list capacity
     float *list_score;      // [grid][L]
     uint64_t *list_rank;    // [grid][L]
-    float *dump_score;      // MODE_SCORES: [rank_end - rank_begin]
+    void *dump;             // MODE_SCORES: float [n]; MODE_TABLES: uint32 [n][3^k][2]
+    // Inclusion-exclusion inputs (k <= 3 with cfg.ie).
+    const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
+    const uint4 *PR;        // restricted pair counts [S_pad][S_pad] (k = 3)
+    uint32_t nn;            // cases | controls << 16
 };
 
 struct TuneConfig {
@@ -125,9 +129,13 @@ struct TuneConfig {
     int NW;         // warps per CTA
     int WT;         // 128-bit words per prefix-table tile
     int grid;       // CTAs
+    bool ie;        // inclusion-exclusion counting (k <= 3)
 };
 
-enum SearchMode { MODE_TOPN = 0, MODE_SCORES = 1 };
+enum SearchMode { MODE_TOPN = 0, MODE_SCORES = 1, MODE_TABLES = 4 };
+
+cudaError_t launch_restricted_pairs(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint4 *PR,
+                                    cudaStream_t st);
 
 cudaError_t launch_search(int k, const TuneConfig &cfg, int mode, const SearchArgs &a,
                           cudaStream_t st, size_t *smem_out);
@@ -226,13 +234,14 @@ struct PairsArgs {
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
     int *gthr;              // global score threshold (ordered int)
+    int *tile_counter;      // next tile of the global order, zeroed before launch
     uint32_t *err;
     float *dump_scores;     // MODE_DUMP: [S][S] (i < j)
     uint32_t *dump_tables;  // MODE_DUMP: [S][S][9][2]
 };
 
 size_t pairs_smem_bytes(int stages, int M, int P2);
-cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, uint8_t *E,
+cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch, uint8_t *E,
                                cudaStream_t st);
 cudaError_t launch_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint16_t *marg,
                              cudaStream_t st);

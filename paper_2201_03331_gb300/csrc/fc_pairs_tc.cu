@@ -34,6 +34,7 @@ constexpr int TC_BN = 128;          // tile columns
 constexpr int TC_BK = 128;          // K bytes (samples) per pipeline stage
 constexpr int TC_SNPS = 64;         // SNPs per tile side
 constexpr int TC_THREADS = 192;
+constexpr int TC_SCHED = 4;         // depth of the tile-scheduling ring
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;   // 16 KiB
 constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK;   // 16 KiB
@@ -204,7 +205,7 @@ __device__ void epi_bitonic_desc(float *s, uint64_t *r, int n, int tid)
 
 // E[2s + g][w*128 + b] = 0x38 (e4m3 1.0) if bit b of word w of genotype row
 // g of SNP s is set, else 0; rows of padding SNPs are zero.
-__global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, uint8_t *E)
+__global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch, uint8_t *E)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= rows * Wt) return;
@@ -215,7 +216,7 @@ __global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, 
     uint4 bits = make_uint4(0, 0, 0, 0);
     if (s < S) bits = X[((size_t)w * 3 + g) * S_pad + s];
     const uint32_t b32[4] = {bits.x, bits.y, bits.z, bits.w};
-    uint4 *dst = reinterpret_cast<uint4 *>(E + row * (int64_t)Wt * 128 + (int64_t)w * 128);
+    uint4 *dst = reinterpret_cast<uint4 *>(E + row * pitch + (int64_t)w * 128);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         uint32_t o[4];
@@ -262,6 +263,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
     __shared__ uint64_t bar_full[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_done;
     __shared__ uint32_t tmem_base_slot;
+    __shared__ uint64_t bar_sfull[TC_SCHED], bar_sempty[TC_SCHED];
+    __shared__ int sched_tile[TC_SCHED];
     __shared__ int abort_flag_s;
     __shared__ int buf_count;
     __shared__ int epi_stop;
@@ -289,6 +292,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
             mbar_init(&bar_tempty[b], 4);
         }
         mbar_init(&bar_done, 1);
+        for (int s = 0; s < TC_SCHED; ++s) {
+            mbar_init(&bar_sfull[s], 1);
+            mbar_init(&bar_sempty[s], 5);   // the MMA thread and the four epilogue warps
+        }
         abort_flag_s = 0;
         buf_count = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -319,7 +326,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
         if (lane == 0) {
             uint32_t fill = 0;   // running stage-fill counter
             bool ok = true;
-            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+            for (int it = 0; ok; ++it) {
+                // Take the next tile of the global order and publish it to
+                // the MMA and epilogue warps through the scheduling ring.
+                const int slot = it % TC_SCHED;
+                const uint32_t sn = (uint32_t)(it / TC_SCHED);
+                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err)) break;
+                int t = atomicAdd(a.tile_counter, 1);
+                if (t >= a.ntiles) t = -1;
+                sched_tile[slot] = t;
+                mbar_arrive(&bar_sfull[slot]);
+                if (t < 0) break;
                 const uint32_t tile = a.tiles[t];
                 const int I = (int)(tile >> 16), J = (int)(tile & 0xffff);
                 for (int c = 0; c < 2 && ok; ++c) {
@@ -349,9 +366,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
         if (lane == 0) {
             const uint32_t idesc = idesc_e4m3_f32(TC_BM, TC_BN);
             uint32_t fill = 0;
-            int it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
+            for (int it = 0; ok; ++it) {
+                const int slot = it % TC_SCHED;
+                const uint32_t sn = (uint32_t)(it / TC_SCHED);
+                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
+                const int t = sched_tile[slot];
+                mbar_arrive(&bar_sempty[slot]);
+                if (t < 0) break;
                 const int b = it & 1;
                 const uint32_t u = (uint32_t)(it >> 1);
                 if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err)) break;
@@ -392,17 +414,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
         const int Bcap = a.Bcap;
         float thr_s = -FLT_MAX;
         uint64_t thr_r = NO_RANK;
-        int it = 0;
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++it) {
+        for (int it = 0;; ++it) {
+            const int slot = it % TC_SCHED;
+            const uint32_t sn = (uint32_t)(it / TC_SCHED);
+            const bool ok = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err);
+            const int t = ok ? sched_tile[slot] : -1;
+            if (ok) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_sempty[slot]);
+            }
             const int b = it & 1;
             const uint32_t u = (uint32_t)(it >> 1);
-            mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
+            if (t >= 0) mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
             // One stop decision for all four epilogue warps (they meet at
-            // named barriers, which have no timeout).
+            // named barriers, which have no timeout); t is the same for all.
             epi_bar();
             if (tid == 0) epi_stop = *abort_flag;
             epi_bar();
-            if (epi_stop) break;
+            if (epi_stop || t < 0) break;
             tc_fence_after();
             const uint32_t tile = a.tiles[t];
             const int I = (int)(tile >> 16), J = (int)(tile & 0xffff);
@@ -553,11 +582,11 @@ size_t pairs_smem_bytes(int stages, int M, int P2)
            (size_t)P2 * (8 + 4);
 }
 
-cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, uint8_t *E,
+cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch, uint8_t *E,
                                cudaStream_t st)
 {
     const int64_t n = rows * Wt;
-    k_expand_e4m3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S, S_pad, Wt, rows, E);
+    k_expand_e4m3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S, S_pad, Wt, rows, pitch, E);
     return cudaGetLastError();
 }
 

@@ -212,6 +212,7 @@ Dataset::~Dataset()
     cudaFree(E);
     cudaFree(marg);
     cudaFree(tiles);
+    cudaFree(PR);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
     if (ev_sweep1) cudaEventDestroy(ev_sweep1);
     if (own_stream && own_stream_handle) cudaStreamDestroy(own_stream_handle);
@@ -239,11 +240,53 @@ float score_error_bound(int k, int64_t M)
     return (float)(2.0 * e);
 }
 
-TuneConfig Dataset::pick_config(int k, int L, int mode)
+bool Dataset::ie_eligible(int k) const
+{
+    const char *mode = getenv("FC_SWEEP");
+    if (mode && strcmp(mode, "full") == 0) return false;
+    if (k != 2 && k != 3) return false;
+    // The restricted pair table of order 3 holds S_pad^2 x 16 bytes.
+    if (k == 3 && (double)S_pad * (double)S_pad * 16.0 > 2.0 * 1024 * 1024 * 1024) return false;
+    return true;
+}
+
+int Dataset::prepare_ie(int k)
+{
+    cudaError_t e;
+    if (!marg) {
+        if ((e = dev_alloc((void **)&marg, sizeof(uint16_t) * 8 * (size_t)S)) != cudaSuccess)
+            return cuda_status(e, "marginal allocation");
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_marginals(X, S, S_pad, W0, Wt, marg, stream)) != cudaSuccess)
+            return cuda_status(e, "marginal kernel");
+        note_launches(1);
+    }
+    if (k == 3 && !PR) {
+        if ((e = dev_alloc((void **)&PR, sizeof(uint4) * (size_t)S_pad * S_pad)) != cudaSuccess)
+            return cuda_status(e, "restricted pair table allocation");
+        if ((e = launch_gate()) != cudaSuccess ||
+            (e = launch_restricted_pairs(X, S, S_pad, W0, Wt, PR, stream)) != cudaSuccess)
+            return cuda_status(e, "restricted pair kernel");
+        note_launches(1);
+    }
+    return FC_OK;
+}
+
+void Dataset::fill_search_args(SearchArgs &sa) const
+{
+    sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
+    sa.logtab = logtab; sa.M = (int)M;
+    sa.hy = (float)hy64(); sa.invN = (float)(1.0 / (double)M);
+    sa.marg4 = reinterpret_cast<const uint4 *>(marg);
+    sa.PR = PR;
+    sa.nn = (uint32_t)M1 | ((uint32_t)M0 << 16);
+}
+
+TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allow_ie)
 {
     TuneConfig c{};
     c.G = 1;
     c.WT = std::min(Wt, 64);
+    c.ie = allow_ie && ie_eligible(k) && (!no_alloc || (marg && (k != 3 || PR)));
     const int nws[3] = {8, 4, 2};
     bool found = false;
     for (int i = 0; i < 3 && !found; ++i) {
@@ -267,7 +310,7 @@ TuneConfig Dataset::pick_config(int k, int L, int mode)
     if (mode == MODE_TOPN) {
         const char *at = getenv("FC_AUTOTUNE");
         const bool enabled = !(at && strcmp(at, "0") == 0);
-        if (enabled && (int64_t)binom(S, k) >= ((int64_t)1 << 24)) c = tuned_config(*this, k, L, c);
+        if (enabled && (int64_t)binom(S, k) >= ((int64_t)1 << 24)) c = tuned_config(*this, k, L, c, no_alloc);
     }
     return c;
 }
@@ -290,10 +333,9 @@ int Dataset::time_sweep(int k, const TuneConfig &cfg, int L, uint64_t n, float *
     if (rc) return rc;
     Arena A2;
     A2.base = scratch;
+    if (cfg.ie && (rc = prepare_ie(k)) != FC_OK) return rc;
     SearchArgs sa{};
-    sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
-    sa.logtab = logtab; sa.M = (int)M;
-    sa.hy = (float)hy64(); sa.invN = (float)(1.0 / (double)M);
+    fill_search_args(sa);
     sa.rank_begin = 0; sa.rank_end = n;
     sa.L = L;
     sa.list_score = (float *)A2.take(sizeof(float) * (size_t)cfg.grid * L);
@@ -322,7 +364,7 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                    CUtensorMapFloatOOBfill);
 
-int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t rows)
+int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t pitch, uint64_t rows)
 {
     static EncodeTiledFn fn = nullptr;
     static std::mutex mu;
@@ -339,7 +381,7 @@ int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t 
         }
     }
     const cuuint64_t dims[2] = {inner_bytes, rows};
-    const cuuint64_t strides[1] = {inner_bytes};
+    const cuuint64_t strides[1] = {pitch};
     const cuuint32_t box[2] = {128, 128};
     const cuuint32_t elem[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, elem,
@@ -390,7 +432,7 @@ PairsArgs Dataset::pairs_args(int L, float hy, float invN)
     pa.Bcap = L > 0 ? std::max(L, 1024) : 0;
     pa.P2 = L > 0 ? pow2_at_least(L + pa.Bcap) : 0;
     pa.stages = 2;
-    for (int st = 4; st >= 2; --st) {
+    for (int st = TC_MAX_STAGES; st >= 2; --st) {
         if (pairs_smem_bytes(st, (int)M, pa.P2) <= (size_t)max_smem_optin) { pa.stages = st; break; }
     }
     return pa;
@@ -402,8 +444,11 @@ int Dataset::prepare_pairs()
     const int64_t S64 = (S + 63) / 64 * 64;
     const int64_t rows = 2 * S64;
     const uint64_t kbytes = (uint64_t)Wt * 128;
+    // Rows are padded by 128 bytes so that the 128 rows of a TMA box do not
+    // fall on a power-of-two stride (which concentrates them in few L2 sets).
+    const uint64_t pitch = kbytes + 128;
     cudaError_t e;
-    if ((e = dev_alloc((void **)&E, (size_t)rows * kbytes)) != cudaSuccess)
+    if ((e = dev_alloc((void **)&E, (size_t)rows * pitch)) != cudaSuccess)
         return cuda_status(e, "e4m3 operand allocation");
     if ((e = dev_alloc((void **)&marg, sizeof(uint16_t) * 8 * (size_t)S)) != cudaSuccess)
         return cuda_status(e, "marginal allocation");
@@ -421,11 +466,11 @@ int Dataset::prepare_pairs()
     if ((e = dev_alloc((void **)&tiles, sizeof(uint32_t) * t.size())) != cudaSuccess)
         return cuda_status(e, "tile list allocation");
     cudaMemcpyAsync(tiles, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice, stream);
-    if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, Wt, rows, E, stream)) != cudaSuccess ||
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, Wt, rows, (int64_t)pitch, E, stream)) != cudaSuccess ||
         (e = launch_marginals(X, S, S_pad, W0, Wt, marg, stream)) != cudaSuccess)
         return cuda_status(e, "pair operand preparation");
     note_launches(2);
-    int rc = encode_tmap_u8(&tmap, E, kbytes, (uint64_t)rows);
+    int rc = encode_tmap_u8(&tmap, E, kbytes, pitch, (uint64_t)rows);
     if (rc) return rc;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair operand preparation");
     pairs_ready = true;
@@ -446,15 +491,20 @@ int Dataset::pairs_dense(float *scores, uint32_t *tables)
     Arena ar;
     ar.take(ns);
     ar.take(nt);
+    ar.take(sizeof(int) * 4);
     rc = reserve_scratch(ar.off);
     if (rc) return rc;
     Arena A2;
     A2.base = scratch;
     pa.dump_scores = scores ? (float *)A2.take(ns) : nullptr;
+    if (!scores) A2.take(ns);
     pa.dump_tables = tables ? (uint32_t *)A2.take(nt) : nullptr;
+    if (!tables) A2.take(nt);
+    pa.tile_counter = (int *)A2.take(sizeof(int) * 4);
     pa.err = err;
     cudaError_t e;
     cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
+    cudaMemsetAsync(pa.tile_counter, 0, sizeof(int), stream);
     if (ns) cudaMemsetAsync(pa.dump_scores, 0, ns, stream);
     if (nt) cudaMemsetAsync(pa.dump_tables, 0, nt, stream);
     const int grid = std::min(sms, ntiles);
@@ -487,10 +537,14 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
     if (M0 > 0) hy -= (M0 / Nd) * std::log(M0 / Nd);
     const int cells = pow3(k);
 
+    // With caller-provided scratch nothing may be allocated: operands that
+    // are built on first use (tensor-core operands, inclusion-exclusion
+    // tables, autotuner timings) are used only if they already exist.
+    const bool no_alloc = ext_scratch != nullptr;
     for (;;) {
         // Order 2 on large SNP counts: tensor-core contraction; else the
         // prefix-table AND/POPC sweep.
-        const bool tc = k == 2 && pairs_tc_eligible(L);
+        const bool tc = k == 2 && pairs_tc_eligible(L) && (!no_alloc || pairs_ready);
         TuneConfig cfg{};
         PairsArgs pa{};
         int grid = 0;
@@ -500,7 +554,11 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             pa = pairs_args(L, (float)hy, (float)(1.0 / Nd));
             grid = std::min(sms, ntiles);
         } else {
-            cfg = pick_config(k, L, MODE_TOPN);
+            cfg = pick_config(k, L, MODE_TOPN, no_alloc);
+            if (cfg.ie) {
+                int rc = prepare_ie(k);
+                if (rc) return rc;
+            }
             grid = cfg.grid;
         }
         if (grid <= 0) return set_error(FC_ERANGE, "no launch configuration fits");
@@ -542,9 +600,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         cudaError_t e;
         cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
         SearchArgs sa{};
-        sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
-        sa.logtab = logtab; sa.M = (int)M;
-        sa.hy = (float)hy; sa.invN = (float)(1.0 / Nd);
+        fill_search_args(sa);
         sa.rank_begin = 0; sa.rank_end = (uint64_t)total;
         sa.L = L;
         sa.list_score = (float *)p[0];
@@ -554,9 +610,11 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             pa.list_score = (float *)p[0];
             pa.list_rank = (uint64_t *)p[1];
             pa.gthr = (int *)p[11];
+            pa.tile_counter = (int *)p[11] + 1;
             pa.err = err;
             // 0x80808080 is below the ordered image of every finite score.
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
+            cudaMemsetAsync(pa.tile_counter, 0, sizeof(int), stream);
             if ((e = launch_gate()) != cudaSuccess || (e = launch_pairs_tc(MODE_TOPN, tmap, pa, grid, stream)) != cudaSuccess)
                 return cuda_status(e, "tensor-core pairs kernel");
         } else {
@@ -566,6 +624,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         if (timing) cudaEventRecord(ev_sweep1, stream);
         note_launches(1);
         last_path_tc = tc;
+        last_sweep_ie = !tc && cfg.ie;
         // Grid merge.
         const float *src_s = (const float *)p[0];
         const uint64_t *src_r = (const uint64_t *)p[1];
@@ -618,34 +677,37 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
     }
 }
 
-int Dataset::scores(int k, uint64_t rank_begin, int64_t n, float *out)
+// Runs the sweep over ranks [rank_begin, rank_begin + n) in a dump mode
+// (MODE_SCORES: float per combination; MODE_TABLES: uint32 [3^k][2]) with
+// the same counting variant fc_search would use, and copies the dump out.
+int Dataset::sweep_dump(int k, int mode, uint64_t rank_begin, int64_t n, void *out)
 {
     if (n == 0) return FC_OK;
-    TuneConfig cfg = pick_config(k, 0, MODE_SCORES);
+    TuneConfig cfg = pick_config(k, 0, mode);
+    int rc;
+    if (cfg.ie && (rc = prepare_ie(k)) != FC_OK) return rc;
     const int64_t per_cta = (int64_t)cfg.NW * 32;
     cfg.grid = (int)std::max<int64_t>(1, std::min<int64_t>(cfg.grid, (n + per_cta - 1) / per_cta));
-    Arena ar;
-    ar.take(sizeof(float) * n);
-    int rc = reserve_scratch(ar.off);
-    if (rc) return rc;
-    const double Nd = (double)M;
-    double hy = 0.0;
-    if (M1 > 0) hy -= (M1 / Nd) * std::log(M1 / Nd);
-    if (M0 > 0) hy -= (M0 / Nd) * std::log(M0 / Nd);
+    const size_t bytes = mode == MODE_SCORES ? sizeof(float) * n : sizeof(uint32_t) * 2 * pow3(k) * (size_t)n;
+    if ((rc = reserve_scratch(bytes)) != FC_OK) return rc;
     SearchArgs sa{};
-    sa.X = X; sa.S = S; sa.S_pad = S_pad; sa.W0 = W0; sa.Wt = Wt;
-    sa.logtab = logtab; sa.M = (int)M;
-    sa.hy = (float)hy; sa.invN = (float)(1.0 / Nd);
+    fill_search_args(sa);
     sa.rank_begin = rank_begin; sa.rank_end = rank_begin + (uint64_t)n;
     sa.L = 0;
-    sa.dump_score = (float *)scratch;
+    sa.dump = scratch;
     cudaError_t e;
-    if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_SCORES, sa, stream, nullptr)) != cudaSuccess)
-        return cuda_status(e, "score kernel");
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, mode, sa, stream, nullptr)) != cudaSuccess)
+        return cuda_status(e, "sweep dump kernel");
     note_launches(1);
-    cudaMemcpyAsync(out, scratch, sizeof(float) * n, cudaMemcpyDeviceToHost, stream);
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "scores");
+    last_sweep_ie = cfg.ie;
+    cudaMemcpyAsync(out, scratch, bytes, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "sweep dump");
     return FC_OK;
+}
+
+int Dataset::scores(int k, uint64_t rank_begin, int64_t n, float *out)
+{
+    return sweep_dump(k, MODE_SCORES, rank_begin, n, out);
 }
 
 int Dataset::tables(int k, const uint32_t *combos, int64_t n, uint32_t *out)
@@ -921,7 +983,24 @@ int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables)
 int fc_last_search_kind(const fc_handle *h)
 {
     if (!h) return set_error(FC_EINVAL, "NULL handle");
-    return h->ds.last_path_tc ? 2 : (h->ds.last_list > 0 ? 1 : 0);
+    if (h->ds.last_path_tc) return 2;
+    if (h->ds.last_list == 0) return 0;
+    return h->ds.last_sweep_ie ? 3 : 1;
+}
+
+int fc_sweep_tables(fc_handle *h, int k, uint64_t rank_begin, int64_t n, uint32_t *out)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (k < 1 || k > FC_KMAX_SEARCH || k > h->ds.S) return set_error(FC_EINVAL, "bad order k=%d", k);
+        if (n < 0 || (n > 0 && !out)) return set_error(FC_EINVAL, "bad output");
+        const int64_t total = fc_num_combinations(h->ds.S, k);
+        if (total < 0) return set_error(FC_ERANGE, "C(S, k) too large");
+        if (rank_begin > (uint64_t)total || (uint64_t)n > (uint64_t)total - rank_begin)
+            return set_error(FC_EINVAL, "rank range outside [0, C(S, k))");
+        DeviceGuard g(h->ds.device);
+        return h->ds.sweep_dump(k, MODE_TABLES, rank_begin, n, out);
+    });
 }
 
 int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls)

@@ -77,7 +77,9 @@ struct Dataset {
     ~Dataset();
     int load(const uint8_t *dG, const uint8_t *dph, int64_t S, int64_t M);
     int reserve_scratch(size_t bytes);
-    TuneConfig pick_config(int k, int L, int mode);
+    // no_alloc: choose only among variants whose operands already exist and
+    // run no autotuning (which needs scratch).
+    TuneConfig pick_config(int k, int L, int mode, bool no_alloc = false, bool allow_ie = true);
     // ext_scratch: if non-null, a device work area of ext_cap bytes used instead
     // of the handle's own (grown-on-demand) scratch allocation.
     int search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
@@ -89,15 +91,23 @@ struct Dataset {
     int prepare_pairs();
     int pairs_dense(float *scores, uint32_t *tables);
     double hy64() const;
+    // Inclusion-exclusion sweep (k = 2, 3): per-SNP genotype counts and, for
+    // k = 3, the restricted pair table, built on first use.
+    uint4 *PR = nullptr;
+    bool last_sweep_ie = false;
+    bool ie_eligible(int k) const;
+    int prepare_ie(int k);
+    void fill_search_args(SearchArgs &sa) const;
+    int sweep_dump(int k, int mode, uint64_t rank_begin, int64_t n, void *out);
     // Device time (ms) of one MODE_TOPN sweep over ranks [0, n) with cfg.
     int time_sweep(int k, const TuneConfig &cfg, int L, uint64_t n, float *ms);
 };
 
 // Sweep configuration chosen by measurement (autotuner), cached per process
 // by (k, words, SNPs, samples, list size); falls back to `fallback`.
-TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback);
+TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback, bool cached_only = false);
 // Candidate sweep configurations that fit on the device for (k, L, M).
-int sweep_candidates(const Dataset &d, int k, int L, int mode, TuneConfig *out, int max_out);
+int sweep_candidates(const Dataset &d, int k, int L, int mode, bool ie, TuneConfig *out, int max_out);
 
 // Many data sets (x phenotype replicates) searched by one persistent launch.
 struct BatchState {

@@ -7,9 +7,20 @@
 // Paper correspondence (Algorithm 1 and Section "Computing the contingency
 // tables"): the warp's (k-1)-prefix genotype table is built once with
 // `combine` (AND of the prefix SNPs' rows) and reused for every extension
-// SNP j; `combine_and_popcount` is the AND of each prefix row with j's three
-// rows followed by a population count; `mutual_information` scores the
-// 3^k x 2 table; `sorted_insert` becomes the warp list below.
+// SNP j; `combine_and_popcount` is the AND of each prefix row with j's rows
+// followed by a population count; `mutual_information` scores the 3^k x 2
+// table; `sorted_insert` becomes the warp list below.
+//
+// Two counting variants produce the same exact table:
+//  * full: all 3^k cells are popcounted (the paper's method);
+//  * inclusion-exclusion (IE, k = 2, 3): only the 2^k cells whose genotypes
+//    are all in {0, 1} are popcounted.  Because the three genotype rows of a
+//    SNP partition the samples, a cell with genotype 2 at SNP t equals the
+//    table of the other SNPs minus the cells with genotype 0 and 1 at t.
+//    The lower-order tables come from per-SNP genotype counts and a table
+//    of restricted pair counts computed once per data set.  The arithmetic
+//    is exact integer subtraction; every intermediate is a count, so the
+//    packed (cases | controls << 16) words never borrow across fields.
 #include <cfloat>
 #include "fc_internal.cuh"
 
@@ -44,15 +55,64 @@ __device__ void block_bitonic_desc(float *s, uint64_t *r, int n)
     __syncthreads();
 }
 
+__host__ __device__ constexpr int prefix_rows(int k, bool ie) { return ie ? (1 << (k - 1)) : pow3(k - 1); }
+
 // Shared-memory layout of the sweep kernels (uint4 units):
 //   [logtab: ceil((M+1)/4)] [prefix tables: NW * P * WT]
 //   [list ranks: NW * L (uint64)] [list scores: NW * L (float)]
-__host__ __device__ inline size_t search_smem_bytes(int k, int NW, int WT, int L, int M)
+__host__ __device__ inline size_t search_smem_bytes(int k, bool ie, int NW, int WT, int L, int M)
 {
     const size_t lt = (size_t)((M + 1 + 3) / 4) * 16;
-    const size_t pt = (size_t)NW * pow3(k - 1) * WT * 16;
+    const size_t pt = (size_t)NW * prefix_rows(k, ie) * WT * 16;
     const size_t ls = (size_t)NW * L * (8 + 4);
     return lt + pt + ls;
+}
+
+// Per-SNP genotype counts, packed per genotype as cases | controls << 16.
+// m = marg row of the SNP: x = c0g0|c0g1<<16, y = c0g2|c1g0<<16, z = c1g1|c1g2<<16.
+__device__ __forceinline__ void unpack_marg(const uint4 m, uint32_t t[3])
+{
+    t[0] = (m.x & 0xffffu) | (m.y & 0xffff0000u);
+    t[1] = (m.x >> 16) | (m.z << 16);
+    t[2] = (m.y & 0xffffu) | (m.z & 0xffff0000u);
+}
+
+// Full 3x3 table T[3a + b] of a SNP pair from its restricted cells
+// R[2a + b] (a, b in {0,1}) and the per-SNP tables Ta, Tb.
+__device__ __forceinline__ void full2(const uint32_t R[4], const uint32_t Ta[3], const uint32_t Tb[3],
+                                      uint32_t T[9])
+{
+    T[0] = R[0]; T[1] = R[1]; T[3] = R[2]; T[4] = R[3];
+    T[2] = Ta[0] - R[0] - R[1];
+    T[5] = Ta[1] - R[2] - R[3];
+    T[6] = Tb[0] - R[0] - R[2];
+    T[7] = Tb[1] - R[1] - R[3];
+    T[8] = Ta[2] - T[6] - T[7];
+}
+
+// Full 3x3x3 table T[9a + 3b + c] from the restricted cells Rr[4a + 2b + c]
+// and the three full pair tables over positions (a,b), (a,c), (b,c).
+__device__ __forceinline__ void full3(const uint32_t Rr[8], const uint32_t T01[9], const uint32_t T02[9],
+                                      const uint32_t T12[9], uint32_t T[27])
+{
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) T[9 * a + 3 * b + c] = Rr[4 * a + 2 * b + c];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) T[18 + 3 * b + c] = T12[3 * b + c] - T[3 * b + c] - T[9 + 3 * b + c];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) T[9 * a + 6 + c] = T02[3 * a + c] - T[9 * a + c] - T[9 * a + 3 + c];
+        T[24 + c] = T12[6 + c] - T[6 + c] - T[15 + c];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) T[9 * a + 3 * b + 2] = T01[3 * a + b] - T[9 * a + 3 * b] - T[9 * a + 3 * b + 1];
 }
 
 // One data set as the sweep sees it.
@@ -61,6 +121,9 @@ struct SweepJob {
     int64_t S, S_pad;
     int W0, Wt;
     float hy, invN;
+    const uint4 *marg4;     // IE: per-SNP genotype counts, one uint4 per SNP
+    const uint4 *PR;        // IE, k = 3: restricted pair table [S_pad][S_pad]
+    uint32_t nn;            // IE: cases | controls << 16
 };
 
 // Warp-uniform state of a warp's top-L list (sorted_insert, warp form).
@@ -119,14 +182,16 @@ __device__ __forceinline__ void warp_offer(bool cand, float score, uint64_t rank
 }
 
 // The warp-level sweep over combination ranks [r, r_end) of one data set.
-template <int K, int G, int MODE>
+template <int K, bool IE, int G, int MODE>
 __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end, uint4 *ptab, const int WT,
                            const float *logtab, float *lsc, uint64_t *lrk, const int L, WarpList &st,
-                           float *dump, const uint64_t dump_base)
+                           void *dump, const uint64_t dump_base)
 {
-    constexpr int P = pow3(K - 1);
-    constexpr int C = pow3(K);
-    constexpr int CPW = 32 / G;             // combinations per warp chunk
+    constexpr int P = prefix_rows(K, IE);  // prefix-table rows
+    constexpr int GJ = IE ? 2 : 3;         // extension-SNP rows used
+    constexpr int CNT = P * GJ;            // popcounted cells
+    constexpr int C = pow3(K);             // cells of the full table
+    constexpr int CPW = 32 / G;            // combinations per warp chunk
     const int lane = threadIdx.x & 31;
     const int slot = lane / G;
     const int q = lane % G;
@@ -138,6 +203,10 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
     for (int t = 0; t < K - 1; ++t) cur[t] = 0xffffffffu;
     int cur_tile = -1;
     const int64_t Sp = jb.S_pad;
+    // IE prefix-level tables (warp-uniform): T0, T1 per-SNP, T01 full pair.
+    uint32_t T0[3] = {0, 0, 0}, T1[3] = {0, 0, 0}, T01[9];
+#pragma unroll
+    for (int x = 0; x < 9; ++x) T01[x] = 0;
 
     while (r < r_end) {
         const uint32_t j0 = cmb[K - 1];
@@ -148,23 +217,32 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
 
         bool same = true;
         for (int t = 0; t < K - 1; ++t) same = same && (cur[t] == cmb[t]);
+        if (IE && !same) {
+            if (K >= 2) unpack_marg(jb.marg4[cmb[0]], T0);
+            if (K == 3) {
+                unpack_marg(jb.marg4[cmb[1]], T1);
+                const uint4 pr = jb.PR[(size_t)cmb[0] * Sp + cmb[1]];
+                const uint32_t R01[4] = {pr.x, pr.y, pr.z, pr.w};
+                full2(R01, T0, T1, T01);
+            }
+        }
 
-        uint32_t acc[C];
+        uint32_t acc[CNT];
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = 0;
+        for (int c = 0; c < CNT; ++c) acc[c] = 0;
 
         for (int t0 = 0; t0 < jb.Wt; t0 += WT) {
             const int tw = min(WT, jb.Wt - t0);
             if (!(same && cur_tile == t0)) {
                 // combine: prefix rows for words [t0, t0 + tw), first SNP most
-                // significant digit.
+                // significant digit (base 3, or base 2 for IE).
                 __syncwarp();
                 for (int w = lane; w < tw; w += 32) {
                     uint4 rows[K > 1 ? K - 1 : 1][3];
 #pragma unroll
                     for (int t = 0; t < K - 1; ++t)
 #pragma unroll
-                        for (int g = 0; g < 3; ++g)
+                        for (int g = 0; g < GJ; ++g)
                             rows[t][g] = jb.X[((size_t)(t0 + w) * 3 + g) * Sp + cmb[t]];
 #pragma unroll
                     for (int pa = 0; pa < P; ++pa) {
@@ -172,8 +250,8 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
                         int rem = pa;
 #pragma unroll
                         for (int t = K - 2; t >= 0; --t) {
-                            const int g = rem % 3;
-                            rem /= 3;
+                            const int g = rem % GJ;
+                            rem /= GJ;
                             v.x &= rows[t][g].x; v.y &= rows[t][g].y;
                             v.z &= rows[t][g].z; v.w &= rows[t][g].w;
                         }
@@ -190,16 +268,15 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
             for (int w = q; w < tw; w += G) {
                 const int wg = t0 + w;
                 const uint4 *xp = jb.X + (size_t)wg * 3 * Sp + j;
-                const uint4 x0 = xp[0];
-                const uint4 x1 = xp[Sp];
-                const uint4 x2 = xp[2 * Sp];
+                uint4 xg[GJ];
+#pragma unroll
+                for (int g = 0; g < GJ; ++g) xg[g] = xp[g * Sp];
                 const int sh = wg < jb.W0 ? 0 : 16;   // cases low, controls high
 #pragma unroll
                 for (int pa = 0; pa < P; ++pa) {
                     const uint4 pv = ptab[pa * WT + w];
-                    acc[3 * pa + 0] += popc_and4(pv, x0) << sh;
-                    acc[3 * pa + 1] += popc_and4(pv, x1) << sh;
-                    acc[3 * pa + 2] += popc_and4(pv, x2) << sh;
+#pragma unroll
+                    for (int g = 0; g < GJ; ++g) acc[GJ * pa + g] += popc_and4(pv, xg[g]) << sh;
                 }
             }
         }
@@ -207,7 +284,31 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1)
 #pragma unroll
-                for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(FULL, acc[c], off);
+                for (int c = 0; c < CNT; ++c) acc[c] += __shfl_xor_sync(FULL, acc[c], off);
+        }
+
+        // The full 3^k table, packed cases | controls << 16, standard cell order.
+        uint32_t T[C];
+        if constexpr (IE) {
+            uint32_t Tj[3];
+            unpack_marg(jb.marg4[j], Tj);
+            if constexpr (K == 1) {
+                T[0] = Tj[0]; T[1] = Tj[1]; T[2] = Tj[2];
+            } else if constexpr (K == 2) {
+                full2(acc, T0, Tj, T);
+            } else {
+                const uint4 p0 = jb.PR[(size_t)cmb[0] * Sp + j];
+                const uint4 p1 = jb.PR[(size_t)cmb[1] * Sp + j];
+                const uint32_t R02[4] = {p0.x, p0.y, p0.z, p0.w};
+                const uint32_t R12[4] = {p1.x, p1.y, p1.z, p1.w};
+                uint32_t T02[9], T12[9];
+                full2(R02, T0, Tj, T02);
+                full2(R12, T1, Tj, T12);
+                full3(acc, T01, T02, T12, T);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) T[c] = acc[c];
         }
 
         // mutual_information in FP32: MI = H(Y) - H(Y|X),
@@ -215,8 +316,8 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
         float hsum = 0.f;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const uint32_t ca = acc[c] & 0xffffu;
-            const uint32_t cb = acc[c] >> 16;
+            const uint32_t ca = T[c] & 0xffffu;
+            const uint32_t cb = T[c] >> 16;
             const float ln = logtab[ca + cb];
             hsum = fmaf((float)ca, ln - logtab[ca], hsum);
             hsum = fmaf((float)cb, ln - logtab[cb], hsum);
@@ -225,7 +326,13 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
         const uint64_t rank = r + (uint64_t)slot;
 
         if (MODE == MODE_SCORES) {
-            if (valid && q == 0) dump[rank - dump_base] = score;
+            if (valid && q == 0) static_cast<float *>(dump)[rank - dump_base] = score;
+        } else if (MODE == MODE_TABLES) {
+            if (valid && q == 0) {
+                uint32_t *o = static_cast<uint32_t *>(dump) + (rank - dump_base) * (uint64_t)(2 * C);
+#pragma unroll
+                for (int c = 0; c < C; ++c) { o[2 * c] = T[c] & 0xffffu; o[2 * c + 1] = T[c] >> 16; }
+            }
         } else {
             warp_offer(valid && q == 0, score, rank, lsc, lrk, L, st, lane);
         }
@@ -242,14 +349,13 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
     }
 }
 
-template <int K, int G, int MODE>
+template <int K, bool IE, int G, int MODE>
 __global__ void __launch_bounds__(256) k_search(SearchArgs a, int NW, int WT)
 {
-    constexpr int P = pow3(K - 1);
+    constexpr int P = prefix_rows(K, IE);
     extern __shared__ uint4 smem4[];
-    const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int L = a.L;
+    const int L = MODE == MODE_TOPN ? a.L : 0;
 
     float *logtab = reinterpret_cast<float *>(smem4);
     uint4 *ptab_all = smem4 + (a.M + 1 + 3) / 4;
@@ -273,12 +379,11 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a, int NW, int WT)
     const uint64_t r = a.rank_begin + (uint64_t)(((unsigned __int128)R * gw) / total_warps);
     const uint64_t r_end = a.rank_begin + (uint64_t)(((unsigned __int128)R * (gw + 1)) / total_warps);
 
-    SweepJob jb{a.X, a.S, a.S_pad, a.W0, a.Wt, a.hy, a.invN};
+    SweepJob jb{a.X, a.S, a.S_pad, a.W0, a.Wt, a.hy, a.invN, a.marg4, a.PR, a.nn};
     WarpList st;
     st.reset();
-    warp_sweep<K, G, MODE>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
-                           lrank_all + (size_t)warp * L, L, st, a.dump_score, a.rank_begin);
-    (void)lane;
+    warp_sweep<K, IE, G, MODE>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
+                               lrank_all + (size_t)warp * L, L, st, a.dump, a.rank_begin);
 
     if (MODE == MODE_TOPN) {
         // Block-level merge of the warp lists: sort all NW*L entries and keep L.
@@ -297,7 +402,7 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a, int NW, int WT)
 template <int K, int G>
 __global__ void __launch_bounds__(256) k_search_batch(BatchArgs b, int NW, int WT)
 {
-    constexpr int P = pow3(K - 1);
+    constexpr int P = prefix_rows(K, false);
     extern __shared__ uint4 smem4[];
     __shared__ int s_item;
     const int warp = threadIdx.x >> 5;
@@ -322,14 +427,14 @@ __global__ void __launch_bounds__(256) k_search_batch(BatchArgs b, int NW, int W
         if (item >= b.n_items) break;
         const BatchItem it = b.items[item];
         const JobDesc jd = b.jobs[it.job];
-        const SweepJob jb{jd.X, jd.S, jd.S_pad, jd.W0, jd.Wt, jd.hy, jd.invN};
+        const SweepJob jb{jd.X, jd.S, jd.S_pad, jd.W0, jd.Wt, jd.hy, jd.invN, nullptr, nullptr, 0u};
         const uint64_t R = it.r1 - it.r0;
         const uint64_t r = it.r0 + (uint64_t)(((unsigned __int128)R * warp) / NW);
         const uint64_t r_end = it.r0 + (uint64_t)(((unsigned __int128)R * (warp + 1)) / NW);
         WarpList st;
         st.reset();
-        warp_sweep<K, G, MODE_TOPN>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
-                                    lrank_all + (size_t)warp * L, L, st, nullptr, 0);
+        warp_sweep<K, false, G, MODE_TOPN>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
+                                           lrank_all + (size_t)warp * L, L, st, nullptr, 0);
         block_bitonic_desc(lscore_all, lrank_all, NW * L);
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
             b.item_score[(size_t)item * L + i] = lscore_all[i];
@@ -337,6 +442,28 @@ __global__ void __launch_bounds__(256) k_search_batch(BatchArgs b, int NW, int W
         }
         __syncthreads();
     }
+}
+
+// Restricted pair counts for inclusion-exclusion: PR[i][j] (i < j) holds the
+// four cells with genotypes in {0,1} of SNPs i and j, packed cases |
+// controls << 16, in the order (0,0), (0,1), (1,0), (1,1).
+__global__ void k_restricted_pairs(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint4 *PR)
+{
+    const int64_t i = blockIdx.y;
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S || j >= S || j <= i) return;
+    uint32_t acc[4] = {0, 0, 0, 0};
+    for (int w = 0; w < Wt; ++w) {
+        const int sh = w < W0 ? 0 : 16;
+        const uint4 *base = X + (size_t)w * 3 * S_pad;
+        const uint4 a0 = base[i], a1 = base[S_pad + i];
+        const uint4 b0 = base[j], b1 = base[S_pad + j];
+        acc[0] += popc_and4(a0, b0) << sh;
+        acc[1] += popc_and4(a0, b1) << sh;
+        acc[2] += popc_and4(a1, b0) << sh;
+        acc[3] += popc_and4(a1, b1) << sh;
+    }
+    PR[(size_t)i * S_pad + j] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
 }
 
 // Grid-level merge: each CTA sorts F lists of L entries and keeps the best L.
@@ -390,20 +517,21 @@ __global__ void k_merge_jobs(const JobDesc *jobs, const float *item_s, const uin
     }
 }
 
-template <int K, int G, int MODE>
-void *search_kernel_ptr()
+template <int K, bool IE, int G>
+void *search_kernel_ptr(int mode)
 {
-    return reinterpret_cast<void *>(&k_search<K, G, MODE>);
+    if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search<K, IE, G, MODE_TOPN>);
+    if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search<K, IE, G, MODE_SCORES>);
+    if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search<K, IE, G, MODE_TABLES>);
+    if (!IE && mode == MODE_BATCH) return reinterpret_cast<void *>(&k_search_batch<K, G>);
+    return nullptr;
 }
 
-void *pick_kernel(int k, int G, int mode)
+void *pick_kernel(int k, bool ie, int G, int mode)
 {
-#define FC_PICK(KK, GG)                                                            \
-    if (k == KK && G == GG) {                                                      \
-        if (mode == MODE_TOPN) return search_kernel_ptr<KK, GG, MODE_TOPN>();      \
-        if (mode == MODE_SCORES) return search_kernel_ptr<KK, GG, MODE_SCORES>();  \
-        return reinterpret_cast<void *>(&k_search_batch<KK, GG>);                  \
-    }
+#define FC_PICK(KK, GG)                                                                      \
+    if (k == KK && G == GG) return ie ? search_kernel_ptr<KK, (KK <= 3), GG>(mode)           \
+                                      : search_kernel_ptr<KK, false, GG>(mode);
     FC_PICK(1, 1) FC_PICK(1, 2) FC_PICK(1, 4)
     FC_PICK(2, 1) FC_PICK(2, 2) FC_PICK(2, 4)
     FC_PICK(3, 1) FC_PICK(3, 2) FC_PICK(3, 4)
@@ -416,9 +544,10 @@ void *pick_kernel(int k, int G, int mode)
 
 int search_max_blocks_per_sm(int k, const TuneConfig &cfg, int mode, int L, int M, size_t *smem)
 {
-    void *fn = pick_kernel(k, cfg.G, mode);
+    const bool ie = cfg.ie && k <= 3;
+    void *fn = pick_kernel(k, ie, cfg.G, mode);
     if (!fn) return 0;
-    const size_t bytes = search_smem_bytes(k, cfg.NW, cfg.WT, mode == MODE_SCORES ? 0 : L, M);
+    const size_t bytes = search_smem_bytes(k, ie, cfg.NW, cfg.WT, (mode == MODE_TOPN || mode == MODE_BATCH) ? L : 0, M);
     if (smem) *smem = bytes;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return 0;
@@ -430,9 +559,10 @@ int search_max_blocks_per_sm(int k, const TuneConfig &cfg, int mode, int L, int 
 cudaError_t launch_search(int k, const TuneConfig &cfg, int mode, const SearchArgs &a,
                           cudaStream_t st, size_t *smem_out)
 {
-    void *fn = pick_kernel(k, cfg.G, mode);
+    const bool ie = cfg.ie && k <= 3;
+    void *fn = pick_kernel(k, ie, cfg.G, mode);
     if (!fn) return cudaErrorInvalidValue;
-    const size_t bytes = search_smem_bytes(k, cfg.NW, cfg.WT, mode == MODE_TOPN ? a.L : 0, a.M);
+    const size_t bytes = search_smem_bytes(k, ie, cfg.NW, cfg.WT, mode == MODE_TOPN ? a.L : 0, a.M);
     if (smem_out) *smem_out = bytes;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -446,13 +576,21 @@ cudaError_t launch_search_batch(int k, const TuneConfig &cfg, const BatchArgs &b
 {
     // The shared-memory attribute was set by search_max_blocks_per_sm with
     // MODE_BATCH and the same (cfg, L, M) before any stream capture.
-    void *fn = pick_kernel(k, cfg.G, MODE_BATCH);
+    void *fn = pick_kernel(k, false, cfg.G, MODE_BATCH);
     if (!fn) return cudaErrorInvalidValue;
-    const size_t bytes = search_smem_bytes(k, cfg.NW, cfg.WT, b.L, b.M);
+    const size_t bytes = search_smem_bytes(k, false, cfg.NW, cfg.WT, b.L, b.M);
     BatchArgs args = b;
     int NW = cfg.NW, WT = cfg.WT;
     void *params[] = {&args, &NW, &WT};
     return cudaLaunchKernel(fn, dim3(cfg.grid), dim3(cfg.NW * 32), params, bytes, st);
+}
+
+cudaError_t launch_restricted_pairs(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint4 *PR,
+                                    cudaStream_t st)
+{
+    dim3 grid((unsigned)((S + 255) / 256), (unsigned)S);
+    k_restricted_pairs<<<grid, 256, 0, st>>>(X, S, S_pad, W0, Wt, PR);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_merge(const float *in_s, const uint64_t *in_r, int nlists, int L,

@@ -86,7 +86,7 @@ def test_tc_and_popc_paths_agree(fc, path):
     assert fc.fc_last_search_kind(h) == 2
     path("popc")
     b = fc.fc_search(h, 2, 300)
-    assert fc.fc_last_search_kind(h) == 1
+    assert fc.fc_last_search_kind(h) in (1, 3)   # a prefix-table sweep
     assert np.array_equal(a[0], b[0])
     np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
 

@@ -1,0 +1,91 @@
+"""The sweep's two counting variants (all 3^k cells, or the 2^k cells with
+genotypes in {0,1} plus exact inclusion-exclusion) against the oracle."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_config, make_dataset
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2201_03331_gb300 as fcm
+    from paper_2201_03331_gb300 import build
+    build.build()
+    return fcm
+
+
+@pytest.fixture(params=["full", "ie"])
+def variant(request, monkeypatch):
+    if request.param == "full":
+        monkeypatch.setenv("FC_SWEEP", "full")
+    else:
+        monkeypatch.delenv("FC_SWEEP", raising=False)
+    return request.param
+
+
+@pytest.mark.parametrize("k,S,cases,controls", [(1, 40, 333, 170), (2, 45, 700, 650), (3, 26, 900, 1311),
+                                                (4, 15, 400, 389), (3, 33, 1, 200)])
+def test_sweep_tables_exact(fc, variant, k, S, cases, controls):
+    ds = make_dataset("sw", seed=500 + k + S, S=S, cases=cases, controls=controls, k=k, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    total = math.comb(S, k)
+    got = fc.fc_sweep_tables(h, k, 0, total)
+    combos = np.array(list(itertools.combinations(range(S), k)), dtype=np.uint32)
+    ref = oracle.tables(ds.genotypes, ds.phenotype, k, combos)
+    bad = np.nonzero(np.any(got != ref, axis=(1, 2)))[0]
+    assert len(bad) == 0, (variant, len(bad), combos[bad[:3]])
+
+
+def test_sweep_tables_full_size_windows(fc, variant):
+    ds = make_config("C2")
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    total = math.comb(ds.S, 3)
+    rng = np.random.default_rng(9)
+    for start in [0, int(rng.integers(0, total - 3000)), total - 2500]:
+        n = min(2500, total - start)
+        got = fc.fc_sweep_tables(h, 3, start, n)
+        combos = np.array([fc.fc_unrank(ds.S, 3, r) for r in range(start, start + n)], dtype=np.uint32)
+        assert np.array_equal(got, oracle.tables(ds.genotypes, ds.phenotype, 3, combos))
+
+
+@pytest.mark.parametrize("k,S", [(2, 400), (3, 160)])
+def test_ie_and_full_searches_agree(fc, monkeypatch, k, S):
+    ds = make_dataset("agree", seed=520 + k, S=S, cases=2000, controls=2100, k=k, top_n=100,
+                      planted=(5, 77, 150)[:k])
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    monkeypatch.setenv("FC_PAIRS_PATH", "popc")
+    monkeypatch.delenv("FC_SWEEP", raising=False)
+    a = fc.fc_search(h, k, 100)
+    assert fc.fc_last_search_kind(h) == 3
+    monkeypatch.setenv("FC_SWEEP", "full")
+    b = fc.fc_search(h, k, 100)
+    assert fc.fc_last_search_kind(h) == 1
+    assert np.array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    assert tuple(a[0][0]) == (5, 77, 150)[:k]
+
+
+def test_static_search_does_not_build_ie_tables(fc, monkeypatch):
+    """fc_search_static must not allocate: on a fresh handle it counts all
+    cells; once fc_search has built the inclusion-exclusion tables it uses
+    them.  Both give the same result."""
+    monkeypatch.delenv("FC_SWEEP", raising=False)
+    ds = make_dataset("st-ie", seed=531, S=120, cases=1000, controls=1000, k=3, top_n=50)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    a = fc.fc_search_static(h, 3, 50)
+    assert fc.fc_last_search_kind(h) == 1
+    b = fc.fc_search(h, 3, 50)
+    assert fc.fc_last_search_kind(h) == 3
+    c = fc.fc_search_static(h, 3, 50)
+    assert fc.fc_last_search_kind(h) == 3
+    for x in (b, c):
+        assert np.array_equal(a[0], x[0])
+        np.testing.assert_allclose(a[1], x[1], rtol=1e-12)

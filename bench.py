@@ -90,6 +90,17 @@ def workload_title(name):
     return CONFIG_TITLES[name]
 
 
+def counted_cells(kind, k):
+    """Cells the sweep popcounts per combination, by fc_last_search_kind:
+    1 all 3^k (the paper's method), 3 the 2^k with genotypes in {0,1}
+    (inclusion-exclusion), 4 the 2 * 3^(k-1) with extension genotype 0/1."""
+    if kind == 3:
+        return 2 ** k, "IE"
+    if kind == 4:
+        return 2 * 3 ** (k - 1), "JR"
+    return 3 ** k, "full"
+
+
 def algorithmic_popc(ds, k):
     """32-bit POPCs per combination of the paper's method (3^k cells x
     32-bit words of both classes), times the number of combinations."""
@@ -332,19 +343,19 @@ def run_ours(args):
         # popcounts 3^k cells per combination (the paper's method); the
         # inclusion-exclusion variant (kind 3) popcounts the 2^k cells with
         # genotypes in {0,1} and derives the rest exactly.
-        ie = kind == 3
         peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
         paper_popc = algorithmic_popc(ds, k)
-        popc = paper_popc * (2 ** k) // (3 ** k) if ie else paper_popc
+        cells, variant = counted_cells(kind, k)
+        popc = paper_popc * cells // (3 ** k)
         achieved = popc / sweep_avg_s / 1e12 if sweeps else None
-        kernel_key = f"k_search<{k},{'IE' if ie else 'full'},TOPN> {args.workload}"
+        kernel_key = f"k_search<{k},{variant},TOPN> {args.workload}"
         roofline = {"bound": "alu", "kernel": kernel_key, "achieved": achieved, "peak": peak,
                     "unit": "Tpopc32/s", "frac": (achieved / peak) if achieved else None,
                     "traffic": traffic_for(kernel_key),
                     "peak_basis": f"{props.multi_processor_count} SMs x {POPC_PER_CLK_PER_SM} POPC/clk x {sm_max:.0f} MHz",
                     "sweep_ms_per_launch": 1e3 * sweep_avg_s,
                     "algorithmic_popc_per_launch": popc,
-                    "counted_cells_per_combination": (2 ** k) if ie else (3 ** k),
+                    "counted_cells_per_combination": cells,
                     "paper_method_popc_per_launch": paper_popc,
                     "paper_method_equivalent_tpopc_s": paper_popc / sweep_avg_s / 1e12 if sweeps else None}
 
@@ -437,7 +448,9 @@ def run_batch(args):
         pass
     sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
     peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-    popc = sum(algorithmic_popc(ds, k) for ds, _ in batch) * args.c5_replicates
+    cells, variant = counted_cells(fc.fc_last_search_kind(h), k)
+    paper_popc = sum(algorithmic_popc(ds, k) for ds, _ in batch) * args.c5_replicates
+    popc = paper_popc * cells // (3 ** k)
     sweep_s = sweep_ms / max(sweeps, 1) / 1e3
     achieved = popc / sweep_s / 1e12 if sweeps else None
     line = {
@@ -449,9 +462,10 @@ def run_batch(args):
                    "(S ~ U[200,1500], M ~ U[1000,8000], case fraction ~ U[0.3,0.7]), top 10 each",
                    "jobs": n_jobs, "combinations": combos, "l2": "flushed between timed steps (256 MiB write)"},
         "sample_combinations_per_s": samples / (ms / 1e3),
-        "roofline": {"bound": "alu", "kernel": "k_search_batch<3,*>", "achieved": achieved, "peak": peak,
-                     "unit": "Tpopc32/s", "frac": achieved / peak if achieved else None, "traffic": None,
-                     "sweep_ms_per_launch": 1e3 * sweep_s},
+        "roofline": {"bound": "alu", "kernel": f"k_search_batch<3,{variant}>", "achieved": achieved,
+                     "peak": peak, "unit": "Tpopc32/s", "frac": achieved / peak if achieved else None,
+                     "traffic": None, "sweep_ms_per_launch": 1e3 * sweep_s,
+                     "counted_cells_per_combination": cells, "paper_method_popc_per_launch": paper_popc},
         "batched_vs_per_job": {"batched_ms": ms, "per_job_ms": per_job_ms, "speedup": per_job_ms / ms,
                                "identical_results": bool(same), "identical_replay": identical_replay},
         "gpu_launches": int(launches), "clocks": clk,

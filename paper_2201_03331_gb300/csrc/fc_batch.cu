@@ -15,7 +15,7 @@ namespace fc {
 
 // ---- autotuner ---------------------------------------------------------------
 
-int sweep_candidates(const Dataset &d, int k, int L, int mode, bool ie, TuneConfig *out, int max_out)
+int sweep_candidates(const Dataset &d, int k, int L, int mode, int var, TuneConfig *out, int max_out)
 {
     int n = 0;
     const int Gs[3] = {1, 2, 4};
@@ -30,7 +30,7 @@ int sweep_candidates(const Dataset &d, int k, int L, int mode, bool ie, TuneConf
             for (int wj = 0; wj < wi; ++wj) dup = dup || WTs[wj] == WT;
             if (dup) continue;
             for (int ni = 0; ni < 2; ++ni) {
-                TuneConfig c{G, NWs[ni], WT, 0, ie};
+                TuneConfig c{G, NWs[ni], WT, 0, var};
                 size_t smem = 0;
                 const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)d.M, &smem);
                 if (nb <= 0) continue;
@@ -52,16 +52,16 @@ std::map<std::tuple<int, int, int64_t, int64_t, int, int>, TuneConfig> g_tune_ca
 // fastest.  Results are cached per process.
 TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback, bool cached_only)
 {
-    const auto key = std::make_tuple(k * 2 + (fallback.ie ? 1 : 0), d.Wt, d.S, d.M, L, d.device);
+    const auto key = std::make_tuple(k * 4 + fallback.var, d.Wt, d.S, d.M, L, d.device);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) return it->second;
     }
     if (cached_only) return fallback;
-    if (fallback.ie && d.prepare_ie(k) != FC_OK) return fallback;
+    if (fallback.var == VAR_IE && d.prepare_ie(k) != FC_OK) return fallback;
     TuneConfig cand[32];
-    const int n = sweep_candidates(d, k, L, MODE_TOPN, fallback.ie, cand, 32);
+    const int n = sweep_candidates(d, k, L, MODE_TOPN, fallback.var, cand, 32);
     const uint64_t total = binom(d.S, k);
     TuneConfig best = fallback;
     float best_ms = 1e30f;
@@ -140,9 +140,25 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
         if (t > binom(h->jobs[rep]->S, k)) rep = j;
     }
     Dataset &R = *h->jobs[rep];
-    // The batched kernel counts all 3^k cells (per-job inclusion-exclusion
-    // tables would multiply the memory by the number of jobs).
-    TuneConfig cfg = R.pick_config(k, L, MODE_TOPN, false, false);
+    // Counting variant for every job: inclusion-exclusion when each job may
+    // build its tables and their total stays within 64 GiB, else the
+    // extension-restricted count (k >= 2) or the full count.
+    bool use_ie = (k == 2 || k == 3);
+    double ie_bytes = 0.0;
+    for (int j = 0; j < nj && use_ie; ++j) {
+        const Dataset &d = *h->jobs[j];
+        use_ie = d.ie_eligible(k);
+        ie_bytes += 16.0 * (double)d.S + (k == 3 ? 16.0 * (double)d.S_pad * (double)d.S_pad : 0.0);
+    }
+    use_ie = use_ie && ie_bytes <= 64.0 * 1024 * 1024 * 1024;
+    if (use_ie) {
+        for (int j = 0; j < nj; ++j) {
+            const int rc = h->jobs[j]->prepare_ie(k);
+            if (rc) return rc;
+        }
+    }
+    TuneConfig cfg = R.pick_config(k, L, MODE_TOPN, false, use_ie);
+    if (!use_ie && cfg.var == VAR_IE) cfg.var = k >= 2 ? VAR_JR : VAR_FULL;
     // The batch kernel holds the ln table of the largest sample count.
     {
         size_t smem = 0;
@@ -175,6 +191,9 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
         jd.invN = (float)(1.0 / (double)d.M);
         jd.eps = score_error_bound(k, d.M);
         jd.total = binom(d.S, k);
+        jd.marg4 = reinterpret_cast<const uint4 *>(d.marg);
+        jd.PR = d.PR;
+        jd.nn = (uint32_t)d.M1 | ((uint32_t)d.M0 << 16);
         jd.N = (int)std::min<uint64_t>((uint64_t)top_n, jd.total);
         int ni = (int)std::min<uint64_t>((uint64_t)max_items_job, (jd.total + target - 1) / target);
         ni = std::max(ni, 1);
@@ -397,6 +416,9 @@ int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doubl
             return cuda_status(e, "batched graph launch");
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e, "batched search");
         Dataset &lead = h->ds;
+        lead.last_list = B.L;
+        lead.last_path_tc = false;
+        lead.last_sweep_var = effective_variant(k, B.cfg.var, MODE_BATCH);
         if (lead.timing) {
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, B.ev0, B.ev1) == cudaSuccess) {

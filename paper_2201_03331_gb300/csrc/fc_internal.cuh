@@ -124,12 +124,20 @@ struct SearchArgs {
     uint32_t nn;            // cases | controls << 16
 };
 
+// Counting variants of the sweep (all give the same exact table):
+//  VAR_FULL: popcount all 3^k cells (the paper's method);
+//  VAR_IE:   popcount the 2^k cells with genotypes in {0,1}; the rest from
+//            per-SNP counts and restricted pair tables (k = 2, 3);
+//  VAR_JR:   popcount the cells whose extension-SNP genotype is 0 or 1
+//            (2 * 3^(k-1)); genotype 2 from the prefix's own table.
+enum SweepVariant { VAR_FULL = 0, VAR_IE = 1, VAR_JR = 2 };
+
 struct TuneConfig {
     int G;          // lanes per combination
     int NW;         // warps per CTA
     int WT;         // 128-bit words per prefix-table tile
     int grid;       // CTAs
-    bool ie;        // inclusion-exclusion counting (k <= 3)
+    int var;        // SweepVariant
 };
 
 enum SearchMode { MODE_TOPN = 0, MODE_SCORES = 1, MODE_TABLES = 4 };
@@ -139,6 +147,8 @@ cudaError_t launch_restricted_pairs(const uint4 *X, int64_t S, int64_t S_pad, in
 
 cudaError_t launch_search(int k, const TuneConfig &cfg, int mode, const SearchArgs &a,
                           cudaStream_t st, size_t *smem_out);
+// The variant a kernel of (order, requested variant, mode) really runs.
+int effective_variant(int k, int var, int mode);
 int search_max_blocks_per_sm(int k, const TuneConfig &cfg, int mode, int L, int M, size_t *smem);
 
 cudaError_t launch_merge(const float *in_s, const uint64_t *in_r, int nlists, int L,
@@ -176,6 +186,9 @@ struct JobDesc {
     int N;                  // min(top_n, C(S, k))
     uint64_t total;         // C(S, k)
     int item_first, n_items;
+    const uint4 *marg4;     // inclusion-exclusion tables of the job (or null)
+    const uint4 *PR;
+    uint32_t nn;            // cases | controls << 16
 };
 
 struct BatchItem {

@@ -499,8 +499,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                     if (valid) {
 #pragma unroll
                         for (int x = 0; x < 9; ++x) {
-                            const uint32_t ca = cell[0][x], cb = cell[1][x];
-                            const float ln = logtab[ca + cb];
+                            // Clamped so that no index can leave the table.
+                            const uint32_t lt = (uint32_t)a.M;
+                            const uint32_t ca = min(cell[0][x], lt), cb = min(cell[1][x], lt);
+                            const float ln = logtab[min(ca + cb, lt)];
                             hsum = fmaf((float)ca, ln - logtab[ca], hsum);
                             hsum = fmaf((float)cb, ln - logtab[cb], hsum);
                         }

@@ -243,7 +243,7 @@ float score_error_bound(int k, int64_t M)
 bool Dataset::ie_eligible(int k) const
 {
     const char *mode = getenv("FC_SWEEP");
-    if (mode && strcmp(mode, "full") == 0) return false;
+    if (mode && (strcmp(mode, "full") == 0 || strcmp(mode, "jr") == 0)) return false;
     if (k != 2 && k != 3) return false;
     // The restricted pair table of order 3 holds S_pad^2 x 16 bytes.
     if (k == 3 && (double)S_pad * (double)S_pad * 16.0 > 2.0 * 1024 * 1024 * 1024) return false;
@@ -286,7 +286,14 @@ TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allo
     TuneConfig c{};
     c.G = 1;
     c.WT = std::min(Wt, 64);
-    c.ie = allow_ie && ie_eligible(k) && (!no_alloc || (marg && (k != 3 || PR)));
+    // Counting variant: inclusion-exclusion where its tables may be built,
+    // else the extension-restricted count (k >= 2), else the full count.
+    // FC_SWEEP=full|ie|jr forces one (where the order supports it).
+    const char *force = getenv("FC_SWEEP");
+    const bool ie_ok = allow_ie && ie_eligible(k) && (!no_alloc || (marg && (k != 3 || PR)));
+    c.var = ie_ok ? VAR_IE : (k >= 2 ? VAR_JR : VAR_FULL);
+    if (force && strcmp(force, "jr") == 0 && k >= 2) c.var = VAR_JR;
+    if (force && strcmp(force, "full") == 0) c.var = VAR_FULL;
     const int nws[3] = {8, 4, 2};
     bool found = false;
     for (int i = 0; i < 3 && !found; ++i) {
@@ -333,7 +340,7 @@ int Dataset::time_sweep(int k, const TuneConfig &cfg, int L, uint64_t n, float *
     if (rc) return rc;
     Arena A2;
     A2.base = scratch;
-    if (cfg.ie && (rc = prepare_ie(k)) != FC_OK) return rc;
+    if (cfg.var == VAR_IE && (rc = prepare_ie(k)) != FC_OK) return rc;
     SearchArgs sa{};
     fill_search_args(sa);
     sa.rank_begin = 0; sa.rank_end = n;
@@ -555,7 +562,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             grid = std::min(sms, ntiles);
         } else {
             cfg = pick_config(k, L, MODE_TOPN, no_alloc);
-            if (cfg.ie) {
+            if (cfg.var == VAR_IE) {
                 int rc = prepare_ie(k);
                 if (rc) return rc;
             }
@@ -624,7 +631,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         if (timing) cudaEventRecord(ev_sweep1, stream);
         note_launches(1);
         last_path_tc = tc;
-        last_sweep_ie = !tc && cfg.ie;
+        last_sweep_var = tc ? -1 : effective_variant(k, cfg.var, MODE_TOPN);
         // Grid merge.
         const float *src_s = (const float *)p[0];
         const uint64_t *src_r = (const uint64_t *)p[1];
@@ -685,7 +692,7 @@ int Dataset::sweep_dump(int k, int mode, uint64_t rank_begin, int64_t n, void *o
     if (n == 0) return FC_OK;
     TuneConfig cfg = pick_config(k, 0, mode);
     int rc;
-    if (cfg.ie && (rc = prepare_ie(k)) != FC_OK) return rc;
+    if (cfg.var == VAR_IE && (rc = prepare_ie(k)) != FC_OK) return rc;
     const int64_t per_cta = (int64_t)cfg.NW * 32;
     cfg.grid = (int)std::max<int64_t>(1, std::min<int64_t>(cfg.grid, (n + per_cta - 1) / per_cta));
     const size_t bytes = mode == MODE_SCORES ? sizeof(float) * n : sizeof(uint32_t) * 2 * pow3(k) * (size_t)n;
@@ -699,7 +706,7 @@ int Dataset::sweep_dump(int k, int mode, uint64_t rank_begin, int64_t n, void *o
     if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, mode, sa, stream, nullptr)) != cudaSuccess)
         return cuda_status(e, "sweep dump kernel");
     note_launches(1);
-    last_sweep_ie = cfg.ie;
+    last_sweep_var = effective_variant(k, cfg.var, mode);
     cudaMemcpyAsync(out, scratch, bytes, cudaMemcpyDeviceToHost, stream);
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "sweep dump");
     return FC_OK;
@@ -985,7 +992,9 @@ int fc_last_search_kind(const fc_handle *h)
     if (!h) return set_error(FC_EINVAL, "NULL handle");
     if (h->ds.last_path_tc) return 2;
     if (h->ds.last_list == 0) return 0;
-    return h->ds.last_sweep_ie ? 3 : 1;
+    if (h->ds.last_sweep_var == VAR_IE) return 3;
+    if (h->ds.last_sweep_var == VAR_JR) return 4;
+    return 1;
 }
 
 int fc_sweep_tables(fc_handle *h, int k, uint64_t rank_begin, int64_t n, uint32_t *out)

@@ -94,7 +94,7 @@ struct Dataset {
     // Inclusion-exclusion sweep (k = 2, 3): per-SNP genotype counts and, for
     // k = 3, the restricted pair table, built on first use.
     uint4 *PR = nullptr;
-    bool last_sweep_ie = false;
+    int last_sweep_var = VAR_FULL;   // counting variant of the last sweep
     bool ie_eligible(int k) const;
     int prepare_ie(int k);
     void fill_search_args(SearchArgs &sa) const;
@@ -107,7 +107,7 @@ struct Dataset {
 // by (k, words, SNPs, samples, list size); falls back to `fallback`.
 TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback, bool cached_only = false);
 // Candidate sweep configurations that fit on the device for (k, L, M).
-int sweep_candidates(const Dataset &d, int k, int L, int mode, bool ie, TuneConfig *out, int max_out);
+int sweep_candidates(const Dataset &d, int k, int L, int mode, int var, TuneConfig *out, int max_out);
 
 // Many data sets (x phenotype replicates) searched by one persistent launch.
 struct BatchState {

@@ -35,6 +35,18 @@ __device__ __forceinline__ uint32_t popc_and4(const uint4 &a, const uint4 &b)
     return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
 }
 
+// Population count of a & b over 128 bits with one carry-save adder: the
+// three words v0, v1, v2 sum bitwise to s + 2c with s = v0 ^ v1 ^ v2 and
+// c = majority(v0, v1, v2), so three POPCs (XU pipe) replace four at the
+// cost of two 3-input logic ops (ALU pipe), which has four times the rate.
+__device__ __forceinline__ uint32_t popc_and4_csa(const uint4 &a, const uint4 &b)
+{
+    const uint32_t v0 = a.x & b.x, v1 = a.y & b.y, v2 = a.z & b.z, v3 = a.w & b.w;
+    const uint32_t s = v0 ^ v1 ^ v2;
+    const uint32_t c = (v0 & v1) | (v2 & (v0 | v1));
+    return __popc(s) + __popc(v3) + (__popc(c) << 1);
+}
+
 // Descending bitonic sort (by better()) of n = 2^p entries in shared memory.
 __device__ void block_bitonic_desc(float *s, uint64_t *r, int n)
 {
@@ -55,15 +67,15 @@ __device__ void block_bitonic_desc(float *s, uint64_t *r, int n)
     __syncthreads();
 }
 
-__host__ __device__ constexpr int prefix_rows(int k, bool ie) { return ie ? (1 << (k - 1)) : pow3(k - 1); }
+__host__ __device__ constexpr int prefix_rows(int k, int var) { return var == VAR_IE ? (1 << (k - 1)) : pow3(k - 1); }
 
 // Shared-memory layout of the sweep kernels (uint4 units):
 //   [logtab: ceil((M+1)/4)] [prefix tables: NW * P * WT]
 //   [list ranks: NW * L (uint64)] [list scores: NW * L (float)]
-__host__ __device__ inline size_t search_smem_bytes(int k, bool ie, int NW, int WT, int L, int M)
+__host__ __device__ inline size_t search_smem_bytes(int k, int var, int NW, int WT, int L, int M)
 {
     const size_t lt = (size_t)((M + 1 + 3) / 4) * 16;
-    const size_t pt = (size_t)NW * prefix_rows(k, ie) * WT * 16;
+    const size_t pt = (size_t)NW * prefix_rows(k, var) * WT * 16;
     const size_t ls = (size_t)NW * L * (8 + 4);
     return lt + pt + ls;
 }
@@ -124,6 +136,7 @@ struct SweepJob {
     const uint4 *marg4;     // IE: per-SNP genotype counts, one uint4 per SNP
     const uint4 *PR;        // IE, k = 3: restricted pair table [S_pad][S_pad]
     uint32_t nn;            // IE: cases | controls << 16
+    uint32_t lt_max;        // last index of the shared-memory ln table
 };
 
 // Warp-uniform state of a warp's top-L list (sorted_insert, warp form).
@@ -182,16 +195,20 @@ __device__ __forceinline__ void warp_offer(bool cand, float score, uint64_t rank
 }
 
 // The warp-level sweep over combination ranks [r, r_end) of one data set.
-template <int K, bool IE, int G, int MODE>
+template <int K, int VAR, int G, int MODE>
 __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end, uint4 *ptab, const int WT,
                            const float *logtab, float *lsc, uint64_t *lrk, const int L, WarpList &st,
                            void *dump, const uint64_t dump_base)
 {
-    constexpr int P = prefix_rows(K, IE);  // prefix-table rows
-    constexpr int GJ = IE ? 2 : 3;         // extension-SNP rows used
-    constexpr int CNT = P * GJ;            // popcounted cells
-    constexpr int C = pow3(K);             // cells of the full table
-    constexpr int CPW = 32 / G;            // combinations per warp chunk
+    constexpr bool IE = VAR == VAR_IE;
+    constexpr bool JR = VAR == VAR_JR && K >= 2;
+    constexpr int P = prefix_rows(K, VAR);   // prefix-table rows
+    constexpr int GJ = (IE || JR) ? 2 : 3;   // extension-SNP rows used
+    constexpr int PB = IE ? 2 : 3;           // digit base of the prefix rows
+    constexpr int CNT = P * GJ;              // popcounted cells
+    constexpr int C = pow3(K);               // cells of the full table
+    constexpr int CPW = 32 / G;              // combinations per warp chunk
+    constexpr int PC = JR ? P : 1;           // prefix counts kept for JR
     const int lane = threadIdx.x & 31;
     const int slot = lane / G;
     const int q = lane % G;
@@ -207,6 +224,10 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
     uint32_t T0[3] = {0, 0, 0}, T1[3] = {0, 0, 0}, T01[9];
 #pragma unroll
     for (int x = 0; x < 9; ++x) T01[x] = 0;
+    // JR: the full table of the (k-1)-prefix, one packed count per prefix row.
+    uint32_t Tpre[PC];
+#pragma unroll
+    for (int x = 0; x < PC; ++x) Tpre[x] = 0;
 
     while (r < r_end) {
         const uint32_t j0 = cmb[K - 1];
@@ -226,6 +247,37 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
                 full2(R01, T0, T1, T01);
             }
         }
+        if constexpr (JR) {
+            if (!same) {
+                // Counts of the prefix's own 3^(k-1) genotype cells: lanes
+                // split the words, the warp reduces.
+#pragma unroll
+                for (int x = 0; x < PC; ++x) Tpre[x] = 0;
+                for (int w = lane; w < jb.Wt; w += 32) {
+                    uint4 rows[K - 1][3];
+#pragma unroll
+                    for (int t = 0; t < K - 1; ++t)
+#pragma unroll
+                        for (int g = 0; g < 3; ++g) rows[t][g] = jb.X[((size_t)w * 3 + g) * Sp + cmb[t]];
+                    const int sh = w < jb.W0 ? 0 : 16;
+#pragma unroll
+                    for (int pa = 0; pa < PC; ++pa) {
+                        uint4 v = make_uint4(~0u, ~0u, ~0u, ~0u);
+                        int rem = pa;
+#pragma unroll
+                        for (int t = K - 2; t >= 0; --t) {
+                            const int g = rem % 3;
+                            rem /= 3;
+                            v.x &= rows[t][g].x; v.y &= rows[t][g].y;
+                            v.z &= rows[t][g].z; v.w &= rows[t][g].w;
+                        }
+                        Tpre[pa] += (__popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w)) << sh;
+                    }
+                }
+#pragma unroll
+                for (int pa = 0; pa < PC; ++pa) Tpre[pa] = __reduce_add_sync(FULL, Tpre[pa]);
+            }
+        }
 
         uint32_t acc[CNT];
 #pragma unroll
@@ -242,7 +294,7 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
 #pragma unroll
                     for (int t = 0; t < K - 1; ++t)
 #pragma unroll
-                        for (int g = 0; g < GJ; ++g)
+                        for (int g = 0; g < PB; ++g)
                             rows[t][g] = jb.X[((size_t)(t0 + w) * 3 + g) * Sp + cmb[t]];
 #pragma unroll
                     for (int pa = 0; pa < P; ++pa) {
@@ -250,8 +302,8 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
                         int rem = pa;
 #pragma unroll
                         for (int t = K - 2; t >= 0; --t) {
-                            const int g = rem % GJ;
-                            rem /= GJ;
+                            const int g = rem % PB;
+                            rem /= PB;
                             v.x &= rows[t][g].x; v.y &= rows[t][g].y;
                             v.z &= rows[t][g].z; v.w &= rows[t][g].w;
                         }
@@ -276,7 +328,7 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
                 for (int pa = 0; pa < P; ++pa) {
                     const uint4 pv = ptab[pa * WT + w];
 #pragma unroll
-                    for (int g = 0; g < GJ; ++g) acc[GJ * pa + g] += popc_and4(pv, xg[g]) << sh;
+                    for (int g = 0; g < GJ; ++g) acc[GJ * pa + g] += popc_and4_csa(pv, xg[g]) << sh;
                 }
             }
         }
@@ -306,6 +358,15 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
                 full2(R12, T1, Tj, T12);
                 full3(acc, T01, T02, T12, T);
             }
+        } else if constexpr (JR) {
+            // Cell (prefix row pa, genotype 2 of j) = prefix cell - the
+            // cells with genotypes 0 and 1 of j.
+#pragma unroll
+            for (int pa = 0; pa < P; ++pa) {
+                T[3 * pa + 0] = acc[2 * pa + 0];
+                T[3 * pa + 1] = acc[2 * pa + 1];
+                T[3 * pa + 2] = Tpre[pa] - acc[2 * pa + 0] - acc[2 * pa + 1];
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < C; ++c) T[c] = acc[c];
@@ -318,9 +379,11 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
         for (int c = 0; c < C; ++c) {
             const uint32_t ca = T[c] & 0xffffu;
             const uint32_t cb = T[c] >> 16;
-            const float ln = logtab[ca + cb];
-            hsum = fmaf((float)ca, ln - logtab[ca], hsum);
-            hsum = fmaf((float)cb, ln - logtab[cb], hsum);
+            // Indices are clamped to the table: exact counts never exceed M,
+            // and nothing outside the table can be read if that ever failed.
+            const float ln = logtab[min(ca + cb, jb.lt_max)];
+            hsum = fmaf((float)ca, ln - logtab[min(ca, jb.lt_max)], hsum);
+            hsum = fmaf((float)cb, ln - logtab[min(cb, jb.lt_max)], hsum);
         }
         const float score = fmaf(-hsum, jb.invN, jb.hy);
         const uint64_t rank = r + (uint64_t)slot;
@@ -349,10 +412,10 @@ __device__ void warp_sweep(const SweepJob &jb, uint64_t r, const uint64_t r_end,
     }
 }
 
-template <int K, bool IE, int G, int MODE>
+template <int K, int VAR, int G, int MODE>
 __global__ void __launch_bounds__(256) k_search(SearchArgs a, int NW, int WT)
 {
-    constexpr int P = prefix_rows(K, IE);
+    constexpr int P = prefix_rows(K, VAR);
     extern __shared__ uint4 smem4[];
     const int warp = threadIdx.x >> 5;
     const int L = MODE == MODE_TOPN ? a.L : 0;
@@ -379,10 +442,10 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a, int NW, int WT)
     const uint64_t r = a.rank_begin + (uint64_t)(((unsigned __int128)R * gw) / total_warps);
     const uint64_t r_end = a.rank_begin + (uint64_t)(((unsigned __int128)R * (gw + 1)) / total_warps);
 
-    SweepJob jb{a.X, a.S, a.S_pad, a.W0, a.Wt, a.hy, a.invN, a.marg4, a.PR, a.nn};
+    SweepJob jb{a.X, a.S, a.S_pad, a.W0, a.Wt, a.hy, a.invN, a.marg4, a.PR, a.nn, (uint32_t)a.M};
     WarpList st;
     st.reset();
-    warp_sweep<K, IE, G, MODE>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
+    warp_sweep<K, VAR, G, MODE>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
                                lrank_all + (size_t)warp * L, L, st, a.dump, a.rank_begin);
 
     if (MODE == MODE_TOPN) {
@@ -399,10 +462,10 @@ __global__ void __launch_bounds__(256) k_search(SearchArgs a, int NW, int WT)
 // global counter; each item's warps sweep equal sub-ranges, the CTA merges
 // their lists and writes the item's best L.  Results do not depend on which
 // CTA takes which item.
-template <int K, int G>
+template <int K, int VB, int G>
 __global__ void __launch_bounds__(256) k_search_batch(BatchArgs b, int NW, int WT)
 {
-    constexpr int P = prefix_rows(K, false);
+    constexpr int P = prefix_rows(K, VB);
     extern __shared__ uint4 smem4[];
     __shared__ int s_item;
     const int warp = threadIdx.x >> 5;
@@ -427,13 +490,13 @@ __global__ void __launch_bounds__(256) k_search_batch(BatchArgs b, int NW, int W
         if (item >= b.n_items) break;
         const BatchItem it = b.items[item];
         const JobDesc jd = b.jobs[it.job];
-        const SweepJob jb{jd.X, jd.S, jd.S_pad, jd.W0, jd.Wt, jd.hy, jd.invN, nullptr, nullptr, 0u};
+        const SweepJob jb{jd.X, jd.S, jd.S_pad, jd.W0, jd.Wt, jd.hy, jd.invN, jd.marg4, jd.PR, jd.nn, (uint32_t)b.M};
         const uint64_t R = it.r1 - it.r0;
         const uint64_t r = it.r0 + (uint64_t)(((unsigned __int128)R * warp) / NW);
         const uint64_t r_end = it.r0 + (uint64_t)(((unsigned __int128)R * (warp + 1)) / NW);
         WarpList st;
         st.reset();
-        warp_sweep<K, false, G, MODE_TOPN>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
+        warp_sweep<K, VB, G, MODE_TOPN>(jb, r, r_end, ptab, WT, logtab, lscore_all + (size_t)warp * L,
                                            lrank_all + (size_t)warp * L, L, st, nullptr, 0);
         block_bitonic_desc(lscore_all, lrank_all, NW * L);
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
@@ -517,21 +580,30 @@ __global__ void k_merge_jobs(const JobDesc *jobs, const float *item_s, const uin
     }
 }
 
-template <int K, bool IE, int G>
+template <int K, int VAR, int G>
 void *search_kernel_ptr(int mode)
 {
-    if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search<K, IE, G, MODE_TOPN>);
-    if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search<K, IE, G, MODE_SCORES>);
-    if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search<K, IE, G, MODE_TABLES>);
-    if (!IE && mode == MODE_BATCH) return reinterpret_cast<void *>(&k_search_batch<K, G>);
+    if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search<K, VAR, G, MODE_TOPN>);
+    if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search<K, VAR, G, MODE_SCORES>);
+    if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search<K, VAR, G, MODE_TABLES>);
     return nullptr;
 }
 
-void *pick_kernel(int k, bool ie, int G, int mode)
+// Kernel for (order, variant, lanes per combination, mode).  Variants a
+// given order does not support fall back to the full count.
+void *pick_kernel(int k, int var, int G, int mode)
 {
 #define FC_PICK(KK, GG)                                                                      \
-    if (k == KK && G == GG) return ie ? search_kernel_ptr<KK, (KK <= 3), GG>(mode)           \
-                                      : search_kernel_ptr<KK, false, GG>(mode);
+    if (k == KK && G == GG) {                                                                \
+        if (mode == MODE_BATCH) {                                                            \
+            if (var == VAR_IE && KK <= 3) return reinterpret_cast<void *>(&k_search_batch<KK, VAR_IE, GG>); \
+            if (var == VAR_JR && KK >= 2) return reinterpret_cast<void *>(&k_search_batch<KK, VAR_JR, GG>); \
+            return reinterpret_cast<void *>(&k_search_batch<KK, VAR_FULL, GG>);             \
+        }                                                                                    \
+        if (var == VAR_IE && KK <= 3) return search_kernel_ptr<KK, VAR_IE, GG>(mode);        \
+        if (var == VAR_JR && KK >= 2) return search_kernel_ptr<KK, VAR_JR, GG>(mode);        \
+        return search_kernel_ptr<KK, VAR_FULL, GG>(mode);                                    \
+    }
     FC_PICK(1, 1) FC_PICK(1, 2) FC_PICK(1, 4)
     FC_PICK(2, 1) FC_PICK(2, 2) FC_PICK(2, 4)
     FC_PICK(3, 1) FC_PICK(3, 2) FC_PICK(3, 4)
@@ -542,12 +614,19 @@ void *pick_kernel(int k, bool ie, int G, int mode)
 
 }  // namespace
 
+int effective_variant(int k, int var, int mode)
+{
+    if (var == VAR_IE && k <= 3) return VAR_IE;
+    if (var == VAR_JR && k >= 2) return VAR_JR;
+    return VAR_FULL;
+}
+
 int search_max_blocks_per_sm(int k, const TuneConfig &cfg, int mode, int L, int M, size_t *smem)
 {
-    const bool ie = cfg.ie && k <= 3;
-    void *fn = pick_kernel(k, ie, cfg.G, mode);
+    const int var = effective_variant(k, cfg.var, mode);
+    void *fn = pick_kernel(k, var, cfg.G, mode);
     if (!fn) return 0;
-    const size_t bytes = search_smem_bytes(k, ie, cfg.NW, cfg.WT, (mode == MODE_TOPN || mode == MODE_BATCH) ? L : 0, M);
+    const size_t bytes = search_smem_bytes(k, var, cfg.NW, cfg.WT, (mode == MODE_TOPN || mode == MODE_BATCH) ? L : 0, M);
     if (smem) *smem = bytes;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
         return 0;
@@ -559,10 +638,10 @@ int search_max_blocks_per_sm(int k, const TuneConfig &cfg, int mode, int L, int 
 cudaError_t launch_search(int k, const TuneConfig &cfg, int mode, const SearchArgs &a,
                           cudaStream_t st, size_t *smem_out)
 {
-    const bool ie = cfg.ie && k <= 3;
-    void *fn = pick_kernel(k, ie, cfg.G, mode);
+    const int var = effective_variant(k, cfg.var, mode);
+    void *fn = pick_kernel(k, var, cfg.G, mode);
     if (!fn) return cudaErrorInvalidValue;
-    const size_t bytes = search_smem_bytes(k, ie, cfg.NW, cfg.WT, mode == MODE_TOPN ? a.L : 0, a.M);
+    const size_t bytes = search_smem_bytes(k, var, cfg.NW, cfg.WT, mode == MODE_TOPN ? a.L : 0, a.M);
     if (smem_out) *smem_out = bytes;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -576,9 +655,9 @@ cudaError_t launch_search_batch(int k, const TuneConfig &cfg, const BatchArgs &b
 {
     // The shared-memory attribute was set by search_max_blocks_per_sm with
     // MODE_BATCH and the same (cfg, L, M) before any stream capture.
-    void *fn = pick_kernel(k, false, cfg.G, MODE_BATCH);
+    void *fn = pick_kernel(k, effective_variant(k, cfg.var, MODE_BATCH), cfg.G, MODE_BATCH);
     if (!fn) return cudaErrorInvalidValue;
-    const size_t bytes = search_smem_bytes(k, false, cfg.NW, cfg.WT, b.L, b.M);
+    const size_t bytes = search_smem_bytes(k, effective_variant(k, cfg.var, MODE_BATCH), cfg.NW, cfg.WT, b.L, b.M);
     BatchArgs args = b;
     int NW = cfg.NW, WT = cfg.WT;
     void *params[] = {&args, &NW, &WT};

@@ -22,12 +22,12 @@ def fc():
     return fcm
 
 
-@pytest.fixture(params=["full", "ie"])
+@pytest.fixture(params=["full", "ie", "jr"])
 def variant(request, monkeypatch):
-    if request.param == "full":
-        monkeypatch.setenv("FC_SWEEP", "full")
-    else:
+    if request.param == "ie":
         monkeypatch.delenv("FC_SWEEP", raising=False)
+    else:
+        monkeypatch.setenv("FC_SWEEP", request.param)
     return request.param
 
 
@@ -68,20 +68,40 @@ def test_ie_and_full_searches_agree(fc, monkeypatch, k, S):
     monkeypatch.setenv("FC_SWEEP", "full")
     b = fc.fc_search(h, k, 100)
     assert fc.fc_last_search_kind(h) == 1
-    assert np.array_equal(a[0], b[0])
-    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    monkeypatch.setenv("FC_SWEEP", "jr")
+    c = fc.fc_search(h, k, 100)
+    assert fc.fc_last_search_kind(h) == 4
+    for x in (b, c):
+        assert np.array_equal(a[0], x[0])
+        np.testing.assert_allclose(a[1], x[1], rtol=1e-12)
     assert tuple(a[0][0]) == (5, 77, 150)[:k]
 
 
+def test_order4_variants_agree(fc, monkeypatch):
+    ds = make_dataset("o4", seed=540, S=32, cases=1500, controls=1500, k=4, top_n=60,
+                      planted=(2, 9, 20, 31))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    monkeypatch.delenv("FC_SWEEP", raising=False)
+    a = fc.fc_search(h, 4, 60)
+    assert fc.fc_last_search_kind(h) == 4      # order 4 counts 2 * 3^3 cells by default
+    monkeypatch.setenv("FC_SWEEP", "full")
+    b = fc.fc_search(h, 4, 60)
+    assert fc.fc_last_search_kind(h) == 1
+    assert np.array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    assert tuple(a[0][0]) == (2, 9, 20, 31)
+
+
 def test_static_search_does_not_build_ie_tables(fc, monkeypatch):
-    """fc_search_static must not allocate: on a fresh handle it counts all
-    cells; once fc_search has built the inclusion-exclusion tables it uses
-    them.  Both give the same result."""
+    """fc_search_static must not allocate: on a fresh handle it uses the
+    extension-restricted count, which needs no extra tables; once fc_search
+    has built the inclusion-exclusion tables it uses them.  Both give the
+    same result."""
     monkeypatch.delenv("FC_SWEEP", raising=False)
     ds = make_dataset("st-ie", seed=531, S=120, cases=1000, controls=1000, k=3, top_n=50)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     a = fc.fc_search_static(h, 3, 50)
-    assert fc.fc_last_search_kind(h) == 1
+    assert fc.fc_last_search_kind(h) == 4
     b = fc.fc_search(h, 3, 50)
     assert fc.fc_last_search_kind(h) == 3
     c = fc.fc_search_static(h, 3, 50)

@@ -48,8 +48,10 @@ extern "C" {
 #define FC_ETIMEOUT (-5) /* a bounded device wait ran out */
 #define FC_ENODEV (-6)   /* no usable CUDA device */
 
-/* Orders accepted by fc_search / fc_scores / fc_search_batch. */
-#define FC_KMAX_SEARCH 4
+/* Orders accepted by fc_search / fc_scores / fc_sweep_tables. */
+#define FC_KMAX_SEARCH 6
+/* Orders accepted by fc_search_batch. */
+#define FC_KMAX_BATCH 4
 /* Orders accepted by fc_tables. */
 #define FC_KMAX_TABLES 6
 /* Per-class sample limit: cases and controls each at most 65535. */

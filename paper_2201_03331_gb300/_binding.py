@@ -21,7 +21,8 @@ FC_ENOMEM = -3
 FC_ECUDA = -4
 FC_ETIMEOUT = -5
 FC_ENODEV = -6
-FC_KMAX_SEARCH = 4
+FC_KMAX_SEARCH = 6
+FC_KMAX_BATCH = 4
 FC_KMAX_TABLES = 6
 FC_MAX_LIST = 4096
 

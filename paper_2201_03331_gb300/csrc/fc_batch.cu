@@ -19,17 +19,20 @@ int sweep_candidates(const Dataset &d, int k, int L, int mode, int var, TuneConf
 {
     int n = 0;
     const int Gs[3] = {1, 2, 4};
-    const int NWs[2] = {8, 4};
-    const int WTs[3] = {std::min(d.Wt, 64), std::min(d.Wt, 32), std::min(d.Wt, 16)};
+    const int NWs[3] = {8, 4, 2};
+    const int WTs[4] = {std::min(d.Wt, 64), std::min(d.Wt, 32), std::min(d.Wt, 16), std::min(d.Wt, 8)};
     for (int gi = 0; gi < 3; ++gi) {
         const int G = Gs[gi];
         if (G == 4 && k < 4) continue;
-        for (int wi = 0; wi < 3; ++wi) {
+        if (G > 1 && k >= 5) continue;   // orders 5, 6 fix their lanes per combination
+        for (int wi = 0; wi < 4; ++wi) {
             const int WT = WTs[wi];
             bool dup = false;
             for (int wj = 0; wj < wi; ++wj) dup = dup || WTs[wj] == WT;
             if (dup) continue;
-            for (int ni = 0; ni < 2; ++ni) {
+            if (WT == 8 && k < 5) continue;
+            for (int ni = 0; ni < 3; ++ni) {
+                if (NWs[ni] == 2 && k < 5) continue;
                 TuneConfig c{G, NWs[ni], WT, 0, var};
                 size_t smem = 0;
                 const int nb = search_max_blocks_per_sm(k, c, mode, L, (int)d.M, &smem);
@@ -394,8 +397,8 @@ int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doubl
         const int nj = (int)h->jobs.size();
         int64_t minS = INT64_MAX;
         for (auto &j : h->jobs) minS = std::min(minS, j->S);
-        if (k < 1 || k > FC_KMAX_SEARCH || k > minS)
-            return set_error(FC_EINVAL, "order k=%d outside [1, min(%d, smallest S)]", k, FC_KMAX_SEARCH);
+        if (k < 1 || k > FC_KMAX_BATCH || k > minS)
+            return set_error(FC_EINVAL, "order k=%d outside [1, min(%d, smallest S)]", k, FC_KMAX_BATCH);
         if (top_n < 0) return set_error(FC_EINVAL, "top_n < 0");
         if (top_n > FC_MAX_LIST / 2) return set_error(FC_ERANGE, "top_n above %d", FC_MAX_LIST / 2);
         if (top_n > 0 && (!out_idx || !out_score)) return set_error(FC_EINVAL, "NULL output");

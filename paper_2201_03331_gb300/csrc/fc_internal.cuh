@@ -19,7 +19,8 @@
 
 namespace fc {
 
-constexpr int KMAX_SEARCH = 4;   // orders of the fused search kernels
+constexpr int KMAX_SEARCH = 6;   // orders of the fused search kernels
+constexpr int KMAX_BATCH = 4;    // orders of the batched kernel
 constexpr int KMAX_TABLES = 6;   // orders of the exact-table kernel
 
 __host__ __device__ constexpr int pow3(int k) { return k <= 0 ? 1 : 3 * pow3(k - 1); }

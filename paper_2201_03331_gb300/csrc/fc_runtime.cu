@@ -285,14 +285,20 @@ TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allo
 {
     TuneConfig c{};
     c.G = 1;
-    c.WT = std::min(Wt, 64);
+    // Prefix tile: at most 64 words and about 32 KiB of prefix rows per warp.
+    {
+        const int rows = pow3(k - 1);
+        int wt = 64;
+        while (wt > 8 && (size_t)rows * wt * 16 > 32768) wt >>= 1;
+        c.WT = std::min(Wt, wt);
+    }
     // Counting variant: inclusion-exclusion where its tables may be built,
     // else the extension-restricted count (k >= 2), else the full count.
     // FC_SWEEP=full|ie|jr forces one (where the order supports it).
     const char *force = getenv("FC_SWEEP");
     const bool ie_ok = allow_ie && ie_eligible(k) && (!no_alloc || (marg && (k != 3 || PR)));
-    c.var = ie_ok ? VAR_IE : (k >= 2 ? VAR_JR : VAR_FULL);
-    if (force && strcmp(force, "jr") == 0 && k >= 2) c.var = VAR_JR;
+    c.var = ie_ok ? VAR_IE : (k >= 2 && k <= 4 ? VAR_JR : VAR_FULL);
+    if (force && strcmp(force, "jr") == 0 && k >= 2 && k <= 4) c.var = VAR_JR;
     if (force && strcmp(force, "full") == 0) c.var = VAR_FULL;
     const int nws[3] = {8, 4, 2};
     bool found = false;

@@ -507,6 +507,167 @@ __global__ void __launch_bounds__(256) k_search_batch(BatchArgs b, int NW, int W
     }
 }
 
+// Row g of SNP s at the word whose first row starts at `base` in the bit table.
+__device__ __forceinline__ uint4 jb_row(const uint4 *X, size_t base, int64_t Sp, uint32_t s, int g)
+{
+    return X[base + (size_t)g * Sp + s];
+}
+
+// Sweep for orders 5 and 6 (all 3^k cells).  The 3^(k-1) prefix rows are
+// split over G = 3^(k-4) lanes per combination, 27 rows each, so every lane
+// keeps 81 counters; a group's lanes sum their partial MI terms with
+// shuffles.  Otherwise as k_search: per-warp rank ranges, prefix table in
+// shared memory (rebuilt when the prefix changes), packed counters, FP32 MI,
+// warp top list, block merge.
+template <int K, int MODE>
+__global__ void __launch_bounds__(256) k_search_rs(SearchArgs a, int NW, int WT)
+{
+    constexpr int P = pow3(K - 1);
+    constexpr int RL = 27;                 // prefix rows per lane
+    constexpr int G = P / RL;              // lanes per combination
+    constexpr int CPW = 32 / G;            // combinations per warp chunk
+    constexpr int C = pow3(K);
+    extern __shared__ uint4 smem4[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int L = MODE == MODE_TOPN ? a.L : 0;
+    const int slot = lane / G;
+    const int q = lane % G;
+    const uint32_t lt_max = (uint32_t)a.M;
+
+    float *logtab = reinterpret_cast<float *>(smem4);
+    uint4 *ptab_all = smem4 + (a.M + 1 + 3) / 4;
+    uint4 *ptab = ptab_all + (size_t)warp * P * WT;
+    uint64_t *lrank_all = reinterpret_cast<uint64_t *>(ptab_all + (size_t)NW * P * WT);
+    float *lscore_all = reinterpret_cast<float *>(lrank_all + (size_t)NW * L);
+    float *lsc = lscore_all + (size_t)warp * L;
+    uint64_t *lrk = lrank_all + (size_t)warp * L;
+
+    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) logtab[i] = a.logtab[i];
+    if (MODE == MODE_TOPN) {
+        for (int i = threadIdx.x; i < NW * L; i += blockDim.x) {
+            lscore_all[i] = -FLT_MAX;
+            lrank_all[i] = NO_RANK;
+        }
+    }
+    __syncthreads();
+
+    const uint64_t total_warps = (uint64_t)gridDim.x * NW;
+    const uint64_t gw = (uint64_t)blockIdx.x * NW + warp;
+    const uint64_t R = a.rank_end - a.rank_begin;
+    uint64_t r = a.rank_begin + (uint64_t)(((unsigned __int128)R * gw) / total_warps);
+    const uint64_t r_end = a.rank_begin + (uint64_t)(((unsigned __int128)R * (gw + 1)) / total_warps);
+
+    WarpList st;
+    st.reset();
+    if (r < r_end) {
+        uint32_t cmb[K];
+        unrank(a.S, K, r, cmb);
+        uint32_t cur[K - 1];
+        for (int t = 0; t < K - 1; ++t) cur[t] = 0xffffffffu;
+        int cur_tile = -1;
+        const int64_t Sp = a.S_pad;
+        while (r < r_end) {
+            const uint32_t j0 = cmb[K - 1];
+            const int n = (int)min((uint64_t)CPW, min((uint64_t)(a.S - j0), r_end - r));
+            if (n <= 0) break;   // unreachable for a valid rank range; guards the loop
+            const bool valid = slot < n;
+            const uint32_t j = valid ? j0 + slot : j0;
+            bool same = true;
+            for (int t = 0; t < K - 1; ++t) same = same && (cur[t] == cmb[t]);
+
+            uint32_t acc[3 * RL];
+#pragma unroll
+            for (int c = 0; c < 3 * RL; ++c) acc[c] = 0;
+            for (int t0 = 0; t0 < a.Wt; t0 += WT) {
+                const int tw = min(WT, a.Wt - t0);
+                if (!(same && cur_tile == t0)) {
+                    __syncwarp();
+                    // combine: all 3^(k-1) prefix rows of this tile's words.
+                    for (int w = lane; w < tw; w += 32) {
+                        const size_t base = (size_t)(t0 + w) * 3 * Sp;
+                        for (int pa = 0; pa < P; ++pa) {
+                            uint4 v = make_uint4(~0u, ~0u, ~0u, ~0u);
+                            int rem = pa;
+#pragma unroll
+                            for (int t = K - 2; t >= 0; --t) {
+                                const int g = rem % 3;
+                                rem /= 3;
+                                const uint4 x = jb_row(a.X, base, Sp, cmb[t], g);
+                                v.x &= x.x; v.y &= x.y; v.z &= x.z; v.w &= x.w;
+                            }
+                            ptab[pa * WT + w] = v;
+                        }
+                    }
+                    __syncwarp();
+                    for (int t = 0; t < K - 1; ++t) cur[t] = cmb[t];
+                    cur_tile = t0;
+                    same = true;
+                }
+                // combine_and_popcount over this lane's 27 prefix rows.
+                for (int w = 0; w < tw; ++w) {
+                    const int wg = t0 + w;
+                    const uint4 *xp = a.X + (size_t)wg * 3 * Sp + j;
+                    const uint4 x0 = xp[0], x1 = xp[Sp], x2 = xp[2 * Sp];
+                    const int sh = wg < a.W0 ? 0 : 16;
+                    const uint4 *prow = ptab + (size_t)(q * RL) * WT + w;
+#pragma unroll
+                    for (int rr = 0; rr < RL; ++rr) {
+                        const uint4 pv = prow[rr * WT];
+                        acc[3 * rr + 0] += popc_and4_csa(pv, x0) << sh;
+                        acc[3 * rr + 1] += popc_and4_csa(pv, x1) << sh;
+                        acc[3 * rr + 2] += popc_and4_csa(pv, x2) << sh;
+                    }
+                }
+            }
+            // mutual_information: this lane's 81 cells, summed over the group.
+            float hsum = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3 * RL; ++c) {
+                const uint32_t ca = acc[c] & 0xffffu;
+                const uint32_t cb = acc[c] >> 16;
+                const float ln = logtab[min(ca + cb, lt_max)];
+                hsum = fmaf((float)ca, ln - logtab[min(ca, lt_max)], hsum);
+                hsum = fmaf((float)cb, ln - logtab[min(cb, lt_max)], hsum);
+            }
+            float tot = 0.f;
+            const int gbase = slot * G;
+#pragma unroll
+            for (int i = 0; i < G; ++i) tot += __shfl_sync(FULL, hsum, (gbase + i) & 31);
+            const float score = fmaf(-tot, a.invN, a.hy);
+            const uint64_t rank = r + (uint64_t)slot;
+            if (MODE == MODE_SCORES) {
+                if (valid && q == 0) static_cast<float *>(a.dump)[rank - a.rank_begin] = score;
+            } else if (MODE == MODE_TABLES) {
+                if (valid) {
+                    uint32_t *o = static_cast<uint32_t *>(a.dump) + (rank - a.rank_begin) * (uint64_t)(2 * C) +
+                                  (size_t)q * RL * 3 * 2;
+#pragma unroll
+                    for (int c = 0; c < 3 * RL; ++c) { o[2 * c] = acc[c] & 0xffffu; o[2 * c + 1] = acc[c] >> 16; }
+                }
+            } else {
+                warp_offer(valid && q == 0, score, rank, lsc, lrk, L, st, lane);
+            }
+            r += (uint64_t)n;
+            cmb[K - 1] += (uint32_t)n;
+            if (r < r_end && cmb[K - 1] >= (uint32_t)a.S) {
+                int t = K - 2;
+                while (t > 0 && cmb[t] >= (uint32_t)(a.S - K + t)) --t;
+                cmb[t] += 1;
+                for (int u = t + 1; u < K; ++u) cmb[u] = cmb[u - 1] + 1;
+            }
+        }
+    }
+
+    if (MODE == MODE_TOPN) {
+        block_bitonic_desc(lscore_all, lrank_all, NW * L);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            a.list_score[(size_t)blockIdx.x * L + i] = lscore_all[i];
+            a.list_rank[(size_t)blockIdx.x * L + i] = lrank_all[i];
+        }
+    }
+}
+
 // Restricted pair counts for inclusion-exclusion: PR[i][j] (i < j) holds the
 // four cells with genotypes in {0,1} of SNPs i and j, packed cases |
 // controls << 16, in the order (0,0), (0,1), (1,0), (1,1).
@@ -609,6 +770,19 @@ void *pick_kernel(int k, int var, int G, int mode)
     FC_PICK(3, 1) FC_PICK(3, 2) FC_PICK(3, 4)
     FC_PICK(4, 1) FC_PICK(4, 2) FC_PICK(4, 4)
 #undef FC_PICK
+    // Orders 5 and 6: row-split kernel (lanes per combination fixed by k).
+    if (k == 5 || k == 6) {
+        if (mode == MODE_BATCH) return nullptr;
+        if (k == 5) {
+            if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search_rs<5, MODE_TOPN>);
+            if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search_rs<5, MODE_SCORES>);
+            if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search_rs<5, MODE_TABLES>);
+        } else {
+            if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search_rs<6, MODE_TOPN>);
+            if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search_rs<6, MODE_SCORES>);
+            if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search_rs<6, MODE_TABLES>);
+        }
+    }
     return nullptr;
 }
 
@@ -616,8 +790,9 @@ void *pick_kernel(int k, int var, int G, int mode)
 
 int effective_variant(int k, int var, int mode)
 {
+    (void)mode;
     if (var == VAR_IE && k <= 3) return VAR_IE;
-    if (var == VAR_JR && k >= 2) return VAR_JR;
+    if (var == VAR_JR && k >= 2 && k <= 4) return VAR_JR;
     return VAR_FULL;
 }
 

@@ -264,7 +264,7 @@ def test_invalid_inputs_are_rejected(fc):
         fc.fc_load(G, bph)
     assert e.value.status == fc.FC_EINVAL
     h = fc.fc_load(G, ph)
-    for k in (0, 6, 5):
+    for k in (0, 6, 7):          # k = 6 exceeds S = 5; 7 exceeds the maximum order
         with pytest.raises(fc.FiunchoError) as e:
             fc.fc_search(h, k, 3)
         assert e.value.status == fc.FC_EINVAL

@@ -109,3 +109,33 @@ def test_static_search_does_not_build_ie_tables(fc, monkeypatch):
     for x in (b, c):
         assert np.array_equal(a[0], x[0])
         np.testing.assert_allclose(a[1], x[1], rtol=1e-12)
+
+
+# ---- orders 5 and 6 (row-split sweep) -----------------------------------------
+
+@pytest.mark.parametrize("k,S,cases,controls", [(5, 9, 300, 211), (6, 9, 250, 199), (6, 8, 600, 700),
+                                                (5, 10, 1, 90)])
+def test_high_order_sweep_tables_exact(fc, k, S, cases, controls):
+    ds = make_dataset("hi", seed=600 + k + S, S=S, cases=cases, controls=controls, k=k, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    total = math.comb(S, k)
+    got = fc.fc_sweep_tables(h, k, 0, total)
+    combos = np.array(list(itertools.combinations(range(S), k)), dtype=np.uint32)
+    ref = oracle.tables(ds.genotypes, ds.phenotype, k, combos)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("k,S,planted", [(5, 16, (1, 4, 8, 11, 15)), (6, 13, (0, 2, 5, 7, 9, 12))])
+def test_high_order_search_matches_oracle(fc, k, S, planted):
+    from tests.parity_util import assert_topn_equal
+    ds = make_dataset("hi-s", seed=620 + k, S=S, cases=2048, controls=2048, k=k, top_n=30,
+                      planted=planted)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    g_idx, g_s = fc.fc_search(h, k, 30)
+    o_idx, o_s, tested = oracle.search(ds.genotypes, ds.phenotype, k, 30)
+    assert tested == math.comb(S, k)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, k, [c]), k)[0])
+    assert_topn_equal(g_idx, g_s, o_idx, o_s, score_of)
+    assert tuple(g_idx[0]) == planted

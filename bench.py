@@ -38,7 +38,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5", "P5", "P6"])
     p.add_argument("--c5-datasets", type=int, default=64)
     p.add_argument("--c5-replicates", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)

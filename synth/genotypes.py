@@ -211,6 +211,12 @@ CONFIGS = {
                planted=(12345, 33333), maf_range=(0.01, 0.5)),
     "C4": dict(seed=4, S=300, cases=3000, controls=3000, k=4, top_n=100,
                planted=(7, 150, 222, 291), maf_range=(0.05, 0.5)),
+    # Orders 5 and 6 at the SNP counts and 2048 samples of the paper's
+    # single-core measurements (Table 3), with a planted interaction.
+    "P5": dict(seed=6, S=152, cases=1024, controls=1024, k=5, top_n=100,
+               planted=(3, 40, 77, 110, 150), maf_range=(0.05, 0.5)),
+    "P6": dict(seed=7, S=76, cases=1024, controls=1024, k=6, top_n=100,
+               planted=(1, 14, 30, 45, 60, 75), maf_range=(0.05, 0.5)),
 }
 
 CONFIG_TITLES = {
@@ -219,6 +225,8 @@ CONFIG_TITLES = {
     "C3": "order-2 all-pairs, 40,000 SNPs x 8,192 samples (4,096/4,096), top 1,000",
     "C4": "order-4 exhaustive, 300 SNPs x 6,000 samples (3,000/3,000), top 100",
     "C5": "order-3 batched, 64 data sets x 20 permutation replicates, top 10 each",
+    "P5": "order-5 exhaustive, 152 SNPs x 2,048 samples (1,024/1,024), top 100",
+    "P6": "order-6 exhaustive, 76 SNPs x 2,048 samples (1,024/1,024), top 100",
 }
 
 

@@ -230,7 +230,11 @@ int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables);
  * 0 none yet, 1 prefix-table AND/POPC sweep counting all 3^k cells,
  * 2 tensor-core order-2 pairs, 3 prefix-table sweep counting the 2^k cells
  * with genotypes in {0,1} and deriving the rest exactly from lower-order
- * tables (inclusion-exclusion; k = 2, 3). */
+ * tables (inclusion-exclusion; k = 2, 3), 4 prefix-table sweep counting the
+ * cells whose last SNP has genotype 0 or 1 and deriving genotype 2 from the
+ * prefix's own table (k = 2..4), 5 (k-2)-prefix table extended by SNP pairs,
+ * all 3^k cells counted (k = 4..6).  Every kind yields the same exact
+ * tables. */
 int fc_last_search_kind(const fc_handle *h);
 
 /*

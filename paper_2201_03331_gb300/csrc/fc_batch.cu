@@ -24,7 +24,7 @@ int sweep_candidates(const Dataset &d, int k, int L, int mode, int var, TuneConf
     for (int gi = 0; gi < 3; ++gi) {
         const int G = Gs[gi];
         if (G == 4 && k < 4) continue;
-        if (G > 1 && k >= 5) continue;   // orders 5, 6 fix their lanes per combination
+        if (G > 1 && (k >= 5 || var == VAR_PX)) continue;   // these fix their lanes per combination
         for (int wi = 0; wi < 4; ++wi) {
             const int WT = WTs[wi];
             bool dup = false;
@@ -160,7 +160,7 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
             if (rc) return rc;
         }
     }
-    TuneConfig cfg = R.pick_config(k, L, MODE_TOPN, false, use_ie);
+    TuneConfig cfg = R.pick_config(k, L, MODE_TOPN, false, use_ie, false);
     if (!use_ie && cfg.var == VAR_IE) cfg.var = k >= 2 ? VAR_JR : VAR_FULL;
     // The batch kernel holds the ln table of the largest sample count.
     {

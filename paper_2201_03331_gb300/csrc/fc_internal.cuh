@@ -131,7 +131,9 @@ struct SearchArgs {
 //            per-SNP counts and restricted pair tables (k = 2, 3);
 //  VAR_JR:   popcount the cells whose extension-SNP genotype is 0 or 1
 //            (2 * 3^(k-1)); genotype 2 from the prefix's own table.
-enum SweepVariant { VAR_FULL = 0, VAR_IE = 1, VAR_JR = 2 };
+//  VAR_PX:   popcount all 3^k cells, with a (k-2)-prefix table extended by
+//            a SNP pair whose 9 rows are formed in registers (k = 4..6).
+enum SweepVariant { VAR_FULL = 0, VAR_IE = 1, VAR_JR = 2, VAR_PX = 3 };
 
 struct TuneConfig {
     int G;          // lanes per combination

@@ -243,7 +243,7 @@ float score_error_bound(int k, int64_t M)
 bool Dataset::ie_eligible(int k) const
 {
     const char *mode = getenv("FC_SWEEP");
-    if (mode && (strcmp(mode, "full") == 0 || strcmp(mode, "jr") == 0)) return false;
+    if (mode && (strcmp(mode, "full") == 0 || strcmp(mode, "jr") == 0 || strcmp(mode, "px") == 0)) return false;
     if (k != 2 && k != 3) return false;
     // The restricted pair table of order 3 holds S_pad^2 x 16 bytes.
     if (k == 3 && (double)S_pad * (double)S_pad * 16.0 > 2.0 * 1024 * 1024 * 1024) return false;
@@ -281,7 +281,7 @@ void Dataset::fill_search_args(SearchArgs &sa) const
     sa.nn = (uint32_t)M1 | ((uint32_t)M0 << 16);
 }
 
-TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allow_ie)
+TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allow_ie, bool allow_px)
 {
     TuneConfig c{};
     c.G = 1;
@@ -297,9 +297,23 @@ TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allo
     // FC_SWEEP=full|ie|jr forces one (where the order supports it).
     const char *force = getenv("FC_SWEEP");
     const bool ie_ok = allow_ie && ie_eligible(k) && (!no_alloc || (marg && (k != 3 || PR)));
-    c.var = ie_ok ? VAR_IE : (k >= 2 && k <= 4 ? VAR_JR : VAR_FULL);
+    // Orders 4 to 6 extend a (k-2)-prefix by SNP pairs (measured faster at
+    // order 4 than the extension-restricted count, although it counts more
+    // cells); the batched kernel has no pair-extension form.
+    if (ie_ok) c.var = VAR_IE;
+    else if (k >= 4 && k <= 6 && mode != MODE_BATCH && allow_px) c.var = VAR_PX;
+    else if (k >= 2 && k <= 4) c.var = VAR_JR;
+    else c.var = VAR_FULL;
     if (force && strcmp(force, "jr") == 0 && k >= 2 && k <= 4) c.var = VAR_JR;
+    if (force && strcmp(force, "px") == 0 && k >= 4 && k <= 6 && mode != MODE_BATCH && allow_px) c.var = VAR_PX;
     if (force && strcmp(force, "full") == 0) c.var = VAR_FULL;
+    if (c.var == VAR_PX) {
+        // Pair extension: 3^(k-2) rows of odd stride, the same 32 KiB bound.
+        const int rows = pow3(k - 2);
+        int wt = 64;
+        while (wt > 8 && (size_t)rows * (wt | 1) * 16 > 32768) wt >>= 1;
+        c.WT = std::min(Wt, wt);
+    }
     const int nws[3] = {8, 4, 2};
     bool found = false;
     for (int i = 0; i < 3 && !found; ++i) {
@@ -1000,6 +1014,7 @@ int fc_last_search_kind(const fc_handle *h)
     if (h->ds.last_list == 0) return 0;
     if (h->ds.last_sweep_var == VAR_IE) return 3;
     if (h->ds.last_sweep_var == VAR_JR) return 4;
+    if (h->ds.last_sweep_var == VAR_PX) return 5;
     return 1;
 }
 

@@ -78,8 +78,10 @@ struct Dataset {
     int load(const uint8_t *dG, const uint8_t *dph, int64_t S, int64_t M);
     int reserve_scratch(size_t bytes);
     // no_alloc: choose only among variants whose operands already exist and
-    // run no autotuning (which needs scratch).
-    TuneConfig pick_config(int k, int L, int mode, bool no_alloc = false, bool allow_ie = true);
+    // run no autotuning (which needs scratch).  allow_px = false keeps to the
+    // variants the batched kernel has.
+    TuneConfig pick_config(int k, int L, int mode, bool no_alloc = false, bool allow_ie = true,
+                           bool allow_px = true);
     // ext_scratch: if non-null, a device work area of ext_cap bytes used instead
     // of the handle's own (grown-on-demand) scratch allocation.
     int search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,

@@ -67,15 +67,23 @@ __device__ void block_bitonic_desc(float *s, uint64_t *r, int n)
     __syncthreads();
 }
 
-__host__ __device__ constexpr int prefix_rows(int k, int var) { return var == VAR_IE ? (1 << (k - 1)) : pow3(k - 1); }
+__host__ __device__ constexpr int prefix_rows(int k, int var)
+{
+    return var == VAR_IE ? (1 << (k - 1)) : var == VAR_PX ? pow3(k - 2) : pow3(k - 1);
+}
+
+// Row stride of a prefix table in uint4 words.  The pair-extension sweep
+// reads rows of G different lanes at once, so its stride is odd and those
+// rows fall in different banks.
+__host__ __device__ constexpr int prefix_stride(int var, int WT) { return var == VAR_PX ? (WT | 1) : WT; }
 
 // Shared-memory layout of the sweep kernels (uint4 units):
-//   [logtab: ceil((M+1)/4)] [prefix tables: NW * P * WT]
+//   [logtab: ceil((M+1)/4)] [prefix tables: NW * P * stride]
 //   [list ranks: NW * L (uint64)] [list scores: NW * L (float)]
 __host__ __device__ inline size_t search_smem_bytes(int k, int var, int NW, int WT, int L, int M)
 {
     const size_t lt = (size_t)((M + 1 + 3) / 4) * 16;
-    const size_t pt = (size_t)NW * prefix_rows(k, var) * WT * 16;
+    const size_t pt = (size_t)NW * prefix_rows(k, var) * prefix_stride(var, WT) * 16;
     const size_t ls = (size_t)NW * L * (8 + 4);
     return lt + pt + ls;
 }
@@ -668,6 +676,216 @@ __global__ void __launch_bounds__(256) k_search_rs(SearchArgs a, int NW, int WT)
     }
 }
 
+// Sweep over pair extensions for orders 4 to 6 (all 3^k cells).  A
+// combination is a (k-2)-prefix followed by a SNP pair (e, f).  The prefix
+// table (3^(k-2) rows) sits in shared memory and is rebuilt when the prefix
+// changes; the 9 rows of the pair (AND of a row of e with a row of f) are
+// formed in registers for every word.  Cell (p, a, b) of the table is the
+// count of prefix row p AND pair row (a, b), the same cell order as one SNP
+// at a time.  A (k-2)-prefix is followed by O(S^2) pairs instead of O(S)
+// single SNPs, so its table is rebuilt rarely even at large k, and every
+// prefix word read from shared memory feeds 9 counts instead of 3.  The
+// prefix rows are split over G = 3^(k-4) lanes per combination, 9 rows
+// each, so every lane keeps 81 counters; a group's lanes sum their partial
+// MI terms with shuffles.  Otherwise as k_search: per-warp rank ranges,
+// packed counters, FP32 MI, warp top list, block merge.
+template <int K, int MODE>
+__global__ void __launch_bounds__(256) k_search_px(SearchArgs a, int NW, int WT)
+{
+    constexpr int P = pow3(K - 2);         // prefix rows
+    constexpr int RL = 9;                  // prefix rows per lane
+    constexpr int G = P / RL;              // lanes per combination
+    constexpr int CPW = 32 / G;            // combinations per warp chunk
+    constexpr int C = pow3(K);
+    extern __shared__ uint4 smem4[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int L = MODE == MODE_TOPN ? a.L : 0;
+    const int slot = lane / G;
+    const int q = lane % G;
+    const uint32_t lt_max = (uint32_t)a.M;
+    const int RS = prefix_stride(VAR_PX, WT);
+
+    float *logtab = reinterpret_cast<float *>(smem4);
+    uint4 *ptab_all = smem4 + (a.M + 1 + 3) / 4;
+    uint4 *ptab = ptab_all + (size_t)warp * P * RS;
+    uint64_t *lrank_all = reinterpret_cast<uint64_t *>(ptab_all + (size_t)NW * P * RS);
+    float *lscore_all = reinterpret_cast<float *>(lrank_all + (size_t)NW * L);
+    float *lsc = lscore_all + (size_t)warp * L;
+    uint64_t *lrk = lrank_all + (size_t)warp * L;
+
+    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) logtab[i] = a.logtab[i];
+    if (MODE == MODE_TOPN) {
+        for (int i = threadIdx.x; i < NW * L; i += blockDim.x) {
+            lscore_all[i] = -FLT_MAX;
+            lrank_all[i] = NO_RANK;
+        }
+    }
+    __syncthreads();
+
+    const uint64_t total_warps = (uint64_t)gridDim.x * NW;
+    const uint64_t gw = (uint64_t)blockIdx.x * NW + warp;
+    const uint64_t R = a.rank_end - a.rank_begin;
+    uint64_t r = a.rank_begin + (uint64_t)(((unsigned __int128)R * gw) / total_warps);
+    const uint64_t r_end = a.rank_begin + (uint64_t)(((unsigned __int128)R * (gw + 1)) / total_warps);
+
+    WarpList st;
+    st.reset();
+    if (r < r_end) {
+        const uint32_t S = (uint32_t)a.S;
+        const int64_t Sp = a.S_pad;
+        uint32_t cmb[K];
+        unrank(a.S, K, r, cmb);
+        uint32_t cur[K - 2];
+        for (int t = 0; t < K - 2; ++t) cur[t] = 0xffffffffu;
+        int cur_tile = -1;
+        while (r < r_end) {
+            const uint32_t e0 = cmb[K - 2], f0 = cmb[K - 1];
+            // Pairs of this prefix from (e0, f0) on: the rest of row e0 and
+            // every pair with a larger first SNP.
+            const uint64_t m = S - 1 - e0;
+            const uint64_t left = (uint64_t)(S - f0) + m * (m - 1) / 2;
+            const int n = (int)min((uint64_t)CPW, min(left, r_end - r));
+            if (n <= 0) break;   // unreachable for a valid rank range; guards the loop
+            const bool valid = slot < n;
+            // This lane's pair: (e0, f0) advanced by `slot` lexicographic steps.
+            uint32_t e = e0, f = f0;
+            if (valid) {
+                f += (uint32_t)slot;
+                for (int it = 0; it < CPW && f >= S; ++it) {
+                    const uint32_t over = f - S;
+                    ++e;
+                    f = e + 1 + over;
+                }
+            }
+            bool same = true;
+            for (int t = 0; t < K - 2; ++t) same = same && (cur[t] == cmb[t]);
+
+            uint32_t acc[9 * RL];
+#pragma unroll
+            for (int c = 0; c < 9 * RL; ++c) acc[c] = 0;
+            for (int t0 = 0; t0 < a.Wt; t0 += WT) {
+                const int tw = min(WT, a.Wt - t0);
+                if (!(same && cur_tile == t0)) {
+                    __syncwarp();
+                    // combine: every task ANDs the rows of the first k-3
+                    // prefix SNPs for one word once and splits the result by
+                    // the genotype of the last prefix SNP (three rows).
+                    constexpr int P3 = P / 3;
+                    for (int task = lane; task < P3 * tw; task += 32) {
+                        const int pa = task / tw;
+                        const int w = task - pa * tw;
+                        const size_t base = (size_t)(t0 + w) * 3 * Sp;
+                        uint4 v = make_uint4(~0u, ~0u, ~0u, ~0u);
+                        int rem = pa;
+#pragma unroll
+                        for (int t = K - 4; t >= 0; --t) {
+                            const int g = rem % 3;
+                            rem /= 3;
+                            const uint4 x = jb_row(a.X, base, Sp, cmb[t], g);
+                            v.x &= x.x; v.y &= x.y; v.z &= x.z; v.w &= x.w;
+                        }
+#pragma unroll
+                        for (int g = 0; g < 3; ++g) {
+                            const uint4 x = jb_row(a.X, base, Sp, cmb[K - 3], g);
+                            ptab[(size_t)(pa * 3 + g) * RS + w] =
+                                make_uint4(v.x & x.x, v.y & x.y, v.z & x.z, v.w & x.w);
+                        }
+                    }
+                    __syncwarp();
+                    for (int t = 0; t < K - 2; ++t) cur[t] = cmb[t];
+                    cur_tile = t0;
+                    same = true;
+                }
+                // combine_and_popcount: this lane's 9 prefix rows against the
+                // pair's 9 rows.
+                for (int w = 0; w < tw; ++w) {
+                    const int wg = t0 + w;
+                    const uint4 *xb = a.X + (size_t)wg * 3 * Sp;
+                    uint4 xe[3], xf[3];
+#pragma unroll
+                    for (int g = 0; g < 3; ++g) {
+                        xe[g] = xb[(size_t)g * Sp + e];
+                        xf[g] = xb[(size_t)g * Sp + f];
+                    }
+                    uint4 pr[9];
+#pragma unroll
+                    for (int ga = 0; ga < 3; ++ga)
+#pragma unroll
+                        for (int gb = 0; gb < 3; ++gb)
+                            pr[3 * ga + gb] = make_uint4(xe[ga].x & xf[gb].x, xe[ga].y & xf[gb].y,
+                                                         xe[ga].z & xf[gb].z, xe[ga].w & xf[gb].w);
+                    const int sh = wg < a.W0 ? 0 : 16;
+                    const uint4 *prow = ptab + (size_t)(q * RL) * RS + w;
+#pragma unroll
+                    for (int rr = 0; rr < RL; ++rr) {
+                        const uint4 pv = prow[rr * RS];
+#pragma unroll
+                        for (int c = 0; c < 9; ++c) acc[9 * rr + c] += popc_and4_csa(pv, pr[c]) << sh;
+                    }
+                }
+            }
+            // mutual_information: this lane's 81 cells, summed over the group.
+            float hsum = 0.f;
+#pragma unroll
+            for (int c = 0; c < 9 * RL; ++c) {
+                const uint32_t ca = acc[c] & 0xffffu;
+                const uint32_t cb = acc[c] >> 16;
+                const float ln = logtab[min(ca + cb, lt_max)];
+                hsum = fmaf((float)ca, ln - logtab[min(ca, lt_max)], hsum);
+                hsum = fmaf((float)cb, ln - logtab[min(cb, lt_max)], hsum);
+            }
+            float tot = 0.f;
+            const int gbase = slot * G;
+#pragma unroll
+            for (int i = 0; i < G; ++i) tot += __shfl_sync(FULL, hsum, (gbase + i) & 31);
+            const float score = fmaf(-tot, a.invN, a.hy);
+            const uint64_t rank = r + (uint64_t)slot;
+            if (MODE == MODE_SCORES) {
+                if (valid && q == 0) static_cast<float *>(a.dump)[rank - a.rank_begin] = score;
+            } else if (MODE == MODE_TABLES) {
+                if (valid) {
+                    // Lane q holds cells [81 q, 81 q + 81) of the table.
+                    uint32_t *o = static_cast<uint32_t *>(a.dump) + (rank - a.rank_begin) * (uint64_t)(2 * C) +
+                                  (size_t)q * RL * 9 * 2;
+#pragma unroll
+                    for (int c = 0; c < 9 * RL; ++c) { o[2 * c] = acc[c] & 0xffffu; o[2 * c + 1] = acc[c] >> 16; }
+                }
+            } else {
+                warp_offer(valid && q == 0, score, rank, lsc, lrk, L, st, lane);
+            }
+            r += (uint64_t)n;
+            if (r < r_end) {
+                if ((uint64_t)n == left) {
+                    // Prefix exhausted: lexicographic successor at the last
+                    // prefix position.
+                    int t = K - 3;
+                    while (t > 0 && cmb[t] >= S - K + (uint32_t)t) --t;
+                    cmb[t] += 1;
+                    for (int u = t + 1; u < K; ++u) cmb[u] = cmb[u - 1] + 1;
+                } else {
+                    uint32_t ne = e0, nf = f0 + (uint32_t)n;
+                    for (int it = 0; it < CPW && nf >= S; ++it) {
+                        const uint32_t over = nf - S;
+                        ++ne;
+                        nf = ne + 1 + over;
+                    }
+                    cmb[K - 2] = ne;
+                    cmb[K - 1] = nf;
+                }
+            }
+        }
+    }
+
+    if (MODE == MODE_TOPN) {
+        block_bitonic_desc(lscore_all, lrank_all, NW * L);
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            a.list_score[(size_t)blockIdx.x * L + i] = lscore_all[i];
+            a.list_rank[(size_t)blockIdx.x * L + i] = lrank_all[i];
+        }
+    }
+}
+
 // Restricted pair counts for inclusion-exclusion: PR[i][j] (i < j) holds the
 // four cells with genotypes in {0,1} of SNPs i and j, packed cases |
 // controls << 16, in the order (0,0), (0,1), (1,0), (1,1).
@@ -754,6 +972,18 @@ void *search_kernel_ptr(int mode)
 // given order does not support fall back to the full count.
 void *pick_kernel(int k, int var, int G, int mode)
 {
+    // Pair-extension sweep, orders 4 to 6 (lanes per combination fixed by k).
+    if (var == VAR_PX && mode != MODE_BATCH) {
+#define FC_PICK_PX(KK)                                                                        \
+        if (k == KK) {                                                                        \
+            if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search_px<KK, MODE_TOPN>);     \
+            if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search_px<KK, MODE_SCORES>); \
+            if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search_px<KK, MODE_TABLES>); \
+        }
+        FC_PICK_PX(4) FC_PICK_PX(5) FC_PICK_PX(6)
+#undef FC_PICK_PX
+        return nullptr;
+    }
 #define FC_PICK(KK, GG)                                                                      \
     if (k == KK && G == GG) {                                                                \
         if (mode == MODE_BATCH) {                                                            \
@@ -790,7 +1020,10 @@ void *pick_kernel(int k, int var, int G, int mode)
 
 int effective_variant(int k, int var, int mode)
 {
-    (void)mode;
+    if (var == VAR_PX) {
+        if (k >= 4 && k <= 6 && mode != MODE_BATCH) return VAR_PX;
+        var = (k >= 2 && k <= 4) ? VAR_JR : VAR_FULL;
+    }
     if (var == VAR_IE && k <= 3) return VAR_IE;
     if (var == VAR_JR && k >= 2 && k <= 4) return VAR_JR;
     return VAR_FULL;

@@ -1,5 +1,9 @@
-"""The sweep's two counting variants (all 3^k cells, or the 2^k cells with
-genotypes in {0,1} plus exact inclusion-exclusion) against the oracle."""
+"""The sweep's counting variants against the oracle: all 3^k cells one
+extension SNP at a time (full), the 2^k cells with genotypes in {0,1} plus
+exact inclusion-exclusion (ie, k = 2, 3), the cells whose extension SNP has
+genotype 0 or 1 plus the prefix's own table (jr, k = 2..4), and all 3^k cells
+from a (k-2)-prefix extended by SNP pairs (px, k = 4..6).  Every variant must
+produce bit-identical tables and the same top list."""
 import itertools
 import math
 
@@ -22,7 +26,7 @@ def fc():
     return fcm
 
 
-@pytest.fixture(params=["full", "ie", "jr"])
+@pytest.fixture(params=["full", "ie", "jr", "px"])
 def variant(request, monkeypatch):
     if request.param == "ie":
         monkeypatch.delenv("FC_SWEEP", raising=False)
@@ -83,12 +87,16 @@ def test_order4_variants_agree(fc, monkeypatch):
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     monkeypatch.delenv("FC_SWEEP", raising=False)
     a = fc.fc_search(h, 4, 60)
-    assert fc.fc_last_search_kind(h) == 4      # order 4 counts 2 * 3^3 cells by default
+    assert fc.fc_last_search_kind(h) == 5      # order 4 extends 2-prefixes by pairs by default
     monkeypatch.setenv("FC_SWEEP", "full")
     b = fc.fc_search(h, 4, 60)
     assert fc.fc_last_search_kind(h) == 1
-    assert np.array_equal(a[0], b[0])
-    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    monkeypatch.setenv("FC_SWEEP", "jr")
+    c = fc.fc_search(h, 4, 60)
+    assert fc.fc_last_search_kind(h) == 4
+    for x in (b, c):
+        assert np.array_equal(a[0], x[0])
+        np.testing.assert_allclose(a[1], x[1], rtol=1e-12)
     assert tuple(a[0][0]) == (2, 9, 20, 31)
 
 
@@ -111,11 +119,23 @@ def test_static_search_does_not_build_ie_tables(fc, monkeypatch):
         np.testing.assert_allclose(a[1], x[1], rtol=1e-12)
 
 
-# ---- orders 5 and 6 (row-split sweep) -----------------------------------------
+# ---- orders 5 and 6: pair-extension sweep (default) and row-split sweep -------
+
+@pytest.fixture(params=["px", "full"])
+def hi_variant(request, monkeypatch):
+    if request.param == "px":
+        monkeypatch.delenv("FC_SWEEP", raising=False)
+    else:
+        monkeypatch.setenv("FC_SWEEP", request.param)
+    return request.param
+
 
 @pytest.mark.parametrize("k,S,cases,controls", [(5, 9, 300, 211), (6, 9, 250, 199), (6, 8, 600, 700),
-                                                (5, 10, 1, 90)])
-def test_high_order_sweep_tables_exact(fc, k, S, cases, controls):
+                                                (5, 10, 1, 90), (6, 6, 40, 33), (5, 5, 20, 0),
+                                                (4, 23, 700, 1300), (5, 14, 3000, 100),
+                                                (6, 8, 3000, 1100), (4, 12, 6000, 3000)])
+def test_high_order_sweep_tables_exact(fc, hi_variant, monkeypatch, k, S, cases, controls):
+    """Includes sample counts whose words span several prefix-table tiles."""
     ds = make_dataset("hi", seed=600 + k + S, S=S, cases=cases, controls=controls, k=k, top_n=5)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     total = math.comb(S, k)
@@ -123,10 +143,27 @@ def test_high_order_sweep_tables_exact(fc, k, S, cases, controls):
     combos = np.array(list(itertools.combinations(range(S), k)), dtype=np.uint32)
     ref = oracle.tables(ds.genotypes, ds.phenotype, k, combos)
     assert np.array_equal(got, ref)
+    if k >= 5:
+        fc.fc_search(h, k, 3)
+        assert fc.fc_last_search_kind(h) == (5 if hi_variant == "px" else 1)
+
+
+@pytest.mark.parametrize("k,S", [(5, 40), (6, 24)])
+def test_high_order_sweep_tables_windows(fc, hi_variant, k, S):
+    """Windows that start and end inside prefix groups and cross them."""
+    ds = make_dataset("hiw", seed=640 + k, S=S, cases=700, controls=900, k=k, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    total = math.comb(S, k)
+    rng = np.random.default_rng(41 + k)
+    for start in [0, int(rng.integers(1, total - 3000)), int(rng.integers(1, total - 3000)), total - 1777]:
+        n = min(1777, total - start)
+        got = fc.fc_sweep_tables(h, k, start, n)
+        combos = np.array([fc.fc_unrank(S, k, r) for r in range(start, start + n)], dtype=np.uint32)
+        assert np.array_equal(got, oracle.tables(ds.genotypes, ds.phenotype, k, combos)), start
 
 
 @pytest.mark.parametrize("k,S,planted", [(5, 16, (1, 4, 8, 11, 15)), (6, 13, (0, 2, 5, 7, 9, 12))])
-def test_high_order_search_matches_oracle(fc, k, S, planted):
+def test_high_order_search_matches_oracle(fc, hi_variant, k, S, planted):
     from tests.parity_util import assert_topn_equal
     ds = make_dataset("hi-s", seed=620 + k, S=S, cases=2048, controls=2048, k=k, top_n=30,
                       planted=planted)

@@ -45,7 +45,33 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target duration of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--snps", type=int, default=None,
+                   help="keep only the workload's first N SNPs (smaller cases for profiler captures)")
     return p.parse_args()
+
+
+class NvtxRange:
+    """An NVTX range around the timed steps, so that a profiler can select
+    the launches inside it; a no-op where NVTX is unavailable."""
+
+    def __init__(self, name):
+        self.name = name
+        self.on = False
+
+    def __enter__(self):
+        try:
+            import torch
+            torch.cuda.nvtx.range_push(self.name)
+            self.on = True
+        except Exception:
+            pass
+        return self
+
+    def __exit__(self, *exc):
+        if self.on:
+            import torch
+            torch.cuda.nvtx.range_pop()
+        return False
 
 
 def dist_info():
@@ -242,7 +268,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_title(args.workload), "k": k, "snps": ds.S, "samples": ds.M,
+        "config": {"workload": workload_title(args.workload) if not args.snps else
+                   f"{args.workload} cut to its first {ds.S} SNPs (profiling case)",
+                   "k": k, "snps": ds.S, "samples": ds.M,
                    "top_n": ds.top_n, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -268,9 +296,12 @@ def run_ours(args):
     fcbuild.build()
     cfg = dict(CONFIGS[args.workload])
     S = cfg.pop("S")
+    if args.snps:
+        S = min(S, args.snps)
+        cfg["planted"] = tuple(p for p in cfg["planted"] if p < S)
     if world > 1:
         cfg["seed"] = cfg["seed"] + 1000 * rank      # independent data set per rank
-    ds = make_dataset(args.workload, S=S, **cfg) if world > 1 else make_config(args.workload)
+    ds = make_dataset(args.workload, S=S, **cfg) if world > 1 else make_config(args.workload, args.snps)
     k, top_n = ds.k, ds.top_n
     total = math.comb(ds.S, k)
 
@@ -290,13 +321,14 @@ def run_ours(args):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                       # L2 flush between timed steps
-        ev[i][0].record(stream)
-        idx, score = fc.fc_search(h, k, top_n)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
+    with NvtxRange("timed"):
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                       # L2 flush between timed steps
+            ev[i][0].record(stream)
+            idx, score = fc.fc_search(h, k, top_n)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
     barrier(dist)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -374,7 +406,9 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": workload_title(args.workload), "k": k, "snps": ds.S, "samples": ds.M,
+        "config": {"workload": workload_title(args.workload) if not args.snps else
+                   f"{args.workload} cut to its first {ds.S} SNPs (profiling case)",
+                   "k": k, "snps": ds.S, "samples": ds.M,
                    "cases": ds.cases, "controls": ds.controls, "top_n": top_n,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "one independent data set per GPU" if world > 1 else "single GPU"},
@@ -424,13 +458,14 @@ def run_batch(args):
     clocks = ClockSampler(0)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        ev[i][0].record(stream)
-        out = fc.fc_search_batch(h, k, top_n)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
+    with NvtxRange("timed"):
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            out = fc.fc_search_batch(h, k, top_n)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
     clk = clocks.stop()
     sweep_ms, sweeps, launches = fc.fc_timing(h, 0)
     step_ms = [a.elapsed_time(b) for a, b in ev]

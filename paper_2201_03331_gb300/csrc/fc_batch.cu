@@ -22,9 +22,16 @@ int sweep_candidates(const Dataset &d, int k, int L, int mode, int var, TuneConf
     const int NWs[3] = {8, 4, 2};
     const int WTs[4] = {std::min(d.Wt, 64), std::min(d.Wt, 32), std::min(d.Wt, 16), std::min(d.Wt, 8)};
     for (int gi = 0; gi < 3; ++gi) {
-        const int G = Gs[gi];
-        if (G == 4 && k < 4) continue;
-        if (G > 1 && (k >= 5 || var == VAR_PX)) continue;   // these fix their lanes per combination
+        int G = Gs[gi];
+        if (var == VAR_PX) {
+            // Pair extension: G = 1 keeps 81 counters per lane, G = 3 splits
+            // the genotype of the first pair SNP over lanes (27 counters).
+            if (G == 4) continue;
+            if (G == 2) G = 3;
+        } else {
+            if (G == 4 && k < 4) continue;
+            if (G > 1 && k >= 5) continue;   // the row-split kernel fixes its lanes per combination
+        }
         for (int wi = 0; wi < 4; ++wi) {
             const int WT = WTs[wi];
             bool dup = false;

@@ -308,7 +308,9 @@ TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allo
     if (force && strcmp(force, "px") == 0 && k >= 4 && k <= 6 && mode != MODE_BATCH && allow_px) c.var = VAR_PX;
     if (force && strcmp(force, "full") == 0) c.var = VAR_FULL;
     if (c.var == VAR_PX) {
-        // Pair extension: 3^(k-2) rows of odd stride, the same 32 KiB bound.
+        // Pair extension: 27 counters per lane; 3^(k-2) rows of odd stride,
+        // the same 32 KiB bound.
+        c.G = 3;
         const int rows = pow3(k - 2);
         int wt = 64;
         while (wt > 8 && (size_t)rows * (wt | 1) * 16 > 32768) wt >>= 1;
@@ -338,6 +340,21 @@ TuneConfig Dataset::pick_config(int k, int L, int mode, bool no_alloc, bool allo
         const char *at = getenv("FC_AUTOTUNE");
         const bool enabled = !(at && strcmp(at, "0") == 0);
         if (enabled && (int64_t)binom(S, k) >= ((int64_t)1 << 24)) c = tuned_config(*this, k, L, c, no_alloc);
+    }
+    // FC_SWEEP_CONFIG=G,NW,WT forces lanes per combination, warps per CTA
+    // and tile words (kept only if that configuration fits the device).
+    if (const char *fc = getenv("FC_SWEEP_CONFIG")) {
+        TuneConfig f = c;
+        if (sscanf(fc, "%d,%d,%d", &f.G, &f.NW, &f.WT) == 3 && f.G >= 1 && f.WT >= 1 &&
+            (f.NW == 1 || f.NW == 2 || f.NW == 4 || f.NW == 8)) {
+            f.WT = std::min(f.WT, Wt);
+            size_t smem = 0;
+            const int nb = search_max_blocks_per_sm(k, f, mode, L, (int)M, &smem);
+            if (nb > 0) {
+                f.grid = nb * sms;
+                c = f;
+            }
+        }
     }
     return c;
 }

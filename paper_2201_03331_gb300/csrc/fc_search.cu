@@ -679,23 +679,28 @@ __global__ void __launch_bounds__(256) k_search_rs(SearchArgs a, int NW, int WT)
 // Sweep over pair extensions for orders 4 to 6 (all 3^k cells).  A
 // combination is a (k-2)-prefix followed by a SNP pair (e, f).  The prefix
 // table (3^(k-2) rows) sits in shared memory and is rebuilt when the prefix
-// changes; the 9 rows of the pair (AND of a row of e with a row of f) are
+// changes; the rows of the pair (AND of a row of e with a row of f) are
 // formed in registers for every word.  Cell (p, a, b) of the table is the
 // count of prefix row p AND pair row (a, b), the same cell order as one SNP
 // at a time.  A (k-2)-prefix is followed by O(S^2) pairs instead of O(S)
-// single SNPs, so its table is rebuilt rarely even at large k, and every
-// prefix word read from shared memory feeds 9 counts instead of 3.  The
-// prefix rows are split over G = 3^(k-4) lanes per combination, 9 rows
-// each, so every lane keeps 81 counters; a group's lanes sum their partial
-// MI terms with shuffles.  Otherwise as k_search: per-warp rank ranges,
-// packed counters, FP32 MI, warp top list, block merge.
-template <int K, int MODE>
+// single SNPs, so its table is rebuilt rarely even at large k, and a prefix
+// word read from shared memory feeds 3 GA counts.
+//
+// The cells of a combination are split over G lanes: a lane owns RL prefix
+// rows and GA of the three genotypes a of e, so it keeps RL * GA * 3
+// counters; G = (3^(k-2) / RL) * (3 / GA).  Fewer counters per lane means
+// fewer registers and more resident warps.  A group's lanes sum their
+// partial MI terms with shuffles.  Otherwise as k_search: per-warp rank
+// ranges, packed counters, FP32 MI, warp top list, block merge.
+template <int K, int MODE, int RL, int GA>
 __global__ void __launch_bounds__(256) k_search_px(SearchArgs a, int NW, int WT)
 {
     constexpr int P = pow3(K - 2);         // prefix rows
-    constexpr int RL = 9;                  // prefix rows per lane
-    constexpr int G = P / RL;              // lanes per combination
+    constexpr int AG = 3 / GA;             // lanes splitting the genotype of e
+    constexpr int G = (P / RL) * AG;       // lanes per combination
+    static_assert(P % RL == 0 && 3 % GA == 0 && G <= 32, "lane split");
     constexpr int CPW = 32 / G;            // combinations per warp chunk
+    constexpr int NC = RL * GA * 3;        // counters per lane
     constexpr int C = pow3(K);
     extern __shared__ uint4 smem4[];
     const int lane = threadIdx.x & 31;
@@ -703,6 +708,8 @@ __global__ void __launch_bounds__(256) k_search_px(SearchArgs a, int NW, int WT)
     const int L = MODE == MODE_TOPN ? a.L : 0;
     const int slot = lane / G;
     const int q = lane % G;
+    const int qp = q / AG;                 // prefix rows [qp * RL, qp * RL + RL)
+    const int qa = q % AG;                 // genotypes of e [qa * GA, qa * GA + GA)
     const uint32_t lt_max = (uint32_t)a.M;
     const int RS = prefix_stride(VAR_PX, WT);
 
@@ -761,9 +768,9 @@ __global__ void __launch_bounds__(256) k_search_px(SearchArgs a, int NW, int WT)
             bool same = true;
             for (int t = 0; t < K - 2; ++t) same = same && (cur[t] == cmb[t]);
 
-            uint32_t acc[9 * RL];
+            uint32_t acc[NC];
 #pragma unroll
-            for (int c = 0; c < 9 * RL; ++c) acc[c] = 0;
+            for (int c = 0; c < NC; ++c) acc[c] = 0;
             for (int t0 = 0; t0 < a.Wt; t0 += WT) {
                 const int tw = min(WT, a.Wt - t0);
                 if (!(same && cur_tile == t0)) {
@@ -797,38 +804,38 @@ __global__ void __launch_bounds__(256) k_search_px(SearchArgs a, int NW, int WT)
                     cur_tile = t0;
                     same = true;
                 }
-                // combine_and_popcount: this lane's 9 prefix rows against the
-                // pair's 9 rows.
+                // combine_and_popcount: this lane's RL prefix rows against
+                // its 3 GA pair rows.
                 for (int w = 0; w < tw; ++w) {
                     const int wg = t0 + w;
                     const uint4 *xb = a.X + (size_t)wg * 3 * Sp;
-                    uint4 xe[3], xf[3];
+                    uint4 xf[3];
 #pragma unroll
-                    for (int g = 0; g < 3; ++g) {
-                        xe[g] = xb[(size_t)g * Sp + e];
-                        xf[g] = xb[(size_t)g * Sp + f];
-                    }
-                    uint4 pr[9];
+                    for (int g = 0; g < 3; ++g) xf[g] = xb[(size_t)g * Sp + f];
+                    uint4 pr[3 * GA];
 #pragma unroll
-                    for (int ga = 0; ga < 3; ++ga)
+                    for (int ai = 0; ai < GA; ++ai) {
+                        const uint4 xe = xb[(size_t)(qa * GA + ai) * Sp + e];
 #pragma unroll
                         for (int gb = 0; gb < 3; ++gb)
-                            pr[3 * ga + gb] = make_uint4(xe[ga].x & xf[gb].x, xe[ga].y & xf[gb].y,
-                                                         xe[ga].z & xf[gb].z, xe[ga].w & xf[gb].w);
+                            pr[3 * ai + gb] = make_uint4(xe.x & xf[gb].x, xe.y & xf[gb].y,
+                                                         xe.z & xf[gb].z, xe.w & xf[gb].w);
+                    }
                     const int sh = wg < a.W0 ? 0 : 16;
-                    const uint4 *prow = ptab + (size_t)(q * RL) * RS + w;
+                    const uint4 *prow = ptab + (size_t)(qp * RL) * RS + w;
 #pragma unroll
                     for (int rr = 0; rr < RL; ++rr) {
                         const uint4 pv = prow[rr * RS];
 #pragma unroll
-                        for (int c = 0; c < 9; ++c) acc[9 * rr + c] += popc_and4_csa(pv, pr[c]) << sh;
+                        for (int c = 0; c < 3 * GA; ++c)
+                            acc[3 * GA * rr + c] += popc_and4_csa(pv, pr[c]) << sh;
                     }
                 }
             }
-            // mutual_information: this lane's 81 cells, summed over the group.
+            // mutual_information: this lane's cells, summed over the group.
             float hsum = 0.f;
 #pragma unroll
-            for (int c = 0; c < 9 * RL; ++c) {
+            for (int c = 0; c < NC; ++c) {
                 const uint32_t ca = acc[c] & 0xffffu;
                 const uint32_t cb = acc[c] >> 16;
                 const float ln = logtab[min(ca + cb, lt_max)];
@@ -845,11 +852,18 @@ __global__ void __launch_bounds__(256) k_search_px(SearchArgs a, int NW, int WT)
                 if (valid && q == 0) static_cast<float *>(a.dump)[rank - a.rank_begin] = score;
             } else if (MODE == MODE_TABLES) {
                 if (valid) {
-                    // Lane q holds cells [81 q, 81 q + 81) of the table.
-                    uint32_t *o = static_cast<uint32_t *>(a.dump) + (rank - a.rank_begin) * (uint64_t)(2 * C) +
-                                  (size_t)q * RL * 9 * 2;
+                    uint32_t *o = static_cast<uint32_t *>(a.dump) + (rank - a.rank_begin) * (uint64_t)(2 * C);
 #pragma unroll
-                    for (int c = 0; c < 9 * RL; ++c) { o[2 * c] = acc[c] & 0xffffu; o[2 * c + 1] = acc[c] >> 16; }
+                    for (int rr = 0; rr < RL; ++rr)
+#pragma unroll
+                        for (int ai = 0; ai < GA; ++ai)
+#pragma unroll
+                            for (int gb = 0; gb < 3; ++gb) {
+                                const uint32_t v = acc[3 * GA * rr + 3 * ai + gb];
+                                const int cell = (qp * RL + rr) * 9 + (qa * GA + ai) * 3 + gb;
+                                o[2 * cell] = v & 0xffffu;
+                                o[2 * cell + 1] = v >> 16;
+                            }
                 }
             } else {
                 warp_offer(valid && q == 0, score, rank, lsc, lrk, L, st, lane);
@@ -974,13 +988,18 @@ void *pick_kernel(int k, int var, int G, int mode)
 {
     // Pair-extension sweep, orders 4 to 6 (lanes per combination fixed by k).
     if (var == VAR_PX && mode != MODE_BATCH) {
-#define FC_PICK_PX(KK)                                                                        \
-        if (k == KK) {                                                                        \
-            if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search_px<KK, MODE_TOPN>);     \
-            if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search_px<KK, MODE_SCORES>); \
-            if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search_px<KK, MODE_TABLES>); \
-        }
-        FC_PICK_PX(4) FC_PICK_PX(5) FC_PICK_PX(6)
+        // G selects the lane split: 1 = 81 counters per lane (prefix rows
+        // split), otherwise 27 (prefix rows and the genotype of e split).
+#define FC_PICK_PX(KK, RLL, GAA)                                                                      \
+        if (mode == MODE_TOPN) return reinterpret_cast<void *>(&k_search_px<KK, MODE_TOPN, RLL, GAA>);     \
+        if (mode == MODE_SCORES) return reinterpret_cast<void *>(&k_search_px<KK, MODE_SCORES, RLL, GAA>); \
+        if (mode == MODE_TABLES) return reinterpret_cast<void *>(&k_search_px<KK, MODE_TABLES, RLL, GAA>);
+        if (k == 4 && G == 1) { FC_PICK_PX(4, 9, 3) }
+        if (k == 4) { FC_PICK_PX(4, 9, 1) }
+        if (k == 5 && G == 1) { FC_PICK_PX(5, 9, 3) }
+        if (k == 5) { FC_PICK_PX(5, 9, 1) }
+        if (k == 6 && G == 1) { FC_PICK_PX(6, 9, 3) }
+        if (k == 6) { FC_PICK_PX(6, 9, 1) }
 #undef FC_PICK_PX
         return nullptr;
     }

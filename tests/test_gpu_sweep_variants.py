@@ -121,12 +121,16 @@ def test_static_search_does_not_build_ie_tables(fc, monkeypatch):
 
 # ---- orders 5 and 6: pair-extension sweep (default) and row-split sweep -------
 
-@pytest.fixture(params=["px", "full"])
+@pytest.fixture(params=["px", "px-g1", "full"])
 def hi_variant(request, monkeypatch):
-    if request.param == "px":
-        monkeypatch.delenv("FC_SWEEP", raising=False)
-    else:
-        monkeypatch.setenv("FC_SWEEP", request.param)
+    """px: pair extension with 27 counters per lane (default); px-g1: pair
+    extension with 81 counters per lane; full: row-split kernel."""
+    monkeypatch.delenv("FC_SWEEP", raising=False)
+    monkeypatch.delenv("FC_SWEEP_CONFIG", raising=False)
+    if request.param == "px-g1":
+        monkeypatch.setenv("FC_SWEEP_CONFIG", "1,4,16")
+    elif request.param == "full":
+        monkeypatch.setenv("FC_SWEEP", "full")
     return request.param
 
 
@@ -145,7 +149,7 @@ def test_high_order_sweep_tables_exact(fc, hi_variant, monkeypatch, k, S, cases,
     assert np.array_equal(got, ref)
     if k >= 5:
         fc.fc_search(h, k, 3)
-        assert fc.fc_last_search_kind(h) == (5 if hi_variant == "px" else 1)
+        assert fc.fc_last_search_kind(h) == (1 if hi_variant == "full" else 5)
 
 
 @pytest.mark.parametrize("k,S", [(5, 40), (6, 24)])

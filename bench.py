@@ -365,17 +365,18 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
     sweep_avg_s = (sweep_ms / max(sweeps, 1)) / 1e3
     kind = fc.fc_last_search_kind(h)
-    if kind == 2:
-        # Tensor-core contraction: 4 cells ({0,1} x {0,1}) x M samples x 2
-        # FLOP per pair; fp8 peak = measured dense bf16 x 2 (nominal ratio).
-        flops = math.comb(ds.S, 2) * 4 * 2 * (ds.cases + ds.controls)
+    if kind in (2, 6):
+        # Tensor-core contraction: 2^k cells (genotypes in {0,1}) x M
+        # samples x 2 FLOP per combination; fp8 peak = measured dense bf16 x 2
+        # (nominal ratio).
+        flops = math.comb(ds.S, k) * (2 ** k) * 2 * (ds.cases + ds.controls)
         bf16 = peaks.get("bf16_tflops")
         peak = 2.0 * float(bf16) if bf16 else 2.0 * 1900.0
         achieved = flops / sweep_avg_s / 1e12 if sweeps else None
-        kernel_key = f"k_pairs_tc<TOPN> {args.workload}"
+        kernel_key = f"{'k_pairs_tc' if kind == 2 else 'k_triples_tc'}<TOPN> {args.workload}"
         roofline = {"bound": "tensor", "kernel": kernel_key, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                    "traffic": traffic_for(kernel_key, "fc_pairs_tc.cu"),
+                    "traffic": traffic_for(kernel_key, "fc_pairs_tc.cu" if kind == 2 else "fc_triples_tc.cu"),
                     "peak_basis": ("2 x measured dense bf16 (fp8 e4m3 kind::f8f6f4)" if bf16
                                    else "2 x fallback 1.9 PFLOP/s bf16"),
                     "sweep_ms_per_launch": 1e3 * sweep_avg_s,

@@ -226,6 +226,22 @@ int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64
  */
 int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables);
 
+/*
+ * fc_triples_dense - every order-3 table or FP32 score computed by the
+ * tensor-core triple kernel (the k = 3 path fc_search takes for S >= 384):
+ * the 8 cells with genotypes in {0,1} from the tensor-core contraction of
+ * pair rows with SNP rows, the other 19 by inclusion-exclusion.  A parity
+ * hook for the contraction and its epilogue (Section "Computing the
+ * contingency tables"; mutual information as in fc_search).
+ * scores : host float [C(S,3)] or NULL, indexed by lexicographic rank
+ *          (S <= 512).
+ * tables : host uint32 [C(S,3)][27][2] or NULL, indexed by rank, in the
+ *          layout of fc_tables (S <= 160).
+ * Needs both classes non-empty.  Returns FC_OK, FC_EINVAL, FC_ERANGE,
+ * FC_ENOMEM, FC_ECUDA or FC_ETIMEOUT.
+ */
+int fc_triples_dense(fc_handle *h, float *scores, uint32_t *tables);
+
 /* fc_last_search_kind - which sweep the last fc_search on h ran:
  * 0 none yet, 1 prefix-table AND/POPC sweep counting all 3^k cells,
  * 2 tensor-core order-2 pairs, 3 prefix-table sweep counting the 2^k cells
@@ -233,8 +249,9 @@ int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables);
  * tables (inclusion-exclusion; k = 2, 3), 4 prefix-table sweep counting the
  * cells whose last SNP has genotype 0 or 1 and deriving genotype 2 from the
  * prefix's own table (k = 2..4), 5 (k-2)-prefix table extended by SNP pairs,
- * all 3^k cells counted (k = 4..6).  Every kind yields the same exact
- * tables. */
+ * all 3^k cells counted (k = 4..6), 6 tensor-core order-3 contraction of
+ * pair rows with SNP rows (8 cells counted, 19 derived).  Every kind yields
+ * the same exact tables. */
 int fc_last_search_kind(const fc_handle *h);
 
 /*

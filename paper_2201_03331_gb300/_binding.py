@@ -44,6 +44,7 @@ _SIGNATURES = {
     "fc_scores": ([P, i32, u64, i64, P], i32),
     "fc_info": ([P, P, P, P, P], i32),
     "fc_pairs_dense": ([P, P, P], i32),
+    "fc_triples_dense": ([P, P, P], i32),
     "fc_load_batch": ([i32, P, P, P, P, i32, P], i32),
     "fc_search_batch": ([P, i32, i64, P, P, P], i32),
     "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
@@ -192,6 +193,19 @@ def fc_pairs_dense(h: Handle, scores: bool = True, tables: bool = False):
     tb = np.zeros((S, S, 9, 2), dtype=np.uint32) if tables else None
     _check(library().fc_pairs_dense(h.ptr, _ptr(sc) if sc is not None else None,
                                     _ptr(tb) if tb is not None else None), "fc_pairs_dense")
+    return sc, tb
+
+
+def fc_triples_dense(h: Handle, scores: bool = True, tables: bool = False):
+    """Dense order-3 output of the tensor-core kernel, indexed by
+    lexicographic rank: ``(scores float32[C(S,3)] or None, tables
+    uint32[C(S,3)][27][2] or None)``."""
+    S = fc_info(h)[0]
+    n = S * (S - 1) * (S - 2) // 6
+    sc = np.zeros(n, dtype=np.float32) if scores else None
+    tb = np.zeros((n, 27, 2), dtype=np.uint32) if tables else None
+    _check(library().fc_triples_dense(h.ptr, _ptr(sc) if sc is not None else None,
+                                      _ptr(tb) if tb is not None else None), "fc_triples_dense")
     return sc, tb
 
 

@@ -263,6 +263,35 @@ cudaError_t launch_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, i
                              cudaStream_t st);
 cudaError_t launch_pairs_tc(int mode, const CUtensorMap &tmap, const PairsArgs &a, int grid, cudaStream_t st);
 
+// Order-3 tensor-core search (fc_triples_tc.cu).  A tile pairs the 64 SNPs
+// l of block Lb (128 e4m3 rows 2 l + g) with the 32 pairs (i, 32 J + q) of
+// slab rows [rowP, rowP + 128) (four rows (a, b) per pair).
+struct TriplesArgs {
+    const uint4 *tiles;     // {rowP, i, J, Lb} per tile of this launch
+    int ntiles;
+    int64_t S, S_pad;
+    int W0, Wt;             // 128-sample chunks: cases [0, W0), controls [W0, Wt)
+    const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
+    const uint4 *PR;        // restricted pair table [S_pad][S_pad]
+    const float *logtab;
+    int M;
+    float hy, invN;
+    uint64_t total;         // C(S, 3)
+    int L, Bcap, P2, stages;
+    float *list_score;      // [grid][L]
+    uint64_t *list_rank;
+    int *gthr;              // global score threshold (ordered int)
+    int *tile_counter;      // next tile of this launch, zeroed before launch
+    uint32_t *err;
+    float *dump_scores;     // MODE_DUMP: [C(S,3)] by rank
+    uint32_t *dump_tables;  // MODE_DUMP: [C(S,3)][27][2]
+};
+
+cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int64_t S32, int64_t i0, int64_t i1,
+                             const int64_t *rowbase, uint8_t *P, cudaStream_t st);
+cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapE, const CUtensorMap &tmapP, const TriplesArgs &a,
+                              int grid, cudaStream_t st);
+
 struct TablesArgs {
     const uint4 *X;
     int64_t S, S_pad;

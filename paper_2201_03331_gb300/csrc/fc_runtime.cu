@@ -213,6 +213,9 @@ Dataset::~Dataset()
     cudaFree(marg);
     cudaFree(tiles);
     cudaFree(PR);
+    cudaFree(P3);
+    cudaFree(tiles3);
+    cudaFree(rowbase3);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
     if (ev_sweep1) cudaEventDestroy(ev_sweep1);
     if (own_stream && own_stream_handle) cudaStreamDestroy(own_stream_handle);
@@ -494,7 +497,8 @@ int Dataset::prepare_pairs()
     cudaError_t e;
     if ((e = dev_alloc((void **)&E, (size_t)rows * pitch)) != cudaSuccess)
         return cuda_status(e, "e4m3 operand allocation");
-    if ((e = dev_alloc((void **)&marg, sizeof(uint16_t) * 8 * (size_t)S)) != cudaSuccess)
+    const bool need_marg = marg == nullptr;
+    if (need_marg && (e = dev_alloc((void **)&marg, sizeof(uint16_t) * 8 * (size_t)S)) != cudaSuccess)
         return cuda_status(e, "marginal allocation");
     const int nb = (int)(S64 / 64);
     std::vector<uint32_t> t;
@@ -511,9 +515,9 @@ int Dataset::prepare_pairs()
         return cuda_status(e, "tile list allocation");
     cudaMemcpyAsync(tiles, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice, stream);
     if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, Wt, rows, (int64_t)pitch, E, stream)) != cudaSuccess ||
-        (e = launch_marginals(X, S, S_pad, W0, Wt, marg, stream)) != cudaSuccess)
+        (need_marg && (e = launch_marginals(X, S, S_pad, W0, Wt, marg, stream)) != cudaSuccess))
         return cuda_status(e, "pair operand preparation");
-    note_launches(2);
+    note_launches(need_marg ? 2 : 1);
     int rc = encode_tmap_u8(&tmap, E, kbytes, pitch, (uint64_t)rows);
     if (rc) return rc;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair operand preparation");
@@ -564,6 +568,182 @@ int Dataset::pairs_dense(float *scores, uint32_t *tables)
     return FC_OK;
 }
 
+// ---- order-3 tensor-core operands --------------------------------------------
+
+bool Dataset::triples_tc_eligible(int L)
+{
+    const char *mode = getenv("FC_TRIPLES_PATH");
+    if (mode && strcmp(mode, "popc") == 0) return false;
+    const bool forced = mode && strcmp(mode, "tc") == 0;
+    if (!forced && S < 384) return false;
+    if (S < 3 || S > 65535 || L > 2048) return false;
+    // Each class needs at least one K chunk, or its accumulator is never written.
+    if (W0 == 0 || Wt == W0) return false;
+    // The restricted pair table of the epilogue holds S_pad^2 x 16 bytes.
+    if ((double)S_pad * (double)S_pad * 16.0 > 2.0 * 1024 * 1024 * 1024) return false;
+    const int Bcap = std::max(L, 1024);
+    const int P2 = pow2_at_least(L + Bcap);
+    return pairs_smem_bytes(2, (int)M, P2) <= (size_t)max_smem_optin;
+}
+
+TriplesArgs Dataset::triples_args(int L, float hy, float invN)
+{
+    TriplesArgs ta{};
+    ta.S = S;
+    ta.S_pad = S_pad;
+    ta.W0 = W0;
+    ta.Wt = Wt;
+    ta.marg4 = reinterpret_cast<const uint4 *>(marg);
+    ta.PR = PR;
+    ta.logtab = logtab;
+    ta.M = (int)M;
+    ta.hy = hy;
+    ta.invN = invN;
+    ta.total = binom(S, 3);
+    ta.L = L;
+    ta.Bcap = L > 0 ? std::max(L, 1024) : 0;
+    ta.P2 = L > 0 ? pow2_at_least(L + ta.Bcap) : 0;
+    ta.stages = 2;
+    for (int st = TC_MAX_STAGES; st >= 2; --st) {
+        if (pairs_smem_bytes(st, (int)M, ta.P2) <= (size_t)max_smem_optin) { ta.stages = st; break; }
+    }
+    return ta;
+}
+
+// Plans the slabs and tiles, allocates the slab buffer and builds the
+// first slab.  A slab holds at most min(16 GiB, half the free device
+// memory) of pair rows (FC_TRIPLES_SLAB_MB overrides the 16 GiB), and at
+// least the rows of one first SNP.
+int Dataset::prepare_triples()
+{
+    if (triples_ready) return FC_OK;
+    int rc = prepare_pairs();
+    if (rc) return rc;
+    if ((rc = prepare_ie(3)) != FC_OK) return rc;
+    const int64_t S32 = (S + 31) / 32 * 32;
+    const int64_t nLb = (S + 63) / 64;
+    const uint64_t kbytes = (uint64_t)Wt * 128;
+    const uint64_t pitch = kbytes + 128;
+    size_t cap = (size_t)16 << 30;
+    if (const char *mb = getenv("FC_TRIPLES_SLAB_MB")) {
+        const long v = atol(mb);
+        if (v > 0) cap = (size_t)v << 20;
+    }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 2);
+    // At least the rows of one first SNP (the largest, i = 0), whatever the cap.
+    const int64_t cap_rows = std::max<int64_t>((int64_t)(cap / pitch), (S32 / 32) * 128);
+    std::vector<int64_t> rowbase((size_t)S, 0);
+    std::vector<uint4> tiles;
+    slabs3.clear();
+    TripleSlab cur;
+    int64_t max_rows = 0;
+    for (int64_t i = 0; i + 2 < S; ++i) {
+        const int64_t Jlo = (i + 1) / 32;
+        const int64_t n = (S32 / 32 - Jlo) * 128;   // rows of the pairs of i
+        if (cur.rows + n > cap_rows && i > cur.i0) {
+            cur.i1 = i;
+            cur.t1 = (int64_t)tiles.size();
+            slabs3.push_back(cur);
+            max_rows = std::max(max_rows, cur.rows);
+            cur = TripleSlab{};
+            cur.i0 = i;
+            cur.t0 = (int64_t)tiles.size();
+        }
+        rowbase[(size_t)i] = cur.rows;
+        for (int64_t J = Jlo; 32 * J <= S - 2; ++J) {
+            const int64_t jmin = std::max<int64_t>(32 * J, i + 1);
+            for (int64_t Lb = (jmin + 1) / 64; Lb < nLb; ++Lb)
+                tiles.push_back(make_uint4((uint32_t)(cur.rows + (J - Jlo) * 128), (uint32_t)i, (uint32_t)J,
+                                           (uint32_t)Lb));
+        }
+        cur.rows += n;
+    }
+    if (S >= 3) {
+        cur.i1 = S - 2;
+        cur.t1 = (int64_t)tiles.size();
+        slabs3.push_back(cur);
+        max_rows = std::max(max_rows, cur.rows);
+    }
+    cudaError_t e;
+    if ((e = dev_alloc((void **)&P3, (size_t)max_rows * pitch)) != cudaSuccess)
+        return cuda_status(e, "pair-row slab allocation");
+    if ((e = dev_alloc((void **)&tiles3, sizeof(uint4) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
+        return cuda_status(e, "triple tile list allocation");
+    if ((e = dev_alloc((void **)&rowbase3, sizeof(int64_t) * (size_t)S)) != cudaSuccess)
+        return cuda_status(e, "slab row table allocation");
+    cudaMemcpyAsync(tiles3, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(rowbase3, rowbase.data(), sizeof(int64_t) * (size_t)S, cudaMemcpyHostToDevice, stream);
+    if ((rc = encode_tmap_u8(&tmap3, P3, kbytes, pitch, (uint64_t)max_rows)) != FC_OK) return rc;
+    built_slab3 = -1;
+    if ((rc = build_slab3(0)) != FC_OK) return rc;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair-row slab");
+    triples_ready = true;
+    return FC_OK;
+}
+
+int Dataset::build_slab3(int s)
+{
+    if (built_slab3 == s || s >= (int)slabs3.size()) return FC_OK;
+    const TripleSlab &sl = slabs3[(size_t)s];
+    const int64_t S32 = (S + 31) / 32 * 32;
+    const int64_t pitch = (int64_t)Wt * 128 + 128;
+    cudaError_t e;
+    if ((e = launch_gate()) != cudaSuccess ||
+        (e = launch_pair_rows(E, pitch, Wt, S, S32, sl.i0, sl.i1, rowbase3 + sl.i0, P3, stream)) != cudaSuccess)
+        return cuda_status(e, "pair-row kernel");
+    note_launches(1);
+    built_slab3 = s;
+    return FC_OK;
+}
+
+int Dataset::triples_dense(float *scores, uint32_t *tables)
+{
+    int rc = prepare_triples();
+    if (rc) return rc;
+    const uint64_t total = binom(S, 3);
+    TriplesArgs ta = triples_args(0, (float)hy64(), (float)(1.0 / (double)M));
+    const size_t ns = scores ? sizeof(float) * (size_t)total : 0;
+    const size_t nt = tables ? sizeof(uint32_t) * 54 * (size_t)total : 0;
+    Arena ar;
+    ar.take(ns);
+    ar.take(nt);
+    ar.take(sizeof(int) * 4);
+    if ((rc = reserve_scratch(ar.off)) != FC_OK) return rc;
+    Arena A2;
+    A2.base = scratch;
+    ta.dump_scores = scores ? (float *)A2.take(ns) : nullptr;
+    if (!scores) A2.take(ns);
+    ta.dump_tables = tables ? (uint32_t *)A2.take(nt) : nullptr;
+    if (!tables) A2.take(nt);
+    ta.tile_counter = (int *)A2.take(sizeof(int) * 4);
+    ta.err = err;
+    cudaError_t e;
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
+    if (ns) cudaMemsetAsync(ta.dump_scores, 0, ns, stream);
+    if (nt) cudaMemsetAsync(ta.dump_tables, 0, nt, stream);
+    for (int s = 0; s < (int)slabs3.size(); ++s) {
+        if ((rc = build_slab3(s)) != FC_OK) return rc;
+        const TripleSlab &sl = slabs3[(size_t)s];
+        TriplesArgs a = ta;
+        a.tiles = tiles3 + sl.t0;
+        a.ntiles = (int)(sl.t1 - sl.t0);
+        if (a.ntiles == 0) continue;
+        cudaMemsetAsync(a.tile_counter, 0, sizeof(int), stream);
+        const int grid = std::min<int64_t>(sms, a.ntiles);
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_triples_tc(MODE_DUMP, tmap, tmap3, a, grid, stream)) != cudaSuccess)
+            return cuda_status(e, "tensor-core triples kernel");
+        note_launches(1);
+    }
+    uint32_t herr = 0;
+    cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
+    if (ns) cudaMemcpyAsync(scores, ta.dump_scores, ns, cudaMemcpyDeviceToHost, stream);
+    if (nt) cudaMemcpyAsync(tables, ta.dump_tables, nt, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "triples dump");
+    if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the triples kernel");
+    return FC_OK;
+}
+
 // ---- search ----------------------------------------------------------------
 
 int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
@@ -589,14 +769,23 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         // Order 2 on large SNP counts: tensor-core contraction; else the
         // prefix-table AND/POPC sweep.
         const bool tc = k == 2 && pairs_tc_eligible(L) && (!no_alloc || pairs_ready);
+        // Order 3 on large SNP counts: tensor-core contraction of pair rows
+        // with SNP rows, one launch per slab of pair rows.
+        const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
         TuneConfig cfg{};
         PairsArgs pa{};
+        TriplesArgs ta{};
         int grid = 0;
         if (tc) {
             int rc = prepare_pairs();
             if (rc) return rc;
             pa = pairs_args(L, (float)hy, (float)(1.0 / Nd));
             grid = std::min(sms, ntiles);
+        } else if (tc3) {
+            int rc = prepare_triples();
+            if (rc) return rc;
+            ta = triples_args(L, (float)hy, (float)(1.0 / Nd));
+            grid = sms * (int)slabs3.size();   // every slab launch writes sms lists
         } else {
             cfg = pick_config(k, L, MODE_TOPN, no_alloc);
             if (cfg.var == VAR_IE) {
@@ -661,6 +850,26 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             cudaMemsetAsync(pa.tile_counter, 0, sizeof(int), stream);
             if ((e = launch_gate()) != cudaSuccess || (e = launch_pairs_tc(MODE_TOPN, tmap, pa, grid, stream)) != cudaSuccess)
                 return cuda_status(e, "tensor-core pairs kernel");
+        } else if (tc3) {
+            ta.gthr = (int *)p[11];
+            ta.tile_counter = (int *)p[11] + 1;
+            ta.err = err;
+            cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
+            for (int si = 0; si < (int)slabs3.size(); ++si) {
+                int rc = build_slab3(si);
+                if (rc) return rc;
+                const TripleSlab &sl = slabs3[(size_t)si];
+                TriplesArgs a = ta;
+                a.tiles = tiles3 + sl.t0;
+                a.ntiles = (int)(sl.t1 - sl.t0);
+                a.list_score = (float *)p[0] + (size_t)si * sms * L;
+                a.list_rank = (uint64_t *)p[1] + (size_t)si * sms * L;
+                cudaMemsetAsync(ta.tile_counter, 0, sizeof(int), stream);
+                if ((e = launch_gate()) != cudaSuccess ||
+                    (e = launch_triples_tc(MODE_TOPN, tmap, tmap3, a, sms, stream)) != cudaSuccess)
+                    return cuda_status(e, "tensor-core triples kernel");
+                if (si > 0) note_launches(1);
+            }
         } else {
             if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_TOPN, sa, stream, nullptr)) != cudaSuccess)
                 return cuda_status(e, "search kernel");
@@ -668,7 +877,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         if (timing) cudaEventRecord(ev_sweep1, stream);
         note_launches(1);
         last_path_tc = tc;
-        last_sweep_var = tc ? -1 : effective_variant(k, cfg.var, MODE_TOPN);
+        last_path_tc3 = tc3;
+        last_sweep_var = (tc || tc3) ? -1 : effective_variant(k, cfg.var, MODE_TOPN);
         // Grid merge.
         const float *src_s = (const float *)p[0];
         const uint64_t *src_r = (const uint64_t *)p[1];
@@ -1007,6 +1217,23 @@ int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64
     return FC_OK;
 }
 
+int fc_triples_dense(fc_handle *h, float *scores, uint32_t *tables)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (!scores && !tables) return set_error(FC_EINVAL, "no output requested");
+        if (h->ds.S < 3) return set_error(FC_EINVAL, "fewer than three SNPs");
+        if (scores && h->ds.S > 512) return set_error(FC_ERANGE, "dense order-3 scores need S <= 512");
+        if (tables && h->ds.S > 160) return set_error(FC_ERANGE, "dense order-3 tables need S <= 160");
+        if (h->ds.W0 == 0 || h->ds.Wt == h->ds.W0)
+            return set_error(FC_EINVAL, "the tensor-core path needs both cases and controls");
+        if ((size_t)pairs_smem_bytes(2, (int)h->ds.M, 0) > (size_t)h->ds.max_smem_optin)
+            return set_error(FC_ERANGE, "too many samples for the tensor-core path");
+        DeviceGuard g(h->ds.device);
+        return h->ds.triples_dense(scores, tables);
+    });
+}
+
 int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables)
 {
     return guarded([&]() -> int {
@@ -1028,6 +1255,7 @@ int fc_last_search_kind(const fc_handle *h)
 {
     if (!h) return set_error(FC_EINVAL, "NULL handle");
     if (h->ds.last_path_tc) return 2;
+    if (h->ds.last_path_tc3) return 6;
     if (h->ds.last_list == 0) return 0;
     if (h->ds.last_sweep_var == VAR_IE) return 3;
     if (h->ds.last_sweep_var == VAR_JR) return 4;

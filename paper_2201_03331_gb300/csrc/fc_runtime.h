@@ -66,6 +66,26 @@ struct Dataset {
     CUtensorMap tmap{};
     bool pairs_ready = false;
 
+    // Order-3 tensor-core operands, built on first use: slabs of pair rows
+    // (E[2i + a] AND E[2j + b], four rows per pair (i, j) with j in
+    // [32 floor((i + 1) / 32), S32)) for consecutive ranges of first SNPs i,
+    // the tiles of every slab, each i's first row within its slab, and the
+    // slab buffer's TMA descriptor.  One slab is built once and kept; with
+    // several, each search rebuilds them in turn in the same buffer.
+    struct TripleSlab {
+        int64_t i0 = 0, i1 = 0;   // first SNPs [i0, i1)
+        int64_t t0 = 0, t1 = 0;   // tiles [t0, t1) of tiles3
+        int64_t rows = 0;         // pair rows
+    };
+    std::vector<TripleSlab> slabs3;
+    uint8_t *P3 = nullptr;
+    uint4 *tiles3 = nullptr;
+    int64_t *rowbase3 = nullptr;
+    CUtensorMap tmap3{};
+    int built_slab3 = -1;
+    bool triples_ready = false;
+    bool last_path_tc3 = false;
+
     // Optional instrumentation (fc_timing): CUDA events around the sweep
     // kernel on the launching stream, and a count of kernel launches.
     bool timing = false;
@@ -92,6 +112,11 @@ struct Dataset {
     PairsArgs pairs_args(int L, float hy, float invN);
     int prepare_pairs();
     int pairs_dense(float *scores, uint32_t *tables);
+    bool triples_tc_eligible(int L);
+    int prepare_triples();
+    int build_slab3(int s);
+    TriplesArgs triples_args(int L, float hy, float invN);
+    int triples_dense(float *scores, uint32_t *tables);
     double hy64() const;
     // Inclusion-exclusion sweep (k = 2, 3): per-SNP genotype counts and, for
     // k = 3, the restricted pair table, built on first use.

@@ -147,7 +147,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier 1 over the NT epilogue threads.
+template <int NT>
+__device__ __forceinline__ void epi_bar_n() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
+__device__ __forceinline__ void epi_bar() { epi_bar_n<128>(); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15])
+        : "r"(taddr));
+}
 
 // Exact integer value of an FP32 accumulator holding an integer in [0, 2^23).
 __device__ __forceinline__ uint32_t f2u_exact(uint32_t bits)
@@ -162,14 +177,15 @@ __device__ __forceinline__ int ordered_int(float f)
 }
 __device__ __forceinline__ float from_ordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
-// Descending bitonic sort of n = 2^p (score, rank) pairs by the 128
-// epilogue threads (tid in [0,128)).
-__device__ void epi_bitonic_desc(float *s, uint64_t *r, int n, int tid)
+// Descending bitonic sort of n = 2^p (score, rank) pairs by the NT
+// epilogue threads (tid in [0, NT)).
+template <int NT>
+__device__ void epi_bitonic_desc_n(float *s, uint64_t *r, int n, int tid)
 {
     for (int size = 2; size <= n; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            epi_bar();
-            for (int i = tid; i < (n >> 1); i += 128) {
+            epi_bar_n<NT>();
+            for (int i = tid; i < (n >> 1); i += NT) {
                 const int lo = 2 * i - (i & (stride - 1));
                 const int hi = lo + stride;
                 const bool desc = (lo & size) == 0;
@@ -180,8 +196,9 @@ __device__ void epi_bitonic_desc(float *s, uint64_t *r, int n, int tid)
             }
         }
     }
-    epi_bar();
+    epi_bar_n<NT>();
 }
+__device__ void epi_bitonic_desc(float *s, uint64_t *r, int n, int tid) { epi_bitonic_desc_n<128>(s, r, n, tid); }
 
 }  // namespace
 }  // namespace fc

@@ -21,10 +21,12 @@
 // [32 floor((i + 1) / 32), S32), four rows (a, b) per pair, zero where
 // j <= i or j >= S.
 //
-// Roles (one persistent CTA per SM, 192 threads), as in the order-2 kernel:
+// Roles (one persistent CTA per SM, 320 threads):
 //   warp 0 : TMA producer (128-byte K chunks of the SNP rows and pair rows)
 //   warp 1 : TMEM allocation and the single-thread MMA issue
-//   warps 2-5 : epilogue (TMEM -> registers -> 27-cell table -> MI -> list)
+//   warps 2-9 : epilogue (TMEM -> registers -> 27-cell table -> MI -> list);
+//               two warps per TMEM lane quarter, each taking half the columns,
+//               so that two warps per scheduler hide the epilogue's latencies
 // Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
 #include "fc_tc.cuh"
 #include "fc_ie.cuh"
@@ -66,11 +68,15 @@ __global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, 
     put(3, a1, b1);
 }
 
+constexpr int T3_EPI_WARPS = 8;
+constexpr int T3_EPI_THREADS = 32 * T3_EPI_WARPS;
+constexpr int T3_THREADS = 64 + T3_EPI_THREADS;
+
 __device__ __forceinline__ uint64_t c3(uint64_t n) { return n * (n - 1) * (n - 2) / 6; }   // 0 for n < 3
 __device__ __forceinline__ uint64_t c2(uint64_t n) { return n * (n - 1) / 2; }             // 0 for n < 2
 
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(T3_THREADS, 1)
     k_triples_tc(const __grid_constant__ CUtensorMap tmapE, const __grid_constant__ CUtensorMap tmapP, TriplesArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -103,12 +109,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_tfull[b], 1);
-            mbar_init(&bar_tempty[b], 4);
+            mbar_init(&bar_tempty[b], T3_EPI_WARPS);
         }
         mbar_init(&bar_done, 1);
         for (int s = 0; s < TC_SCHED; ++s) {
             mbar_init(&bar_sfull[s], 1);
-            mbar_init(&bar_sempty[s], 5);   // the MMA thread and the four epilogue warps
+            mbar_init(&bar_sempty[s], 1 + T3_EPI_WARPS);   // the MMA thread and the epilogue warps
         }
         abort_flag_s = 0;
         buf_count = 0;
@@ -218,9 +224,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else {
         // ---------------- epilogue ----------------
         // TMEM lane = tile row = SNP row 2 l_loc + g of the A block; column
-        // 4 q + (2a + b) = pair q of the B block, genotypes (a, b).
-        const int tid = threadIdx.x - 64;           // 0..127
+        // 4 q + (2a + b) = pair q of the B block, genotypes (a, b).  Warp w
+        // reads lane quarter w % 4 and the columns of half (w - 2) / 4.
+        const int tid = threadIdx.x - 64;           // 0 .. T3_EPI_THREADS - 1
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
         const int l_loc = row >> 1;
         const int g = row & 1;
@@ -242,11 +250,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int b = it & 1;
             const uint32_t u = (uint32_t)(it >> 1);
             if (t >= 0) mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
-            // One stop decision for all four epilogue warps (they meet at
-            // named barriers, which have no timeout); t is the same for all.
-            epi_bar();
+            // One stop decision for all epilogue warps (they meet at named
+            // barriers, which have no timeout); t is the same for all.
+            epi_bar_n<T3_EPI_THREADS>();
             if (tid == 0) epi_stop = *abort_flag;
-            epi_bar();
+            epi_bar_n<T3_EPI_THREADS>();
             if (epi_stop || t < 0) break;
             tc_fence_after();
             const uint4 tile = a.tiles[t];
@@ -266,24 +274,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             const uint64_t base_i = a.total - c3((uint64_t)(a.S - i)) + c2((uint64_t)(a.S - i - 1));
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            for (int ch = 0; ch < TC_BN / 32; ++ch) {
-                uint32_t v0[32], v1[32];
-                tmem_ld32(taddr + ch * 32, v0);
-                tmem_ld32(taddr + 128 + ch * 32, v1);
+            for (int cc = 0; cc < 4; ++cc) {
+                const int ch = half * 4 + cc;           // 16-column chunk: pairs 4 ch .. 4 ch + 3
+                // The chunk's lower-order tables, loaded before the TMEM
+                // reads so that their latency overlaps; indices are clamped
+                // into the tables (entries of invalid combinations are loaded
+                // but not used).
+                const int64_t lc = l < a.S ? l : a.S - 1;
+                uint4 mj[2], pij[2], pjl[2];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const int64_t jj = min((int64_t)J * 32 + ch * 4 + 2 * m + g, a.S - 1);
+                    mj[m] = a.marg4[jj];
+                    pij[m] = a.PR[(size_t)i * Sp + jj];
+                    pjl[m] = a.PR[(size_t)jj * Sp + lc];
+                }
+                uint32_t v0[16], v1[16];
+                tmem_ld16(taddr + ch * 16, v0);
+                tmem_ld16(taddr + 128 + ch * 16, v1);
                 tmem_wait_ld();
-                if (ch == TC_BN / 32 - 1) {
+                if (cc == 3) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar_tempty[b]);
                 }
-                float sc[4];
-                uint64_t rk[4];
-                bool val[4];
+                float sc[2];
+                uint64_t rk[2];
+                bool val[2];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
+                for (int m = 0; m < 2; ++m) {
                     // This thread scores pair 2m + g of the chunk; the partner
                     // lane (genotype 1 - g of the same SNP l) scores 2m + 1 - g
-                    // and sends the cells this thread lacks.
+                    // and sends the packed cells this thread lacks.
                     uint32_t Rr[8];
 #pragma unroll
                     for (int ab = 0; ab < 4; ++ab) {
@@ -291,25 +313,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint32_t own1 = g ? v1[8 * m + 4 + ab] : v1[8 * m + ab];
                         const uint32_t snd0 = g ? v0[8 * m + ab] : v0[8 * m + 4 + ab];
                         const uint32_t snd1 = g ? v1[8 * m + ab] : v1[8 * m + 4 + ab];
-                        const uint32_t oth0 = __shfl_xor_sync(FULL, snd0, 1);
-                        const uint32_t oth1 = __shfl_xor_sync(FULL, snd1, 1);
                         const uint32_t po = f2u_exact(own0) | (f2u_exact(own1) << 16);
-                        const uint32_t pt = f2u_exact(oth0) | (f2u_exact(oth1) << 16);
-                        Rr[2 * ab + g] = po;
-                        Rr[2 * ab + 1 - g] = pt;
+                        const uint32_t ps = f2u_exact(snd0) | (f2u_exact(snd1) << 16);
+                        const uint32_t pt = __shfl_xor_sync(FULL, ps, 1);
+                        Rr[2 * ab] = g ? pt : po;
+                        Rr[2 * ab + 1] = g ? po : pt;
                     }
-                    const int q = ch * 8 + 2 * m + g;
+                    const int q = ch * 4 + 2 * m + g;
                     const int64_t j = (int64_t)J * 32 + q;
                     const bool valid = i < j && j < l && l < a.S;
                     uint32_t T[27];
                     float hsum = 0.f;
                     if (valid) {
                         uint32_t Tj[3], T01[9], T12[9];
-                        unpack_marg(a.marg4[j], Tj);
-                        const uint4 pij = a.PR[(size_t)i * Sp + j];
-                        const uint4 pjl = a.PR[(size_t)j * Sp + l];
-                        const uint32_t R01[4] = {pij.x, pij.y, pij.z, pij.w};
-                        const uint32_t R12[4] = {pjl.x, pjl.y, pjl.z, pjl.w};
+                        unpack_marg(mj[m], Tj);
+                        const uint32_t R01[4] = {pij[m].x, pij[m].y, pij[m].z, pij[m].w};
+                        const uint32_t R12[4] = {pjl[m].x, pjl[m].y, pjl[m].z, pjl[m].w};
                         full2(R01, Ti, Tj, T01);
                         full2(R12, Tj, Tl, T12);
                         full3(Rr, T01, T02, T12, T);
@@ -339,23 +358,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
                 if (MODE == MODE_TOPN) {
-                    // Merge the buffer into the list when a full chunk might not fit.
-                    epi_bar();
-                    if (buf_count > Bcap - 512) {
+                    // Merge the buffer into the list when a full chunk (2 per
+                    // thread) might not fit.
+                    epi_bar_n<T3_EPI_THREADS>();
+                    if (buf_count > Bcap - 2 * T3_EPI_THREADS) {
                         const int nb = buf_count;
-                        for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
-                        epi_bitonic_desc(lscore, lrank, a.P2, tid);
+                        for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) {
+                            lscore[x] = -FLT_MAX;
+                            lrank[x] = NO_RANK;
+                        }
+                        epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
                         if (tid == 0) {
                             buf_count = 0;
                             if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr, ordered_int(lscore[L - 1]));
                         }
-                        epi_bar();
+                        epi_bar_n<T3_EPI_THREADS>();
                     }
                     thr_s = lscore[L - 1];
                     thr_r = lrank[L - 1];
                     const float gthr = from_ordered(*(volatile int *)a.gthr);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
+                    for (int m = 0; m < 2; ++m) {
                         const bool cand = val[m] && sc[m] >= gthr && better(sc[m], rk[m], thr_s, thr_r);
                         const unsigned mk = __ballot_sync(FULL, cand);
                         int base = 0;
@@ -371,11 +394,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
         if (MODE == MODE_TOPN) {
-            epi_bar();
+            epi_bar_n<T3_EPI_THREADS>();
             const int nb = buf_count;
-            for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
-            epi_bitonic_desc(lscore, lrank, a.P2, tid);
-            for (int x = tid; x < L; x += 128) {
+            for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
+            epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
+            for (int x = tid; x < L; x += T3_EPI_THREADS) {
                 a.list_score[(size_t)blockIdx.x * L + x] = lscore[x];
                 a.list_rank[(size_t)blockIdx.x * L + x] = lrank[x];
             }
@@ -414,7 +437,7 @@ cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapE, const CUtensor
     CUtensorMap mE = tmapE, mP = tmapP;
     TriplesArgs args = a;
     void *params[] = {&mE, &mP, &args};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(TC_THREADS), params, bytes, st);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(T3_THREADS), params, bytes, st);
 }
 
 }  // namespace fc

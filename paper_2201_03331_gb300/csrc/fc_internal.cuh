@@ -106,6 +106,7 @@ struct PackArgs {
 cudaError_t launch_class_index(const PackArgs &a, cudaStream_t st);
 cudaError_t launch_pack(const PackArgs &a, int64_t M1, int64_t M0, cudaStream_t st);
 cudaError_t launch_logtab(float *logtab, int64_t M, cudaStream_t st);
+cudaError_t launch_xlogx(float *t, int64_t M, cudaStream_t st);
 
 struct SearchArgs {
     const uint4 *X;
@@ -273,7 +274,7 @@ struct TriplesArgs {
     int W0, Wt;             // 128-sample chunks: cases [0, W0), controls [W0, Wt)
     const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
     const uint4 *PR;        // restricted pair table [S_pad][S_pad]
-    const float *logtab;
+    const float *xlogx;     // x ln x for x = 0..M (FP64 rounded once to FP32)
     int M;
     float hy, invN;
     uint64_t total;         // C(S, 3)

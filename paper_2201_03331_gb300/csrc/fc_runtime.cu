@@ -214,6 +214,7 @@ Dataset::~Dataset()
     cudaFree(tiles);
     cudaFree(PR);
     cudaFree(P3);
+    cudaFree(xlogx);
     cudaFree(tiles3);
     cudaFree(rowbase3);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
@@ -595,7 +596,7 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.Wt = Wt;
     ta.marg4 = reinterpret_cast<const uint4 *>(marg);
     ta.PR = PR;
-    ta.logtab = logtab;
+    ta.xlogx = xlogx;
     ta.M = (int)M;
     ta.hy = hy;
     ta.invN = invN;
@@ -620,6 +621,14 @@ int Dataset::prepare_triples()
     int rc = prepare_pairs();
     if (rc) return rc;
     if ((rc = prepare_ie(3)) != FC_OK) return rc;
+    cudaError_t e;
+    if (!xlogx) {
+        if ((e = dev_alloc((void **)&xlogx, sizeof(float) * (size_t)(M + 1))) != cudaSuccess)
+            return cuda_status(e, "x ln x table allocation");
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_xlogx(xlogx, M, stream)) != cudaSuccess)
+            return cuda_status(e, "x ln x table");
+        note_launches(1);
+    }
     const int64_t S32 = (S + 31) / 32 * 32;
     const int64_t nLb = (S + 63) / 64;
     const uint64_t kbytes = (uint64_t)Wt * 128;
@@ -665,7 +674,6 @@ int Dataset::prepare_triples()
         slabs3.push_back(cur);
         max_rows = std::max(max_rows, cur.rows);
     }
-    cudaError_t e;
     if ((e = dev_alloc((void **)&P3, (size_t)max_rows * pitch)) != cudaSuccess)
         return cuda_status(e, "pair-row slab allocation");
     if ((e = dev_alloc((void **)&tiles3, sizeof(uint4) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)

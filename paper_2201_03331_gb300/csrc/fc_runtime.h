@@ -79,6 +79,7 @@ struct Dataset {
     };
     std::vector<TripleSlab> slabs3;
     uint8_t *P3 = nullptr;
+    float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)
     uint4 *tiles3 = nullptr;
     int64_t *rowbase3 = nullptr;
     CUtensorMap tmap3{};

@@ -16,6 +16,16 @@
 // epilogue scores every combination with the same FP32 mutual information
 // as the sweep and keeps a CTA top list; no count is written to memory.
 //
+// The epilogue scores with a table of x ln x instead of ln x: per cell
+// t = (xl[n] - xl[a]) - xl[b] = a ln(n/a) + b ln(n/b), MI = H(Y) - sum t / N.
+// With each entry correctly rounded (relative error u = 2^-24), a cell errs
+// by at most u n (2 ln M) from the entries, u n ln M from the first
+// subtraction and u n ln 2 from the second; over the 27 cells (sum n = N),
+// the 27 accumulations (partial sums <= N ln 2) and the final scaling this
+// gives |MI32 - MI| <= u (3 ln M + 31 ln 2), within the sweep's bound
+// u (2 ln M + 60 ln 2) for every M < 2^29, so the same FP64 rescoring window
+// applies.
+//
 // The pair rows live in a slab in device memory, built by k_pair_rows for a
 // range of first SNPs i: for each i the rows of the pairs (i, j) with j in
 // [32 floor((i + 1) / 32), S32), four rows (a, b) per pair, zero where
@@ -72,6 +82,16 @@ constexpr int T3_EPI_WARPS = 8;
 constexpr int T3_EPI_THREADS = 32 * T3_EPI_WARPS;
 constexpr int T3_THREADS = 64 + T3_EPI_THREADS;
 
+// Two exact FP32 accumulators (integers below 2^16) packed as lo | hi << 16:
+// x + 2^23 has the integer in its low mantissa bits, and the exponent
+// field of the high word falls outside 32 bits after the shift.
+__device__ __forceinline__ uint32_t pack_exact(uint32_t lo_bits, uint32_t hi_bits)
+{
+    const uint32_t a = __float_as_uint(__uint_as_float(lo_bits) + 8388608.0f);
+    const uint32_t b = __float_as_uint(__uint_as_float(hi_bits) + 8388608.0f);
+    return a + (b << 16) - 0x4B000000u;
+}
+
 __device__ __forceinline__ uint64_t c3(uint64_t n) { return n * (n - 1) * (n - 2) / 6; }   // 0 for n < 3
 __device__ __forceinline__ uint64_t c2(uint64_t n) { return n * (n - 1) / 2; }             // 0 for n < 2
 
@@ -97,9 +117,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *stA = smem;
     uint8_t *stB = smem + (size_t)stages * TC_A_BYTES;
-    float *logtab = reinterpret_cast<float *>(stB + (size_t)stages * TC_B_BYTES);
+    float *xltab = reinterpret_cast<float *>(stB + (size_t)stages * TC_B_BYTES);   // x ln x
     const int lt_floats = (a.M + 1 + 3) & ~3;
-    uint64_t *lrank = reinterpret_cast<uint64_t *>(logtab + lt_floats);
+    uint64_t *lrank = reinterpret_cast<uint64_t *>(xltab + lt_floats);
     float *lscore = reinterpret_cast<float *>(lrank + a.P2);
 
     if (threadIdx.x == 0) {
@@ -127,7 +147,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) logtab[i] = a.logtab[i];
+    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) xltab[i] = a.xlogx[i];
     if (MODE == MODE_TOPN) {
         for (int i = threadIdx.x; i < a.P2; i += blockDim.x) {
             lscore[i] = -FLT_MAX;
@@ -309,15 +329,12 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     uint32_t Rr[8];
 #pragma unroll
                     for (int ab = 0; ab < 4; ++ab) {
-                        const uint32_t own0 = g ? v0[8 * m + 4 + ab] : v0[8 * m + ab];
-                        const uint32_t own1 = g ? v1[8 * m + 4 + ab] : v1[8 * m + ab];
-                        const uint32_t snd0 = g ? v0[8 * m + ab] : v0[8 * m + 4 + ab];
-                        const uint32_t snd1 = g ? v1[8 * m + ab] : v1[8 * m + 4 + ab];
-                        const uint32_t po = f2u_exact(own0) | (f2u_exact(own1) << 16);
-                        const uint32_t ps = f2u_exact(snd0) | (f2u_exact(snd1) << 16);
-                        const uint32_t pt = __shfl_xor_sync(FULL, ps, 1);
-                        Rr[2 * ab] = g ? pt : po;
-                        Rr[2 * ab + 1] = g ? po : pt;
+                        const uint32_t pA = pack_exact(v0[8 * m + ab], v1[8 * m + ab]);           // pair 2m
+                        const uint32_t pB = pack_exact(v0[8 * m + 4 + ab], v1[8 * m + 4 + ab]);   // pair 2m+1
+                        const uint32_t own = g ? pB : pA;
+                        const uint32_t pt = __shfl_xor_sync(FULL, g ? pA : pB, 1);
+                        Rr[2 * ab] = g ? pt : own;
+                        Rr[2 * ab + 1] = g ? own : pt;
                     }
                     const int q = ch * 4 + 2 * m + g;
                     const int64_t j = (int64_t)J * 32 + q;
@@ -334,11 +351,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         full3(Rr, T01, T02, T12, T);
 #pragma unroll
                         for (int x = 0; x < 27; ++x) {
-                            // Clamped so that no index can leave the table.
-                            const uint32_t ca = min(T[x] & 0xffffu, lt), cb = min(T[x] >> 16, lt);
-                            const float ln = logtab[min(ca + cb, lt)];
-                            hsum = fmaf((float)ca, ln - logtab[ca], hsum);
-                            hsum = fmaf((float)cb, ln - logtab[cb], hsum);
+                            // Clamped so that no index can leave the table
+                            // (a, b <= n for exact counts, so nothing changes).
+                            const uint32_t ca = T[x] & 0xffffu, cb = T[x] >> 16;
+                            const uint32_t n = min(ca + cb, lt);
+                            hsum += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
                         }
                     }
                     const float score = fmaf(-hsum, a.invN, a.hy);

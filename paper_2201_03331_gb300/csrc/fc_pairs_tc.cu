@@ -274,6 +274,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                 tmem_ld32(taddr + ch * 32, v0);
                 tmem_ld32(taddr + 128 + ch * 32, v1);
                 tmem_wait_ld();
+                tmem_regs_after_wait(v0);
+                tmem_regs_after_wait(v1);
                 if (ch == TC_BN / 32 - 1) {
                     tc_fence_before();
                     __syncwarp();

@@ -147,6 +147,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Ties registers written by tcgen05.ld to a point after tcgen05.wait::ld:
+// the compiler sees them redefined here, so no use can move above the wait.
+template <int N>
+__device__ __forceinline__ void tmem_regs_after_wait(uint32_t (&v)[N])
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) asm volatile("" : "+r"(v[i]));
+}
+
 // Named barrier 1 over the NT epilogue threads.
 template <int NT>
 __device__ __forceinline__ void epi_bar_n() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }

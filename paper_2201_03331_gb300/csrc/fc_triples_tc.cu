@@ -294,8 +294,26 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             }
             const uint64_t base_i = a.total - c3((uint64_t)(a.S - i)) + c2((uint64_t)(a.S - i - 1));
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+            // Chunk cc + 1 is read from TMEM while chunk cc is scored; the
+            // buffer is released once the last chunk has landed.
+            uint32_t v0[16], v1[16];
+            tmem_ld16(taddr + half * 64, v0);
+            tmem_ld16(taddr + 128 + half * 64, v1);
+            tmem_wait_ld();
+            tmem_regs_after_wait(v0);
+            tmem_regs_after_wait(v1);
+#pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 const int ch = half * 4 + cc;           // 16-column chunk: pairs 4 ch .. 4 ch + 3
+                uint32_t w0[16], w1[16];
+                if (cc < 3) {
+                    tmem_ld16(taddr + (ch + 1) * 16, w0);
+                    tmem_ld16(taddr + 128 + (ch + 1) * 16, w1);
+                } else {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar_tempty[b]);
+                }
                 // The chunk's lower-order tables, loaded before the TMEM
                 // reads so that their latency overlaps; indices are clamped
                 // into the tables (entries of invalid combinations are loaded
@@ -308,15 +326,6 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     mj[m] = a.marg4[jj];
                     pij[m] = a.PR[(size_t)i * Sp + jj];
                     pjl[m] = a.PR[(size_t)jj * Sp + lc];
-                }
-                uint32_t v0[16], v1[16];
-                tmem_ld16(taddr + ch * 16, v0);
-                tmem_ld16(taddr + 128 + ch * 16, v1);
-                tmem_wait_ld();
-                if (cc == 3) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bar_tempty[b]);
                 }
                 float sc[2];
                 uint64_t rk[2];
@@ -407,6 +416,13 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                             lrank[s2] = rk[m];
                         }
                     }
+                }
+                if (cc < 3) {
+                    tmem_wait_ld();
+                    tmem_regs_after_wait(w0);
+                    tmem_regs_after_wait(w1);
+#pragma unroll
+                    for (int x = 0; x < 16; ++x) { v0[x] = w0[x]; v1[x] = w1[x]; }
                 }
             }
         }

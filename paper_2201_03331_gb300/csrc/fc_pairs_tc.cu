@@ -353,8 +353,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                 }
                 if (MODE == MODE_TOPN) {
                     // Merge the buffer into the list when a full chunk might not fit.
+                    // Every thread reads the buffer fill before any thread of
+                    // this round adds to it, so that all take the same branch.
                     epi_bar();
-                    if (buf_count > Bcap - 1024) {
+                    const int fill_now = buf_count;
+                    epi_bar();
+                    if (fill_now > Bcap - 1024) {
                         const int nb = buf_count;
                         for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
                         epi_bitonic_desc(lscore, lrank, a.P2, tid);

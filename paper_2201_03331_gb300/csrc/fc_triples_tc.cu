@@ -31,12 +31,13 @@
 // [32 floor((i + 1) / 32), S32), four rows (a, b) per pair, zero where
 // j <= i or j >= S.
 //
-// Roles (one persistent CTA per SM, 320 threads):
+// Roles (one persistent CTA per SM, 64 + 32 T3_EPI_WARPS threads):
 //   warp 0 : TMA producer (128-byte K chunks of the SNP rows and pair rows)
 //   warp 1 : TMEM allocation and the single-thread MMA issue
-//   warps 2-9 : epilogue (TMEM -> registers -> 27-cell table -> MI -> list);
-//               two warps per TMEM lane quarter, each taking half the columns,
-//               so that two warps per scheduler hide the epilogue's latencies
+//   warps 2.. : epilogue (TMEM -> registers -> 27-cell table -> MI -> list);
+//               T3_EPI_WARPS / 4 warps per TMEM lane quarter, each taking
+//               every (T3_EPI_WARPS / 4)-th 16-column chunk, so that several
+//               warps per scheduler hide the epilogue's latencies
 // Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
 #include "fc_tc.cuh"
 #include "fc_ie.cuh"
@@ -79,6 +80,7 @@ __global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, 
 }
 
 constexpr int T3_EPI_WARPS = 8;
+constexpr int T3_EPI_PER_Q = T3_EPI_WARPS / 4;     // epilogue warps per TMEM lane quarter
 constexpr int T3_EPI_THREADS = 32 * T3_EPI_WARPS;
 constexpr int T3_THREADS = 64 + T3_EPI_THREADS;
 
@@ -245,10 +247,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         // ---------------- epilogue ----------------
         // TMEM lane = tile row = SNP row 2 l_loc + g of the A block; column
         // 4 q + (2a + b) = pair q of the B block, genotypes (a, b).  Warp w
-        // reads lane quarter w % 4 and the columns of half (w - 2) / 4.
+        // reads lane quarter w % 4 and the chunks of part (w - 2) / 4.
         const int tid = threadIdx.x - 64;           // 0 .. T3_EPI_THREADS - 1
         const int quarter = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;           // 0 .. T3_EPI_PER_Q - 1
         const int row = quarter * 32 + lane;
         const int l_loc = row >> 1;
         const int g = row & 1;
@@ -294,38 +296,42 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             }
             const uint64_t base_i = a.total - c3((uint64_t)(a.S - i)) + c2((uint64_t)(a.S - i - 1));
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            // Chunk cc + 1 is read from TMEM while chunk cc is scored; the
-            // buffer is released once the last chunk has landed.
-            uint32_t v0[16], v1[16];
-            tmem_ld16(taddr + half * 64, v0);
-            tmem_ld16(taddr + 128 + half * 64, v1);
-            tmem_wait_ld();
-            tmem_regs_after_wait(v0);
-            tmem_regs_after_wait(v1);
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                const int ch = half * 4 + cc;           // 16-column chunk: pairs 4 ch .. 4 ch + 3
-                uint32_t w0[16], w1[16];
-                if (cc < 3) {
-                    tmem_ld16(taddr + (ch + 1) * 16, w0);
-                    tmem_ld16(taddr + 128 + (ch + 1) * 16, w1);
-                } else {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bar_tempty[b]);
-                }
+            // Chunks part, part + T3_EPI_PER_Q, ... of the eight 16-column
+            // chunks; the buffer is released after this warp's last read.
+            // Every warp runs the same number of rounds (a round without a
+            // chunk scores nothing), because each round of the top-N step
+            // meets at block barriers.
+            constexpr int ROUNDS = (8 + T3_EPI_PER_Q - 1) / T3_EPI_PER_Q;
+            for (int rnd = 0; rnd < ROUNDS; ++rnd) {
+                const int ch = part + rnd * T3_EPI_PER_Q;
+                const bool has = ch < 8;               // warp-uniform
                 // The chunk's lower-order tables, loaded before the TMEM
                 // reads so that their latency overlaps; indices are clamped
                 // into the tables (entries of invalid combinations are loaded
                 // but not used).
                 const int64_t lc = l < a.S ? l : a.S - 1;
                 uint4 mj[2], pij[2], pjl[2];
+                uint32_t v0[16], v1[16];
 #pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int64_t jj = min((int64_t)J * 32 + ch * 4 + 2 * m + g, a.S - 1);
-                    mj[m] = a.marg4[jj];
-                    pij[m] = a.PR[(size_t)i * Sp + jj];
-                    pjl[m] = a.PR[(size_t)jj * Sp + lc];
+                for (int x = 0; x < 16; ++x) { v0[x] = 0; v1[x] = 0; }
+                if (has) {
+#pragma unroll
+                    for (int m = 0; m < 2; ++m) {
+                        const int64_t jj = min((int64_t)J * 32 + ch * 4 + 2 * m + g, a.S - 1);
+                        mj[m] = a.marg4[jj];
+                        pij[m] = a.PR[(size_t)i * Sp + jj];
+                        pjl[m] = a.PR[(size_t)jj * Sp + lc];
+                    }
+                    tmem_ld16(taddr + ch * 16, v0);
+                    tmem_ld16(taddr + 128 + ch * 16, v1);
+                    tmem_wait_ld();
+                    tmem_regs_after_wait(v0);
+                    tmem_regs_after_wait(v1);
+                    if (ch + T3_EPI_PER_Q >= 8) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&bar_tempty[b]);
+                    }
                 }
                 float sc[2];
                 uint64_t rk[2];
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                     const int q = ch * 4 + 2 * m + g;
                     const int64_t j = (int64_t)J * 32 + q;
-                    const bool valid = i < j && j < l && l < a.S;
+                    const bool valid = has && i < j && j < l && l < a.S;
                     uint32_t T[27];
                     float hsum = 0.f;
                     if (valid) {
@@ -386,8 +392,12 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 if (MODE == MODE_TOPN) {
                     // Merge the buffer into the list when a full chunk (2 per
                     // thread) might not fit.
+                    // Every thread reads the buffer fill before any thread of
+                    // this round adds to it, so that all take the same branch.
                     epi_bar_n<T3_EPI_THREADS>();
-                    if (buf_count > Bcap - 2 * T3_EPI_THREADS) {
+                    const int fill_now = buf_count;
+                    epi_bar_n<T3_EPI_THREADS>();
+                    if (fill_now > Bcap - 2 * T3_EPI_THREADS) {
                         const int nb = buf_count;
                         for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) {
                             lscore[x] = -FLT_MAX;
@@ -416,13 +426,6 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                             lrank[s2] = rk[m];
                         }
                     }
-                }
-                if (cc < 3) {
-                    tmem_wait_ld();
-                    tmem_regs_after_wait(w0);
-                    tmem_regs_after_wait(w1);
-#pragma unroll
-                    for (int x = 0; x < 16; ++x) { v0[x] = w0[x]; v1[x] = w1[x]; }
                 }
             }
         }

@@ -575,6 +575,7 @@ bool Dataset::triples_tc_eligible(int L)
 {
     const char *mode = getenv("FC_TRIPLES_PATH");
     if (mode && strcmp(mode, "popc") == 0) return false;
+    if (!allow_tc3) return false;
     const bool forced = mode && strcmp(mode, "tc") == 0;
     if (!forced && S < 384) return false;
     if (S < 3 || S > 65535 || L > 2048) return false;
@@ -612,9 +613,10 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
 }
 
 // Plans the slabs and tiles, allocates the slab buffer and builds the
-// first slab.  A slab holds at most min(16 GiB, half the free device
+// first slab.  A slab holds at most min(16 GiB, a quarter of the free device
 // memory) of pair rows (FC_TRIPLES_SLAB_MB overrides the 16 GiB), and at
-// least the rows of one first SNP.
+// least the rows of one first SNP.  A single slab is kept for later
+// searches; with several, the buffer is released after each search.
 int Dataset::prepare_triples()
 {
     if (triples_ready) return FC_OK;
@@ -639,7 +641,7 @@ int Dataset::prepare_triples()
         if (v > 0) cap = (size_t)v << 20;
     }
     size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 2);
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 4);
     // At least the rows of one first SNP (the largest, i = 0), whatever the cap.
     const int64_t cap_rows = std::max<int64_t>((int64_t)(cap / pitch), (S32 / 32) * 128);
     std::vector<int64_t> rowbase((size_t)S, 0);
@@ -688,6 +690,20 @@ int Dataset::prepare_triples()
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair-row slab");
     triples_ready = true;
     return FC_OK;
+}
+
+void Dataset::release_triples()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    cudaFree(P3);
+    cudaFree(tiles3);
+    cudaFree(rowbase3);
+    P3 = nullptr;
+    tiles3 = nullptr;
+    rowbase3 = nullptr;
+    slabs3.clear();
+    built_slab3 = -1;
+    triples_ready = false;
 }
 
 int Dataset::build_slab3(int s)
@@ -748,6 +764,7 @@ int Dataset::triples_dense(float *scores, uint32_t *tables)
     if (ns) cudaMemcpyAsync(scores, ta.dump_scores, ns, cudaMemcpyDeviceToHost, stream);
     if (nt) cudaMemcpyAsync(tables, ta.dump_tables, nt, cudaMemcpyDeviceToHost, stream);
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "triples dump");
+    if (slabs3.size() > 1) release_triples();
     if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the triples kernel");
     return FC_OK;
 }
@@ -934,6 +951,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                                  FC_MAX_LIST);
             continue;
         }
+        // Several slabs are rebuilt by every search anyway: do not keep them.
+        if (tc3 && slabs3.size() > 1) release_triples();
         *out_count = N;
         return FC_OK;
     }

@@ -86,6 +86,7 @@ struct Dataset {
     int built_slab3 = -1;
     bool triples_ready = false;
     bool last_path_tc3 = false;
+    bool allow_tc3 = true;     // false for the jobs of a batch handle
 
     // Optional instrumentation (fc_timing): CUDA events around the sweep
     // kernel on the launching stream, and a count of kernel launches.
@@ -116,6 +117,7 @@ struct Dataset {
     bool triples_tc_eligible(int L);
     int prepare_triples();
     int build_slab3(int s);
+    void release_triples();
     TriplesArgs triples_args(int L, float hy, float invN);
     int triples_dense(float *scores, uint32_t *tables);
     double hy64() const;

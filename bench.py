@@ -365,18 +365,22 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
     sweep_avg_s = (sweep_ms / max(sweeps, 1)) / 1e3
     kind = fc.fc_last_search_kind(h)
-    if kind in (2, 6):
-        # Tensor-core contraction: 2^k cells (genotypes in {0,1}) x M
-        # samples x 2 FLOP per combination; fp8 peak = measured dense bf16 x 2
-        # (nominal ratio).
-        flops = math.comb(ds.S, k) * (2 ** k) * 2 * (ds.cases + ds.controls)
+    if kind in (2, 6, 7):
+        # Tensor-core contraction: contracted cells x M samples x 2 FLOP per
+        # combination (orders 2, 3: the 2^k cells with genotypes in {0,1};
+        # order 4: all 81 cells); fp8 peak = measured dense bf16 x 2 (nominal
+        # ratio).
+        cells = {2: 4, 6: 8, 7: 81}[kind]
+        flops = math.comb(ds.S, k) * cells * 2 * (ds.cases + ds.controls)
         bf16 = peaks.get("bf16_tflops")
         peak = 2.0 * float(bf16) if bf16 else 2.0 * 1900.0
         achieved = flops / sweep_avg_s / 1e12 if sweeps else None
-        kernel_key = f"{'k_pairs_tc' if kind == 2 else 'k_triples_tc'}<TOPN> {args.workload}"
+        tc_name = {2: "k_pairs_tc", 6: "k_triples_tc", 7: "k_quads_tc"}[kind]
+        kernel_key = f"{tc_name}<TOPN> {args.workload}"
         roofline = {"bound": "tensor", "kernel": kernel_key, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                    "traffic": traffic_for(kernel_key, "fc_pairs_tc.cu" if kind == 2 else "fc_triples_tc.cu"),
+                    "traffic": traffic_for(kernel_key, {2: "fc_pairs_tc.cu", 6: "fc_triples_tc.cu",
+                                                        7: "fc_quads_tc.cu"}[kind]),
                     "peak_basis": ("2 x measured dense bf16 (fp8 e4m3 kind::f8f6f4)" if bf16
                                    else "2 x fallback 1.9 PFLOP/s bf16"),
                     "sweep_ms_per_launch": 1e3 * sweep_avg_s,

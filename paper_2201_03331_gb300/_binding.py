@@ -45,6 +45,7 @@ _SIGNATURES = {
     "fc_info": ([P, P, P, P, P], i32),
     "fc_pairs_dense": ([P, P, P], i32),
     "fc_triples_dense": ([P, P, P], i32),
+    "fc_quads_dense": ([P, P, P], i32),
     "fc_load_batch": ([i32, P, P, P, P, i32, P], i32),
     "fc_search_batch": ([P, i32, i64, P, P, P], i32),
     "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
@@ -206,6 +207,19 @@ def fc_triples_dense(h: Handle, scores: bool = True, tables: bool = False):
     tb = np.zeros((n, 27, 2), dtype=np.uint32) if tables else None
     _check(library().fc_triples_dense(h.ptr, _ptr(sc) if sc is not None else None,
                                       _ptr(tb) if tb is not None else None), "fc_triples_dense")
+    return sc, tb
+
+
+def fc_quads_dense(h: Handle, scores: bool = True, tables: bool = False):
+    """Dense order-4 output of the tensor-core kernel, indexed by
+    lexicographic rank: ``(scores float32[C(S,4)] or None, tables
+    uint32[C(S,4)][81][2] or None)``."""
+    S = fc_info(h)[0]
+    n = S * (S - 1) * (S - 2) * (S - 3) // 24
+    sc = np.zeros(n, dtype=np.float32) if scores else None
+    tb = np.zeros((n, 81, 2), dtype=np.uint32) if tables else None
+    _check(library().fc_quads_dense(h.ptr, _ptr(sc) if sc is not None else None,
+                                    _ptr(tb) if tb is not None else None), "fc_quads_dense")
     return sc, tb
 
 

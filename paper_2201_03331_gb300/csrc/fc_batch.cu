@@ -377,7 +377,7 @@ int fc_load_batch(int n_data, const uint8_t *const *genotypes, const int64_t *S,
                 // Jobs are searched by the batched sweep; the per-job path
                 // runs the same sweep, and no job keeps a pair-row slab
                 // (many resident jobs could not each hold one).
-                job->allow_tc3 = false;
+                job->allow_slabs = false;
                 rc = job->load(dG, dph + (size_t)r * M[d], S[d], M[d]);
                 if (rc) {
                     rc = set_error(rc, "data set %d replicate %d: %s", d, r, fc_last_error());

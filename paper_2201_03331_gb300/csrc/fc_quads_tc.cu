@@ -1,0 +1,407 @@
+// Order-4 exhaustive search on the fifth-generation tensor cores (tcgen05).
+//
+// For a combination (i, j, e, f) every cell of the 3^4 table is, per class c
+// (Section "Computing the contingency tables": the population count of the
+// AND of one row of each SNP's table),
+//     n_c(a, b, g, h) = < P_c[(i, j), (a, b)], P_c[(e, f), (g, h)] >,
+// the dot product over the samples of two pair rows P[(s, t), (a, b)] =
+// [G_s = a][G_t = b] stored as 0/1 e4m3 bytes.  With the left operand a block
+// of 12 pairs (i, j) and the right operand a block of 12 pairs (e, f), both
+// with all nine genotype pairs, one 128 x 128 tcgen05.mma kind::f8f6f4 tile
+// per class yields all 81 cells of 144 combinations at once (exact: products
+// of 0/1, FP32 sums of integers below 2^24).  No cell is derived: the table
+// is complete, and combinations with j < e are the valid ones.
+//
+// Row layout of a 128-row block (left and right alike): 32-row quarter w
+// holds pairs 3w, 3w + 1, 3w + 2 in rows 9p + 3a + b (p the pair within the
+// quarter), rows 27..31 zero.  So one TMEM lane quarter (one epilogue warp)
+// holds three left pairs whole, and a thread owns the 9 cells (g, h) of its
+// (pair, a, b) row against each right pair.
+//
+// Scoring: MI = H(Y) - (1/N) sum_cells [x ln x (n) - x ln x (a) - x ln x (b)]
+// with a table of x ln x correctly rounded to FP32.  Each thread sums the
+// terms of its 9 cells, the 9 lanes of a pair add their partial sums; every
+// addend is a sum of non-negative cell terms bounded by N ln 2.  As for
+// order 3, |MI32 - MI| <= u (3 ln M + (3^4 + 4) ln 2) (u = 2^-24), within the
+// sweep's bound u (2 ln M + (2 3^4 + 6) ln 2) for every M < 2^83.
+//
+// Roles (one persistent CTA per SM, 192 threads), as in the order-2 kernel:
+//   warp 0 : TMA producer (128-byte K chunks of the left and right blocks)
+//   warp 1 : TMEM allocation and the single-thread MMA issue
+//   warps 2-5 : epilogue (TMEM -> registers -> 9-cell partial MI -> pair sum
+//               -> CTA top list)
+// Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
+#include "fc_tc.cuh"
+
+namespace fc {
+
+namespace {
+
+// Pair-row slab: thread (row, 16-byte chunk) of block row rows; the row is
+// [G_s = a][G_t = b] over 16 samples of one class word, expanded to bytes.
+__global__ void k_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_t *pairs, int64_t nblocks,
+                            int64_t pitch, uint8_t *Q)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int cw = 8 * Wt;                          // 16-byte chunks per row
+    if (t >= nblocks * 128 * cw) return;
+    const int64_t row = t / cw;
+    const int ch = (int)(t - row * cw);
+    const int64_t blk = row >> 7;
+    const int r = (int)(row & 127);
+    const int quarter = r >> 5, r32 = r & 31;
+    uint32_t bits = 0;
+    if (r32 < 27) {
+        const uint32_t pr = pairs[blk * Q4_PAIRS_PER_BLOCK + quarter * 3 + r32 / 9];
+        if (pr != ~0u) {
+            const uint32_t s = pr & 0xffffu, u = pr >> 16;
+            const int ab = r32 % 9;
+            const int w = ch >> 3, sub = ch & 7;    // 128-sample word, 16-sample part
+            const uint4 x = X[((size_t)w * 3 + ab / 3) * S_pad + s];
+            const uint4 y = X[((size_t)w * 3 + ab % 3) * S_pad + u];
+            const int q32 = sub >> 1;
+            const uint32_t xw = q32 == 0 ? x.x : q32 == 1 ? x.y : q32 == 2 ? x.z : x.w;
+            const uint32_t yw = q32 == 0 ? y.x : q32 == 1 ? y.y : q32 == 2 ? y.z : y.w;
+            bits = ((xw & yw) >> ((sub & 1) * 16)) & 0xffffu;
+        }
+    }
+    uint32_t o[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v |= ((bits >> (4 * q + e)) & 1u ? 0x38u : 0u) << (8 * e);
+        o[q] = v;
+    }
+    *(reinterpret_cast<uint4 *>(Q + row * pitch) + ch) = make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+__device__ __forceinline__ uint64_t cn4(uint64_t n) { return n < 4 ? 0 : n * (n - 1) * (n - 2) * (n - 3) / 24; }
+__device__ __forceinline__ uint64_t cn3(uint64_t n) { return n < 3 ? 0 : n * (n - 1) * (n - 2) / 6; }
+__device__ __forceinline__ uint64_t cn2(uint64_t n) { return n < 2 ? 0 : n * (n - 1) / 2; }
+
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_quads_tc(const __grid_constant__ CUtensorMap tmapL, const __grid_constant__ CUtensorMap tmapR, QuadsArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar_full[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
+    __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_done;
+    __shared__ uint32_t tmem_base_slot;
+    __shared__ uint64_t bar_sfull[TC_SCHED], bar_sempty[TC_SCHED];
+    __shared__ int sched_tile[TC_SCHED];
+    __shared__ int abort_flag_s;
+    __shared__ int buf_count;
+    __shared__ int epi_stop;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int stages = a.stages;
+    volatile int *abort_flag = &abort_flag_s;
+
+    uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stA = smem;
+    uint8_t *stB = smem + (size_t)stages * TC_A_BYTES;
+    float *xltab = reinterpret_cast<float *>(stB + (size_t)stages * TC_B_BYTES);   // x ln x
+    const int lt_floats = (a.M + 1 + 3) & ~3;
+    uint64_t *lrank = reinterpret_cast<uint64_t *>(xltab + lt_floats);
+    float *lscore = reinterpret_cast<float *>(lrank + a.P2);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_tfull[b], 1);
+            mbar_init(&bar_tempty[b], 4);
+        }
+        mbar_init(&bar_done, 1);
+        for (int s = 0; s < TC_SCHED; ++s) {
+            mbar_init(&bar_sfull[s], 1);
+            mbar_init(&bar_sempty[s], 5);   // the MMA thread and the four epilogue warps
+        }
+        abort_flag_s = 0;
+        buf_count = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) xltab[i] = a.xlogx[i];
+    if (MODE == MODE_TOPN) {
+        for (int i = threadIdx.x; i < a.P2; i += blockDim.x) {
+            lscore[i] = -FLT_MAX;
+            lrank[i] = NO_RANK;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = tmem_base_slot;
+
+    const int kc0 = a.W0, kc1 = a.Wt - a.W0;   // 128-sample chunks per class
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            uint32_t fill = 0;
+            bool ok = true;
+            for (int it = 0; ok; ++it) {
+                const int slot = it % TC_SCHED;
+                const uint32_t sn = (uint32_t)(it / TC_SCHED);
+                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err)) break;
+                int t = atomicAdd(a.tile_counter, 1);
+                if (t >= a.ntiles) t = -1;
+                sched_tile[slot] = t;
+                mbar_arrive(&bar_sfull[slot]);
+                if (t < 0) break;
+                const uint2 tile = a.tiles[t];
+                const int rowL = (int)tile.x * 128, rowR = (int)tile.y * 128;
+                for (int c = 0; c < 2 && ok; ++c) {
+                    const int nk = c ? kc1 : kc0;
+                    const int xbase = c ? kc0 * TC_BK : 0;
+                    for (int kc = 0; kc < nk; ++kc, ++fill) {
+                        const int s = fill % stages;
+                        const uint32_t n = fill / stages;
+                        if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
+                        mbar_expect_tx(&bar_full[s], TC_A_BYTES + TC_B_BYTES);
+                        tma_load_2d(&tmapL, &bar_full[s], stA + (size_t)s * TC_A_BYTES, xbase + kc * TC_BK, rowL);
+                        tma_load_2d(&tmapR, &bar_full[s], stB + (size_t)s * TC_B_BYTES, xbase + kc * TC_BK, rowR);
+                    }
+                }
+            }
+            // Let every copy issued so far land before the CTA can exit.
+            const uint32_t issued = fill;
+            for (uint32_t f = (issued > (uint32_t)stages ? issued - stages : 0); f < issued; ++f) {
+                const int s = f % stages;
+                const uint32_t n = f / stages;
+                long long t0 = clock64();
+                while (!mbar_try(&bar_full[s], n & 1) && clock64() - t0 < WAIT_BUDGET) {}
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_e4m3_f32(TC_BM, TC_BN);
+            uint32_t fill = 0;
+            bool ok = true;
+            for (int it = 0; ok; ++it) {
+                const int slot = it % TC_SCHED;
+                const uint32_t sn = (uint32_t)(it / TC_SCHED);
+                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
+                const int t = sched_tile[slot];
+                mbar_arrive(&bar_sempty[slot]);
+                if (t < 0) break;
+                const int b = it & 1;
+                const uint32_t u = (uint32_t)(it >> 1);
+                if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err)) break;
+                tc_fence_after();
+                for (int c = 0; c < 2 && ok; ++c) {
+                    const int nk = c ? kc1 : kc0;
+                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + c * 128);
+                    for (int kc = 0; kc < nk; ++kc, ++fill) {
+                        const int s = fill % stages;
+                        const uint32_t n = fill / stages;
+                        if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t aaddr = smem_u32(stA + (size_t)s * TC_A_BYTES);
+                        const uint32_t baddr = smem_u32(stB + (size_t)s * TC_B_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 32; ++kk) {
+                            mma_e4m3(d, smem_desc_sw128(aaddr + kk * 32), smem_desc_sw128(baddr + kk * 32), idesc,
+                                     (kc > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(&bar_empty[s]);
+                    }
+                }
+                if (ok) mma_commit(&bar_tfull[b]);
+            }
+            // All MMAs issued by this thread complete before TMEM is released.
+            mma_commit(&bar_done);
+            long long t0 = clock64();
+            while (!mbar_try(&bar_done, 0) && clock64() - t0 < WAIT_BUDGET) {}
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        // TMEM lane = left row 32 w + 9 p + 3 a_i + a_j; column 32 c + 9 q + 3 g + h
+        // = right pair 3 c + q of the tile, genotypes (g, h) of (e, f).
+        const int tid = threadIdx.x - 64;           // 0..127
+        const int quarter = warp & 3;
+        const int p = lane / 9;                     // left pair within the quarter (3 = padding lanes)
+        const int cell_ab = lane - 9 * p;           // 3 a + b of this lane's row
+        const int seg0 = 9 * min(p, 2);             // first lane of this pair's 9 lanes
+        const int L = a.L;
+        const int Bcap = a.Bcap;
+        const uint32_t lt = (uint32_t)a.M;
+        float thr_s = -FLT_MAX;
+        uint64_t thr_r = NO_RANK;
+        for (int it = 0;; ++it) {
+            const int slot = it % TC_SCHED;
+            const uint32_t sn = (uint32_t)(it / TC_SCHED);
+            const bool ok = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err);
+            const int t = ok ? sched_tile[slot] : -1;
+            if (ok) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_sempty[slot]);
+            }
+            const int b = it & 1;
+            const uint32_t u = (uint32_t)(it >> 1);
+            if (t >= 0) mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
+            // One stop decision for all four epilogue warps (they meet at
+            // named barriers, which have no timeout); t is the same for all.
+            epi_bar();
+            if (tid == 0) epi_stop = *abort_flag;
+            epi_bar();
+            if (epi_stop || t < 0) break;
+            tc_fence_after();
+            const uint2 tile = a.tiles[t];
+            // This lane's left pair (i, j).
+            uint32_t lp = ~0u;
+            if (p < 3) lp = a.lpairs[(size_t)tile.x * Q4_PAIRS_PER_BLOCK + quarter * 3 + p];
+            const int64_t pi = lp & 0xffffu, pj = lp >> 16;
+            const uint64_t base_ij = (lp != ~0u)
+                                         ? a.total - cn4((uint64_t)(a.S - pi)) + cn3((uint64_t)(a.S - pi - 1)) -
+                                               cn3((uint64_t)(a.S - pj))
+                                         : 0;
+            const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
+            for (int ch = 0; ch < 4; ++ch) {
+                uint32_t v0[32], v1[32];
+                tmem_ld32(taddr + ch * 32, v0);
+                tmem_ld32(taddr + 128 + ch * 32, v1);
+                tmem_wait_ld();
+                tmem_regs_after_wait(v0);
+                tmem_regs_after_wait(v1);
+                if (ch == 3) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar_tempty[b]);
+                }
+                float sc[3];
+                uint64_t rk[3];
+                bool val[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    // Right pair 3 ch + q: 9 cells (g, h) of this row.
+                    const uint32_t rp = a.rpairs[(size_t)tile.y * Q4_PAIRS_PER_BLOCK + ch * 3 + q];
+                    const int64_t pe = rp & 0xffffu, pf = rp >> 16;
+                    float part = 0.f;
+                    uint32_t cnt[9][2];
+#pragma unroll
+                    for (int gh = 0; gh < 9; ++gh) {
+                        // Clamped so that no index can leave the table.
+                        const uint32_t ca = min(f2u_exact(v0[9 * q + gh]), lt);
+                        const uint32_t cb = min(f2u_exact(v1[9 * q + gh]), lt);
+                        const uint32_t n = min(ca + cb, lt);
+                        part += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
+                        cnt[gh][0] = ca;
+                        cnt[gh][1] = cb;
+                    }
+                    // Sum over the 9 lanes of this left pair.
+                    float tot = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) tot += __shfl_sync(FULL, part, min(seg0 + k, 31));
+                    const bool valid = p < 3 && lp != ~0u && rp != ~0u && pj < pe;
+                    const float score = fmaf(-tot, a.invN, a.hy);
+                    // Lexicographic rank of (i, j, e, f).
+                    const uint64_t rank =
+                        valid ? base_ij + cn2((uint64_t)(a.S - pj - 1)) - cn2((uint64_t)(a.S - pe)) + (uint64_t)(pf - pe - 1)
+                              : NO_RANK;
+                    sc[q] = score;
+                    rk[q] = rank;
+                    val[q] = valid && cell_ab == 0;
+                    if (MODE == MODE_DUMP && valid) {
+                        if (a.dump_scores && cell_ab == 0) a.dump_scores[rank] = score;
+                        if (a.dump_tables) {
+                            uint32_t *o = a.dump_tables + (size_t)rank * 162 + (size_t)cell_ab * 18;
+#pragma unroll
+                            for (int gh = 0; gh < 9; ++gh) { o[2 * gh] = cnt[gh][0]; o[2 * gh + 1] = cnt[gh][1]; }
+                        }
+                    }
+                }
+                if (MODE == MODE_TOPN) {
+                    // Every thread reads the buffer fill before any thread of
+                    // this round adds to it, so that all take the same branch.
+                    epi_bar();
+                    const int fill_now = buf_count;
+                    epi_bar();
+                    if (fill_now > Bcap - 3 * 128) {
+                        const int nb = buf_count;
+                        for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
+                        epi_bitonic_desc(lscore, lrank, a.P2, tid);
+                        if (tid == 0) {
+                            buf_count = 0;
+                            if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr, ordered_int(lscore[L - 1]));
+                        }
+                        epi_bar();
+                    }
+                    thr_s = lscore[L - 1];
+                    thr_r = lrank[L - 1];
+                    const float gthr = from_ordered(*(volatile int *)a.gthr);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const bool cand = val[q] && sc[q] >= gthr && better(sc[q], rk[q], thr_s, thr_r);
+                        const unsigned mk = __ballot_sync(FULL, cand);
+                        int base = 0;
+                        if (lane == 0 && mk) base = atomicAdd(&buf_count, __popc(mk));
+                        base = __shfl_sync(FULL, base, 0);
+                        if (cand) {
+                            const int s2 = L + base + __popc(mk & ((1u << lane) - 1u));
+                            lscore[s2] = sc[q];
+                            lrank[s2] = rk[q];
+                        }
+                    }
+                }
+            }
+        }
+        if (MODE == MODE_TOPN) {
+            epi_bar();
+            const int nb = buf_count;
+            for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
+            epi_bitonic_desc(lscore, lrank, a.P2, tid);
+            for (int x = tid; x < L; x += 128) {
+                a.list_score[(size_t)blockIdx.x * L + x] = lscore[x];
+                a.list_rank[(size_t)blockIdx.x * L + x] = lrank[x];
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_t *pairs, int64_t nblocks,
+                             int64_t pitch, uint8_t *Q, cudaStream_t st)
+{
+    const int64_t n = nblocks * 128 * 8 * (int64_t)Wt;
+    if (n == 0) return cudaSuccess;
+    k_quad_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S_pad, Wt, pairs, nblocks, pitch, Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quads_tc(int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
+                            int grid, cudaStream_t st)
+{
+    const size_t bytes = pairs_smem_bytes(a.stages, a.M, a.P2);
+    void *fn = mode == MODE_TOPN ? reinterpret_cast<void *>(&k_quads_tc<MODE_TOPN>)
+                                 : reinterpret_cast<void *>(&k_quads_tc<MODE_DUMP>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    CUtensorMap mL = tmapL, mR = tmapR;
+    QuadsArgs args = a;
+    void *params[] = {&mL, &mR, &args};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(TC_THREADS), params, bytes, st);
+}
+
+}  // namespace fc

@@ -215,6 +215,11 @@ Dataset::~Dataset()
     cudaFree(PR);
     cudaFree(P3);
     cudaFree(xlogx);
+    cudaFree(QL);
+    cudaFree(QR);
+    cudaFree(lpairs4);
+    cudaFree(rpairs4);
+    cudaFree(tiles4);
     cudaFree(tiles3);
     cudaFree(rowbase3);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
@@ -575,7 +580,7 @@ bool Dataset::triples_tc_eligible(int L)
 {
     const char *mode = getenv("FC_TRIPLES_PATH");
     if (mode && strcmp(mode, "popc") == 0) return false;
-    if (!allow_tc3) return false;
+    if (!allow_slabs) return false;
     const bool forced = mode && strcmp(mode, "tc") == 0;
     if (!forced && S < 384) return false;
     if (S < 3 || S > 65535 || L > 2048) return false;
@@ -769,6 +774,174 @@ int Dataset::triples_dense(float *scores, uint32_t *tables)
     return FC_OK;
 }
 
+// ---- order-4 tensor-core operands ----------------------------------------------
+
+namespace {
+// Pairs usable on each side of an order-4 combination: left (i, j) needs
+// j <= S - 3, right (e, f) needs e >= 2; both counts are (S-3)(S-2)/2.
+int64_t quad_side_pairs(int64_t S) { return S < 4 ? 0 : (S - 3) * (S - 2) / 2; }
+int64_t quad_blocks(int64_t S) { return (quad_side_pairs(S) + Q4_PAIRS_PER_BLOCK - 1) / Q4_PAIRS_PER_BLOCK; }
+// Tiles of the plan below, about S^4 / 3456; bounded so the list stays small.
+constexpr int64_t Q4_MAX_TILES = (int64_t)1 << 25;
+}  // namespace
+
+bool Dataset::quads_tc_eligible(int L)
+{
+    const char *mode = getenv("FC_QUADS_PATH");
+    if (mode && strcmp(mode, "popc") == 0) return false;
+    if (!allow_slabs) return false;
+    const bool forced = mode && strcmp(mode, "tc") == 0;
+    if (!forced && S < 64) return false;
+    if (S < 4 || S > 65535 || L > 2048) return false;
+    if (W0 == 0 || Wt == W0) return false;
+    if ((double)S * S * S * S / 3456.0 > (double)Q4_MAX_TILES) return false;
+    const double slab = 2.0 * (double)quad_blocks(S) * 128.0 * ((double)Wt * 128 + 128);
+    size_t free_b = 0, total_b = 0;
+    double cap = 32.0 * 1024 * 1024 * 1024;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, (double)free_b / 4);
+    if (!quads_ready && slab > cap) return false;
+    const int Bcap = std::max(L, 1024);
+    const int P2 = pow2_at_least(L + Bcap);
+    return pairs_smem_bytes(2, (int)M, P2) <= (size_t)max_smem_optin;
+}
+
+QuadsArgs Dataset::quads_args(int L, float hy, float invN)
+{
+    QuadsArgs qa{};
+    qa.tiles = tiles4;
+    qa.ntiles = (int)ntiles4;
+    qa.S = S;
+    qa.W0 = W0;
+    qa.Wt = Wt;
+    qa.lpairs = lpairs4;
+    qa.rpairs = rpairs4;
+    qa.xlogx = xlogx;
+    qa.M = (int)M;
+    qa.hy = hy;
+    qa.invN = invN;
+    qa.total = binom(S, 4);
+    qa.L = L;
+    qa.Bcap = L > 0 ? std::max(L, 1024) : 0;
+    qa.P2 = L > 0 ? pow2_at_least(L + qa.Bcap) : 0;
+    qa.stages = 2;
+    for (int st = TC_MAX_STAGES; st >= 2; --st) {
+        if (pairs_smem_bytes(st, (int)M, qa.P2) <= (size_t)max_smem_optin) { qa.stages = st; break; }
+    }
+    return qa;
+}
+
+// Pair lists, tile plan, slabs and descriptors.  Tiles come in groups of 64
+// left blocks: for each right block with a usable pair (largest e above the
+// group's smallest j) the group's left blocks follow one another, so the
+// group stays in L2 while the right blocks stream.
+int Dataset::prepare_quads()
+{
+    if (quads_ready) return FC_OK;
+    cudaError_t e;
+    if (!xlogx) {
+        if ((e = dev_alloc((void **)&xlogx, sizeof(float) * (size_t)(M + 1))) != cudaSuccess)
+            return cuda_status(e, "x ln x table allocation");
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_xlogx(xlogx, M, stream)) != cudaSuccess)
+            return cuda_status(e, "x ln x table");
+        note_launches(1);
+    }
+    const int64_t nb = quad_blocks(S);
+    std::vector<uint32_t> lp((size_t)nb * Q4_PAIRS_PER_BLOCK, ~0u), rp((size_t)nb * Q4_PAIRS_PER_BLOCK, ~0u);
+    {
+        size_t n = 0;
+        for (int64_t j = 1; j <= S - 3; ++j)
+            for (int64_t i = 0; i < j; ++i) lp[n++] = (uint32_t)i | ((uint32_t)j << 16);
+        n = 0;
+        for (int64_t a0 = 2; a0 <= S - 2; ++a0)
+            for (int64_t f = a0 + 1; f < S; ++f) rp[n++] = (uint32_t)a0 | ((uint32_t)f << 16);
+    }
+    const int64_t npairs = quad_side_pairs(S);
+    auto jmin = [&](int64_t blk) { return (int64_t)(lp[(size_t)blk * Q4_PAIRS_PER_BLOCK] >> 16); };
+    auto emax = [&](int64_t blk) {
+        const int64_t last = std::min<int64_t>((blk + 1) * Q4_PAIRS_PER_BLOCK, npairs) - 1;
+        return (int64_t)(rp[(size_t)last] & 0xffffu);
+    };
+    std::vector<uint2> tiles;
+    const int64_t Gr = 64;
+    for (int64_t g0 = 0; g0 < nb; g0 += Gr) {
+        const int64_t g1 = std::min(nb, g0 + Gr);
+        // First right block whose largest e exceeds the group's smallest j.
+        int64_t lo = 0, hi = nb;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (emax(mid) > jmin(g0)) hi = mid; else lo = mid + 1;
+        }
+        for (int64_t b = lo; b < nb; ++b)
+            for (int64_t a = g0; a < g1; ++a)
+                if (emax(b) > jmin(a)) tiles.push_back(make_uint2((uint32_t)a, (uint32_t)b));
+    }
+    ntiles4 = (int64_t)tiles.size();
+    const uint64_t kbytes = (uint64_t)Wt * 128;
+    const uint64_t pitch = kbytes + 128;
+    const size_t slab = (size_t)nb * 128 * pitch;
+    if ((e = dev_alloc((void **)&QL, std::max<size_t>(slab, 1))) != cudaSuccess) return cuda_status(e, "order-4 slab");
+    if ((e = dev_alloc((void **)&QR, std::max<size_t>(slab, 1))) != cudaSuccess) return cuda_status(e, "order-4 slab");
+    if ((e = dev_alloc((void **)&lpairs4, sizeof(uint32_t) * std::max<size_t>(lp.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&rpairs4, sizeof(uint32_t) * std::max<size_t>(rp.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&tiles4, sizeof(uint2) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
+        return cuda_status(e, "order-4 lists");
+    cudaMemcpyAsync(lpairs4, lp.data(), sizeof(uint32_t) * lp.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(rpairs4, rp.data(), sizeof(uint32_t) * rp.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(tiles4, tiles.data(), sizeof(uint2) * tiles.size(), cudaMemcpyHostToDevice, stream);
+    if ((e = launch_gate()) != cudaSuccess ||
+        (e = launch_quad_rows(X, S_pad, Wt, lpairs4, nb, (int64_t)pitch, QL, stream)) != cudaSuccess ||
+        (e = launch_quad_rows(X, S_pad, Wt, rpairs4, nb, (int64_t)pitch, QR, stream)) != cudaSuccess)
+        return cuda_status(e, "order-4 slab kernel");
+    note_launches(2);
+    int rc;
+    if ((rc = encode_tmap_u8(&tmapQL, QL, kbytes, pitch, (uint64_t)nb * 128)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&tmapQR, QR, kbytes, pitch, (uint64_t)nb * 128)) != FC_OK) return rc;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "order-4 operands");
+    quads_ready = true;
+    return FC_OK;
+}
+
+int Dataset::quads_dense(float *scores, uint32_t *tables)
+{
+    int rc = prepare_quads();
+    if (rc) return rc;
+    const uint64_t total = binom(S, 4);
+    QuadsArgs qa = quads_args(0, (float)hy64(), (float)(1.0 / (double)M));
+    const size_t ns = scores ? sizeof(float) * (size_t)total : 0;
+    const size_t nt = tables ? sizeof(uint32_t) * 162 * (size_t)total : 0;
+    Arena ar;
+    ar.take(ns);
+    ar.take(nt);
+    ar.take(sizeof(int) * 4);
+    if ((rc = reserve_scratch(ar.off)) != FC_OK) return rc;
+    Arena A2;
+    A2.base = scratch;
+    qa.dump_scores = scores ? (float *)A2.take(ns) : nullptr;
+    if (!scores) A2.take(ns);
+    qa.dump_tables = tables ? (uint32_t *)A2.take(nt) : nullptr;
+    if (!tables) A2.take(nt);
+    qa.tile_counter = (int *)A2.take(sizeof(int) * 4);
+    qa.err = err;
+    cudaError_t e;
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
+    cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
+    if (ns) cudaMemsetAsync(qa.dump_scores, 0, ns, stream);
+    if (nt) cudaMemsetAsync(qa.dump_tables, 0, nt, stream);
+    if (ntiles4 > 0) {
+        const int grid = (int)std::min<int64_t>(sms, ntiles4);
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_quads_tc(MODE_DUMP, tmapQL, tmapQR, qa, grid, stream)) != cudaSuccess)
+            return cuda_status(e, "tensor-core quads kernel");
+        note_launches(1);
+    }
+    uint32_t herr = 0;
+    cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
+    if (ns) cudaMemcpyAsync(scores, qa.dump_scores, ns, cudaMemcpyDeviceToHost, stream);
+    if (nt) cudaMemcpyAsync(tables, qa.dump_tables, nt, cudaMemcpyDeviceToHost, stream);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "quads dump");
+    if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the quads kernel");
+    return FC_OK;
+}
+
 // ---- search ----------------------------------------------------------------
 
 int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
@@ -797,9 +970,12 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         // Order 3 on large SNP counts: tensor-core contraction of pair rows
         // with SNP rows, one launch per slab of pair rows.
         const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
+        // Order 4: tensor-core contraction of pair rows with pair rows.
+        const bool tc4 = k == 4 && quads_tc_eligible(L) && (!no_alloc || quads_ready);
         TuneConfig cfg{};
         PairsArgs pa{};
         TriplesArgs ta{};
+        QuadsArgs qa{};
         int grid = 0;
         if (tc) {
             int rc = prepare_pairs();
@@ -811,6 +987,11 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             if (rc) return rc;
             ta = triples_args(L, (float)hy, (float)(1.0 / Nd));
             grid = sms * (int)slabs3.size();   // every slab launch writes sms lists
+        } else if (tc4) {
+            int rc = prepare_quads();
+            if (rc) return rc;
+            qa = quads_args(L, (float)hy, (float)(1.0 / Nd));
+            grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, ntiles4));
         } else {
             cfg = pick_config(k, L, MODE_TOPN, no_alloc);
             if (cfg.var == VAR_IE) {
@@ -875,6 +1056,16 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             cudaMemsetAsync(pa.tile_counter, 0, sizeof(int), stream);
             if ((e = launch_gate()) != cudaSuccess || (e = launch_pairs_tc(MODE_TOPN, tmap, pa, grid, stream)) != cudaSuccess)
                 return cuda_status(e, "tensor-core pairs kernel");
+        } else if (tc4) {
+            qa.list_score = (float *)p[0];
+            qa.list_rank = (uint64_t *)p[1];
+            qa.gthr = (int *)p[11];
+            qa.tile_counter = (int *)p[11] + 1;
+            qa.err = err;
+            cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
+            cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
+            if ((e = launch_gate()) != cudaSuccess || (e = launch_quads_tc(MODE_TOPN, tmapQL, tmapQR, qa, grid, stream)) != cudaSuccess)
+                return cuda_status(e, "tensor-core quads kernel");
         } else if (tc3) {
             ta.gthr = (int *)p[11];
             ta.tile_counter = (int *)p[11] + 1;
@@ -903,7 +1094,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         note_launches(1);
         last_path_tc = tc;
         last_path_tc3 = tc3;
-        last_sweep_var = (tc || tc3) ? -1 : effective_variant(k, cfg.var, MODE_TOPN);
+        last_path_tc4 = tc4;
+        last_sweep_var = (tc || tc3 || tc4) ? -1 : effective_variant(k, cfg.var, MODE_TOPN);
         // Grid merge.
         const float *src_s = (const float *)p[0];
         const uint64_t *src_r = (const uint64_t *)p[1];
@@ -1244,6 +1436,23 @@ int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64
     return FC_OK;
 }
 
+int fc_quads_dense(fc_handle *h, float *scores, uint32_t *tables)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (!scores && !tables) return set_error(FC_EINVAL, "no output requested");
+        if (h->ds.S < 4) return set_error(FC_EINVAL, "fewer than four SNPs");
+        if (scores && h->ds.S > 160) return set_error(FC_ERANGE, "dense order-4 scores need S <= 160");
+        if (tables && h->ds.S > 64) return set_error(FC_ERANGE, "dense order-4 tables need S <= 64");
+        if (h->ds.W0 == 0 || h->ds.Wt == h->ds.W0)
+            return set_error(FC_EINVAL, "the tensor-core path needs both cases and controls");
+        if ((size_t)pairs_smem_bytes(2, (int)h->ds.M, 0) > (size_t)h->ds.max_smem_optin)
+            return set_error(FC_ERANGE, "too many samples for the tensor-core path");
+        DeviceGuard g(h->ds.device);
+        return h->ds.quads_dense(scores, tables);
+    });
+}
+
 int fc_triples_dense(fc_handle *h, float *scores, uint32_t *tables)
 {
     return guarded([&]() -> int {
@@ -1283,6 +1492,7 @@ int fc_last_search_kind(const fc_handle *h)
     if (!h) return set_error(FC_EINVAL, "NULL handle");
     if (h->ds.last_path_tc) return 2;
     if (h->ds.last_path_tc3) return 6;
+    if (h->ds.last_path_tc4) return 7;
     if (h->ds.last_list == 0) return 0;
     if (h->ds.last_sweep_var == VAR_IE) return 3;
     if (h->ds.last_sweep_var == VAR_JR) return 4;

@@ -86,7 +86,19 @@ struct Dataset {
     int built_slab3 = -1;
     bool triples_ready = false;
     bool last_path_tc3 = false;
-    bool allow_tc3 = true;     // false for the jobs of a batch handle
+    bool allow_slabs = true;   // false for the jobs of a batch handle (no pair-row slabs)
+
+    // Order-4 tensor-core operands, built on first use and kept: left pairs
+    // (i, j) in (j, i) order and right pairs (e, f) in (e, f) order, 12 per
+    // 128-row block, as e4m3 pair-row slabs with all nine genotype pairs; the
+    // tile list (left block, right block) and the slabs' TMA descriptors.
+    uint8_t *QL = nullptr, *QR = nullptr;
+    uint32_t *lpairs4 = nullptr, *rpairs4 = nullptr;
+    uint2 *tiles4 = nullptr;
+    int64_t ntiles4 = 0;
+    CUtensorMap tmapQL{}, tmapQR{};
+    bool quads_ready = false;
+    bool last_path_tc4 = false;
 
     // Optional instrumentation (fc_timing): CUDA events around the sweep
     // kernel on the launching stream, and a count of kernel launches.
@@ -120,6 +132,10 @@ struct Dataset {
     void release_triples();
     TriplesArgs triples_args(int L, float hy, float invN);
     int triples_dense(float *scores, uint32_t *tables);
+    bool quads_tc_eligible(int L);
+    int prepare_quads();
+    QuadsArgs quads_args(int L, float hy, float invN);
+    int quads_dense(float *scores, uint32_t *tables);
     double hy64() const;
     // Inclusion-exclusion sweep (k = 2, 3): per-SNP genotype counts and, for
     // k = 3, the restricted pair table, built on first use.

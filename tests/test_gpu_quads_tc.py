@@ -1,0 +1,108 @@
+"""Order-4 tensor-core path (tcgen05 contraction of 0/1 pair rows with pair
+rows, all 81 cells) against the CPU oracle and against the pair-extension
+sweep."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_config, make_dataset
+from tests.parity_util import assert_topn_equal
+
+pytestmark = pytest.mark.gpu
+
+
+def fp32_bound(k, M):
+    u = 2.0 ** -24
+    return 2.0 * u * (2.0 * math.log(max(M, 2)) + (2.0 * 3 ** k + 6.0) * math.log(2.0))
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2201_03331_gb300 as fcm
+    from paper_2201_03331_gb300 import build
+    build.build()
+    return fcm
+
+
+@pytest.fixture
+def path(monkeypatch):
+    def set_path(p):
+        monkeypatch.setenv("FC_QUADS_PATH", p)
+    return set_path
+
+
+def all_quads(S):
+    return np.array(list(itertools.combinations(range(S), 4)), dtype=np.uint32)
+
+
+@pytest.mark.parametrize("S,cases,controls,seed", [(4, 40, 50, 1), (13, 700, 650, 2), (30, 129, 1000, 3),
+                                                   (41, 1500, 2100, 4), (26, 1, 300, 5), (19, 300, 1, 6)])
+def test_dense_tables_exact(fc, S, cases, controls, seed):
+    """Every combination's 81-cell table, for pair counts that leave partial
+    blocks and ragged sample counts."""
+    ds = make_dataset("q4", seed=800 + seed, S=S, cases=cases, controls=controls, k=4, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    _, tab = fc.fc_quads_dense(h, scores=False, tables=True)
+    ref = oracle.tables(ds.genotypes, ds.phenotype, 4, all_quads(S))
+    bad = np.nonzero(np.any(tab != ref, axis=(1, 2)))[0]
+    assert len(bad) == 0, (len(bad), all_quads(S)[bad[:5]])
+
+
+def test_dense_scores_within_fp32_bound(fc):
+    ds = make_dataset("q4sc", seed=830, S=48, cases=1500, controls=1711, k=4, top_n=5, planted=(3, 17, 30, 44))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    sc, _ = fc.fc_quads_dense(h, scores=True, tables=False)
+    ref = oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 4, all_quads(ds.S)), 4)
+    assert np.abs(sc.astype(np.float64) - ref).max() <= fp32_bound(4, ds.M)
+
+
+@pytest.mark.parametrize("S,cases,controls,top_n", [(40, 900, 1100, 100), (70, 2000, 1000, 60)])
+def test_search_tc_matches_oracle(fc, path, S, cases, controls, top_n):
+    path("tc")
+    ds = make_dataset("q4search", seed=840 + S, S=S, cases=cases, controls=controls, k=4, top_n=top_n,
+                      planted=(3, S // 3, S // 2, S - 5))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    g_idx, g_s = fc.fc_search(h, 4, top_n)
+    assert fc.fc_last_search_kind(h) == 7
+    o_idx, o_s, _ = oracle.search(ds.genotypes, ds.phenotype, 4, top_n)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 4, [c]), 4)[0])
+    assert_topn_equal(g_idx, g_s, o_idx, o_s, score_of)
+    assert tuple(g_idx[0]) == (3, S // 3, S // 2, S - 5)
+
+
+def test_tc_and_sweep_agree_full_size(fc, path):
+    """300 SNPs x 6,000 samples, top 100: the tensor-core path and the
+    pair-extension sweep return the same list; the planted quadruple ranks
+    first and the returned tables are exact."""
+    ds = make_config("C4")
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    path("tc")
+    a = fc.fc_search(h, 4, ds.top_n)
+    assert fc.fc_last_search_kind(h) == 7
+    path("popc")
+    b = fc.fc_search(h, 4, ds.top_n)
+    assert fc.fc_last_search_kind(h) == 5
+    assert np.array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+    assert tuple(a[0][0]) == tuple(ds.planted)
+    o_tab = oracle.tables(ds.genotypes, ds.phenotype, 4, a[0])
+    assert np.array_equal(fc.fc_tables(h, 4, a[0]), o_tab)
+    np.testing.assert_allclose(a[1], oracle.mi(o_tab, 4), rtol=1e-6, atol=1e-12)
+
+
+def test_quads_dense_rejects_bad_inputs(fc):
+    ds = make_dataset("q4bad", seed=860, S=200, cases=100, controls=100, k=4, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    with pytest.raises(fc.FiunchoError):
+        fc.fc_quads_dense(h, scores=True)           # S > 160
+    one = make_dataset("q4one", seed=861, S=12, cases=50, controls=0, k=4, top_n=5)
+    h1 = fc.fc_load(one.genotypes, one.phenotype)
+    with pytest.raises(fc.FiunchoError):
+        fc.fc_quads_dense(h1, scores=True)          # a single class

@@ -368,14 +368,14 @@ def run_ours(args):
     if kind in (2, 6, 7):
         # Tensor-core contraction: contracted cells x M samples x 2 FLOP per
         # combination (orders 2, 3: the 2^k cells with genotypes in {0,1};
-        # order 4: all 81 cells); fp8 peak = measured dense bf16 x 2 (nominal
-        # ratio).
-        cells = {2: 4, 6: 8, 7: 81}[kind]
+        # orders 4-6: all 3^k cells); fp8 peak = measured dense bf16 x 2
+        # (nominal ratio).
+        cells = {2: 4, 6: 8, 7: 3 ** k}[kind]
         flops = math.comb(ds.S, k) * cells * 2 * (ds.cases + ds.controls)
         bf16 = peaks.get("bf16_tflops")
         peak = 2.0 * float(bf16) if bf16 else 2.0 * 1900.0
         achieved = flops / sweep_avg_s / 1e12 if sweeps else None
-        tc_name = {2: "k_pairs_tc", 6: "k_triples_tc", 7: "k_quads_tc"}[kind]
+        tc_name = {2: "k_pairs_tc", 6: "k_triples_tc", 7: f"k_quads_tc<{k}>"}[kind]
         kernel_key = f"{tc_name}<TOPN> {args.workload}"
         roofline = {"bound": "tensor", "kernel": kernel_key, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,

@@ -243,20 +243,21 @@ int fc_pairs_dense(fc_handle *h, float *scores, uint32_t *tables);
 int fc_triples_dense(fc_handle *h, float *scores, uint32_t *tables);
 
 /*
- * fc_quads_dense - every order-4 table or FP32 score computed by the
- * tensor-core quadruple kernel (the k = 4 path fc_search takes from 64 SNPs):
- * all 81 cells as dot products of pair rows (i, j) x pair rows (e, f) over
- * each class's samples (Section "Computing the contingency tables"; mutual
- * information as in fc_search).  A parity hook for the contraction and its
- * epilogue.
- * scores : host float [C(S,4)] or NULL, indexed by lexicographic rank
- *          (S <= 160).
- * tables : host uint32 [C(S,4)][81][2] or NULL, indexed by rank, in the
- *          layout of fc_tables (S <= 64).
+ * fc_tuples_dense - every table or FP32 score of order k = 4, 5 or 6
+ * computed by the tensor-core tuple kernel (the path fc_search takes from
+ * 64 / 48 / 32 SNPs): all 3^k cells as dot products of left tuple rows
+ * (pairs, or triples for k = 6) with right tuple rows (pairs for k = 4,
+ * triples for k = 5, 6) over each class's samples (Section "Computing the
+ * contingency tables"; mutual information as in fc_search).  A parity hook
+ * for the contraction and its epilogue.
+ * scores : host float [C(S,k)] or NULL, indexed by lexicographic rank
+ *          (C(S,k) <= 2^25).
+ * tables : host uint32 [C(S,k)][3^k][2] or NULL, indexed by rank, in the
+ *          layout of fc_tables (C(S,k) * 3^k <= 2^25).
  * Needs both classes non-empty.  Returns FC_OK, FC_EINVAL, FC_ERANGE,
  * FC_ENOMEM, FC_ECUDA or FC_ETIMEOUT.
  */
-int fc_quads_dense(fc_handle *h, float *scores, uint32_t *tables);
+int fc_tuples_dense(fc_handle *h, int k, float *scores, uint32_t *tables);
 
 /* fc_last_search_kind - which sweep the last fc_search on h ran:
  * 0 none yet, 1 prefix-table AND/POPC sweep counting all 3^k cells,
@@ -267,8 +268,8 @@ int fc_quads_dense(fc_handle *h, float *scores, uint32_t *tables);
  * prefix's own table (k = 2..4), 5 (k-2)-prefix table extended by SNP pairs,
  * all 3^k cells counted (k = 4..6), 6 tensor-core order-3 contraction of
  * pair rows with SNP rows (8 cells counted, 19 derived), 7 tensor-core
- * order-4 contraction of pair rows with pair rows (all 81 cells).  Every
- * kind yields the same exact tables. */
+ * contraction of tuple rows with tuple rows, orders 4-6 (all 3^k cells).
+ * Every kind yields the same exact tables. */
 int fc_last_search_kind(const fc_handle *h);
 
 /*

@@ -6,6 +6,7 @@ any entry point raises instead of falling back to anything else.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -45,7 +46,7 @@ _SIGNATURES = {
     "fc_info": ([P, P, P, P, P], i32),
     "fc_pairs_dense": ([P, P, P], i32),
     "fc_triples_dense": ([P, P, P], i32),
-    "fc_quads_dense": ([P, P, P], i32),
+    "fc_tuples_dense": ([P, i32, P, P], i32),
     "fc_load_batch": ([i32, P, P, P, P, i32, P], i32),
     "fc_search_batch": ([P, i32, i64, P, P, P], i32),
     "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
@@ -210,16 +211,16 @@ def fc_triples_dense(h: Handle, scores: bool = True, tables: bool = False):
     return sc, tb
 
 
-def fc_quads_dense(h: Handle, scores: bool = True, tables: bool = False):
-    """Dense order-4 output of the tensor-core kernel, indexed by
-    lexicographic rank: ``(scores float32[C(S,4)] or None, tables
-    uint32[C(S,4)][81][2] or None)``."""
+def fc_tuples_dense(h: Handle, k: int, scores: bool = True, tables: bool = False):
+    """Dense output of order k = 4..6 of the tensor-core tuple kernel,
+    indexed by lexicographic rank: ``(scores float32[C(S,k)] or None, tables
+    uint32[C(S,k)][3^k][2] or None)``."""
     S = fc_info(h)[0]
-    n = S * (S - 1) * (S - 2) * (S - 3) // 24
+    n = math.comb(S, k)
     sc = np.zeros(n, dtype=np.float32) if scores else None
-    tb = np.zeros((n, 81, 2), dtype=np.uint32) if tables else None
-    _check(library().fc_quads_dense(h.ptr, _ptr(sc) if sc is not None else None,
-                                    _ptr(tb) if tb is not None else None), "fc_quads_dense")
+    tb = np.zeros((n, 3 ** k, 2), dtype=np.uint32) if tables else None
+    _check(library().fc_tuples_dense(h.ptr, k, _ptr(sc) if sc is not None else None,
+                                     _ptr(tb) if tb is not None else None), "fc_tuples_dense")
     return sc, tb
 
 

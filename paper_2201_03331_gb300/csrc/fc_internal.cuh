@@ -293,36 +293,40 @@ cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S,
 cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapE, const CUtensorMap &tmapP, const TriplesArgs &a,
                               int grid, cudaStream_t st);
 
-// Order-4 tensor-core search (fc_quads_tc.cu).  Two slabs of pair rows with
-// all nine genotype pairs: "left" pairs (i, j) in (j, i) order and "right"
-// pairs (e, f) in (e, f) order, 12 pairs per 128-row block (in each 32-row
-// quarter 3 pairs x 9 rows, then 5 zero rows).  A tile is one left block x
-// one right block.
-constexpr int Q4_PAIRS_PER_BLOCK = 12;
+// Orders 4 to 6 on tensor cores (fc_quads_tc.cu): left tuples of LT SNPs
+// x right tuples of RT SNPs, k = LT + RT (2 + 2, 2 + 3, 3 + 3).  Each side is
+// a slab of tuple rows with all 3^T genotype combinations, left tuples in
+// order of their last SNP, right tuples in order of their first; a 128-row
+// block holds 27 / 3^T tuples in each 32-row quarter (27 rows, then 5 zero
+// rows): 12 pairs or 4 triples.  A tile is one left block x one right block.
+constexpr int tc_left_size(int k) { return k == 6 ? 3 : 2; }
+constexpr int tc_tuples_per_block(int T) { return 4 * (27 / (T == 2 ? 9 : 27)); }
+constexpr uint64_t NO_TUPLE = ~0ull;
 struct QuadsArgs {
     const uint2 *tiles;     // {left block, right block} per tile
     int ntiles;
     int64_t S;
     int W0, Wt;
-    const uint32_t *lpairs; // [n left blocks * 12]: i | j << 16, or ~0u for padding
-    const uint32_t *rpairs; // [n right blocks * 12]: e | f << 16, or ~0u
+    const uint64_t *ltup;   // left tuples: SNP t in bits [16 t, 16 t + 16), NO_TUPLE for padding
+    const uint64_t *lrank;  // rank part of a left tuple (the terms of its SNPs and of its last SNP)
+    const uint64_t *rtup;   // right tuples
+    const uint64_t *rrank;  // rank part of a right tuple (modulo 2^64)
     const float *xlogx;     // x ln x for x = 0..M
     int M;
     float hy, invN;
-    uint64_t total;         // C(S, 4)
     int L, Bcap, P2, stages;
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
     int *gthr;
     int *tile_counter;
     uint32_t *err;
-    float *dump_scores;     // MODE_DUMP: [C(S,4)] by rank
-    uint32_t *dump_tables;  // MODE_DUMP: [C(S,4)][81][2]
+    float *dump_scores;     // MODE_DUMP: [C(S,k)] by rank
+    uint32_t *dump_tables;  // MODE_DUMP: [C(S,k)][3^k][2]
 };
 
-cudaError_t launch_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_t *pairs, int64_t nblocks,
-                             int64_t pitch, uint8_t *Q, cudaStream_t st);
-cudaError_t launch_quads_tc(int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
+cudaError_t launch_tuple_rows(int T, const uint4 *X, int64_t S_pad, int Wt, const uint64_t *tuples, int64_t nblocks,
+                              int64_t pitch, uint8_t *Q, cudaStream_t st);
+cudaError_t launch_quads_tc(int k, int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
                             int grid, cudaStream_t st);
 
 struct TablesArgs {

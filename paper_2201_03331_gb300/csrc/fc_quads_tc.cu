@@ -1,35 +1,40 @@
-// Order-4 exhaustive search on the fifth-generation tensor cores (tcgen05).
+// Orders 4 to 6 of the exhaustive search on the fifth-generation tensor
+// cores (tcgen05).
 //
-// For a combination (i, j, e, f) every cell of the 3^4 table is, per class c
-// (Section "Computing the contingency tables": the population count of the
-// AND of one row of each SNP's table),
-//     n_c(a, b, g, h) = < P_c[(i, j), (a, b)], P_c[(e, f), (g, h)] >,
-// the dot product over the samples of two pair rows P[(s, t), (a, b)] =
-// [G_s = a][G_t = b] stored as 0/1 e4m3 bytes.  With the left operand a block
-// of 12 pairs (i, j) and the right operand a block of 12 pairs (e, f), both
-// with all nine genotype pairs, one 128 x 128 tcgen05.mma kind::f8f6f4 tile
-// per class yields all 81 cells of 144 combinations at once (exact: products
-// of 0/1, FP32 sums of integers below 2^24).  No cell is derived: the table
-// is complete, and combinations with j < e are the valid ones.
+// A k-combination is a left tuple of LT SNPs followed by a right tuple of RT
+// SNPs (k = LT + RT: 2 + 2, 2 + 3, 3 + 3).  Every cell of its 3^k table is,
+// per class c (Section "Computing the contingency tables": the population
+// count of the AND of one row of each SNP's table),
+//     n_c(cell_L, cell_R) = < P_c[left, cell_L], P_c[right, cell_R] >,
+// the dot product over the samples of two tuple rows P[t, d] = [G_t = d]
+// (all SNPs of tuple t at genotypes d) stored as 0/1 e4m3 bytes.  With the
+// left operand a block of left tuples and the right operand a block of right
+// tuples, both with all 3^T genotype rows, one 128 x 128 tcgen05.mma
+// kind::f8f6f4 tile per class yields every cell of every combination of the
+// two blocks (exact: products of 0/1, FP32 sums of integers below 2^24).
+// No cell is derived; combinations whose left tuple ends before the right
+// tuple starts are the valid ones.
 //
-// Row layout of a 128-row block (left and right alike): 32-row quarter w
-// holds pairs 3w, 3w + 1, 3w + 2 in rows 9p + 3a + b (p the pair within the
-// quarter), rows 27..31 zero.  So one TMEM lane quarter (one epilogue warp)
-// holds three left pairs whole, and a thread owns the 9 cells (g, h) of its
-// (pair, a, b) row against each right pair.
+// Row layout of a 128-row block: each 32-row quarter holds 27 / 3^T tuples
+// (3 pairs or 1 triple) in rows 3^T t + d, then 5 zero rows.  So one TMEM
+// lane quarter (one epilogue warp) holds whole left tuples, and a thread
+// owns the 3^RT cells of its (left tuple, d) row against each right tuple.
 //
 // Scoring: MI = H(Y) - (1/N) sum_cells [x ln x (n) - x ln x (a) - x ln x (b)]
 // with a table of x ln x correctly rounded to FP32.  Each thread sums the
-// terms of its 9 cells, the 9 lanes of a pair add their partial sums; every
-// addend is a sum of non-negative cell terms bounded by N ln 2.  As for
-// order 3, |MI32 - MI| <= u (3 ln M + (3^4 + 4) ln 2) (u = 2^-24), within the
-// sweep's bound u (2 ln M + (2 3^4 + 6) ln 2) for every M < 2^83.
+// terms of its row's cells, the 3^LT lanes of a left tuple add their partial
+// sums; every addend is a sum of non-negative cell terms bounded by N ln 2.
+// As for order 3, |MI32 - MI| <= u (3 ln M + (3^k + 4) ln 2) (u = 2^-24),
+// within the sweep's bound u (2 ln M + (2 3^k + 6) ln 2) for M < 2^(3^k + 2).
+// The lexicographic rank of a combination is the sum of a part that depends
+// on the left tuple only and one that depends on the right tuple only, both
+// computed on the host.
 //
 // Roles (one persistent CTA per SM, 192 threads), as in the order-2 kernel:
 //   warp 0 : TMA producer (128-byte K chunks of the left and right blocks)
 //   warp 1 : TMEM allocation and the single-thread MMA issue
-//   warps 2-5 : epilogue (TMEM -> registers -> 9-cell partial MI -> pair sum
-//               -> CTA top list)
+//   warps 2-5 : epilogue (TMEM -> registers -> partial MI over a row's cells
+//               -> sum over a left tuple's lanes -> CTA top list)
 // Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
 #include "fc_tc.cuh"
 
@@ -37,11 +42,15 @@ namespace fc {
 
 namespace {
 
-// Pair-row slab: thread (row, 16-byte chunk) of block row rows; the row is
-// [G_s = a][G_t = b] over 16 samples of one class word, expanded to bytes.
-__global__ void k_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_t *pairs, int64_t nblocks,
-                            int64_t pitch, uint8_t *Q)
+// Tuple-row slab: thread (row, 16-byte chunk); the row is [G_t = d] (every
+// SNP of the tuple at its genotype digit, first SNP most significant) over
+// 16 samples of one class word, expanded to bytes.
+template <int T>
+__global__ void k_tuple_rows(const uint4 *X, int64_t S_pad, int Wt, const uint64_t *tuples, int64_t nblocks,
+                             int64_t pitch, uint8_t *Q)
 {
+    constexpr int R = T == 2 ? 9 : 27;              // rows per tuple
+    constexpr int PQ = 27 / R;                      // tuples per quarter
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int cw = 8 * Wt;                          // 16-byte chunks per row
     if (t >= nblocks * 128 * cw) return;
@@ -52,17 +61,21 @@ __global__ void k_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_
     const int quarter = r >> 5, r32 = r & 31;
     uint32_t bits = 0;
     if (r32 < 27) {
-        const uint32_t pr = pairs[blk * Q4_PAIRS_PER_BLOCK + quarter * 3 + r32 / 9];
-        if (pr != ~0u) {
-            const uint32_t s = pr & 0xffffu, u = pr >> 16;
-            const int ab = r32 % 9;
+        const uint64_t tup = tuples[blk * (4 * PQ) + quarter * PQ + r32 / R];
+        if (tup != NO_TUPLE) {
             const int w = ch >> 3, sub = ch & 7;    // 128-sample word, 16-sample part
-            const uint4 x = X[((size_t)w * 3 + ab / 3) * S_pad + s];
-            const uint4 y = X[((size_t)w * 3 + ab % 3) * S_pad + u];
             const int q32 = sub >> 1;
-            const uint32_t xw = q32 == 0 ? x.x : q32 == 1 ? x.y : q32 == 2 ? x.z : x.w;
-            const uint32_t yw = q32 == 0 ? y.x : q32 == 1 ? y.y : q32 == 2 ? y.z : y.w;
-            bits = ((xw & yw) >> ((sub & 1) * 16)) & 0xffffu;
+            uint32_t acc = ~0u;
+            int d = r32 % R;
+#pragma unroll
+            for (int u = T - 1; u >= 0; --u) {
+                const int g = d % 3;
+                d /= 3;
+                const uint32_t s = (uint32_t)(tup >> (16 * u)) & 0xffffu;
+                const uint4 x = X[((size_t)w * 3 + g) * S_pad + s];
+                acc &= q32 == 0 ? x.x : q32 == 1 ? x.y : q32 == 2 ? x.z : x.w;
+            }
+            bits = (acc >> ((sub & 1) * 16)) & 0xffffu;
         }
     }
     uint32_t o[4];
@@ -76,14 +89,15 @@ __global__ void k_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_
     *(reinterpret_cast<uint4 *>(Q + row * pitch) + ch) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
-__device__ __forceinline__ uint64_t cn4(uint64_t n) { return n < 4 ? 0 : n * (n - 1) * (n - 2) * (n - 3) / 24; }
-__device__ __forceinline__ uint64_t cn3(uint64_t n) { return n < 3 ? 0 : n * (n - 1) * (n - 2) / 6; }
-__device__ __forceinline__ uint64_t cn2(uint64_t n) { return n < 2 ? 0 : n * (n - 1) / 2; }
-
-template <int MODE>
+template <int LT, int RT, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_quads_tc(const __grid_constant__ CUtensorMap tmapL, const __grid_constant__ CUtensorMap tmapR, QuadsArgs a)
 {
+    constexpr int RL = LT == 2 ? 9 : 27;            // rows (cells) per left tuple
+    constexpr int RR = RT == 2 ? 9 : 27;            // columns (cells) per right tuple
+    constexpr int LPQ = 27 / RL;                    // left tuples per lane quarter
+    constexpr int RPC = 27 / RR;                    // right tuples per 32-column chunk
+    constexpr int CK = RL * RR;                     // cells of a table (3^k)
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_full[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_done;
@@ -228,13 +242,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ---------------- epilogue ----------------
-        // TMEM lane = left row 32 w + 9 p + 3 a_i + a_j; column 32 c + 9 q + 3 g + h
-        // = right pair 3 c + q of the tile, genotypes (g, h) of (e, f).
+        // TMEM lane = left row 32 w + RL p + d_L; column 32 c + RR q + d_R =
+        // right tuple RPC c + q of the tile, genotype digits d_R.
         const int tid = threadIdx.x - 64;           // 0..127
         const int quarter = warp & 3;
-        const int p = lane / 9;                     // left pair within the quarter (3 = padding lanes)
-        const int cell_ab = lane - 9 * p;           // 3 a + b of this lane's row
-        const int seg0 = 9 * min(p, 2);             // first lane of this pair's 9 lanes
+        const int p = lane / RL;                    // left tuple within the quarter (LPQ: padding lanes)
+        const int cell_l = lane - RL * p;           // genotype digits of this lane's row
+        const int seg0 = RL * min(p, LPQ - 1);      // first lane of this left tuple
         const int L = a.L;
         const int Bcap = a.Bcap;
         const uint32_t lt = (uint32_t)a.M;
@@ -260,14 +274,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (epi_stop || t < 0) break;
             tc_fence_after();
             const uint2 tile = a.tiles[t];
-            // This lane's left pair (i, j).
-            uint32_t lp = ~0u;
-            if (p < 3) lp = a.lpairs[(size_t)tile.x * Q4_PAIRS_PER_BLOCK + quarter * 3 + p];
-            const int64_t pi = lp & 0xffffu, pj = lp >> 16;
-            const uint64_t base_ij = (lp != ~0u)
-                                         ? a.total - cn4((uint64_t)(a.S - pi)) + cn3((uint64_t)(a.S - pi - 1)) -
-                                               cn3((uint64_t)(a.S - pj))
-                                         : 0;
+            // This lane's left tuple: its last SNP and its part of the rank.
+            uint64_t ltp = NO_TUPLE, lrk = 0;
+            if (p < LPQ) {
+                const size_t li = (size_t)tile.x * (4 * LPQ) + quarter * LPQ + p;
+                ltp = a.ltup[li];
+                lrk = a.lrank[li];
+            }
+            const uint32_t llast = (uint32_t)(ltp >> (16 * (LT - 1))) & 0xffffu;
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
             for (int ch = 0; ch < 4; ++ch) {
                 uint32_t v0[32], v1[32];
@@ -281,45 +295,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar_tempty[b]);
                 }
-                float sc[3];
-                uint64_t rk[3];
-                bool val[3];
+                float sc[RPC];
+                uint64_t rk[RPC];
+                bool val[RPC];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    // Right pair 3 ch + q: 9 cells (g, h) of this row.
-                    const uint32_t rp = a.rpairs[(size_t)tile.y * Q4_PAIRS_PER_BLOCK + ch * 3 + q];
-                    const int64_t pe = rp & 0xffffu, pf = rp >> 16;
+                for (int q = 0; q < RPC; ++q) {
+                    // Right tuple RPC ch + q: the RR cells of this row.
+                    const size_t ri = (size_t)tile.y * (4 * RPC) + ch * RPC + q;
+                    const uint64_t rtp = a.rtup[ri];
+                    const uint32_t rfirst = (uint32_t)rtp & 0xffffu;
                     float part = 0.f;
-                    uint32_t cnt[9][2];
 #pragma unroll
-                    for (int gh = 0; gh < 9; ++gh) {
+                    for (int c = 0; c < RR; ++c) {
                         // Clamped so that no index can leave the table.
-                        const uint32_t ca = min(f2u_exact(v0[9 * q + gh]), lt);
-                        const uint32_t cb = min(f2u_exact(v1[9 * q + gh]), lt);
+                        const uint32_t ca = min(f2u_exact(v0[RR * q + c]), lt);
+                        const uint32_t cb = min(f2u_exact(v1[RR * q + c]), lt);
                         const uint32_t n = min(ca + cb, lt);
                         part += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
-                        cnt[gh][0] = ca;
-                        cnt[gh][1] = cb;
                     }
-                    // Sum over the 9 lanes of this left pair.
+                    // Sum over the RL lanes of this left tuple.
                     float tot = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 9; ++k) tot += __shfl_sync(FULL, part, min(seg0 + k, 31));
-                    const bool valid = p < 3 && lp != ~0u && rp != ~0u && pj < pe;
+                    for (int k2 = 0; k2 < RL; ++k2) tot += __shfl_sync(FULL, part, min(seg0 + k2, 31));
+                    const bool valid = p < LPQ && ltp != NO_TUPLE && rtp != NO_TUPLE && llast < rfirst;
                     const float score = fmaf(-tot, a.invN, a.hy);
-                    // Lexicographic rank of (i, j, e, f).
-                    const uint64_t rank =
-                        valid ? base_ij + cn2((uint64_t)(a.S - pj - 1)) - cn2((uint64_t)(a.S - pe)) + (uint64_t)(pf - pe - 1)
-                              : NO_RANK;
+                    const uint64_t rank = valid ? lrk + a.rrank[ri] : NO_RANK;   // modulo 2^64
                     sc[q] = score;
                     rk[q] = rank;
-                    val[q] = valid && cell_ab == 0;
+                    val[q] = valid && cell_l == 0;
                     if (MODE == MODE_DUMP && valid) {
-                        if (a.dump_scores && cell_ab == 0) a.dump_scores[rank] = score;
+                        if (a.dump_scores && cell_l == 0) a.dump_scores[rank] = score;
                         if (a.dump_tables) {
-                            uint32_t *o = a.dump_tables + (size_t)rank * 162 + (size_t)cell_ab * 18;
+                            uint32_t *o = a.dump_tables + (size_t)rank * (2 * CK) + (size_t)cell_l * (2 * RR);
 #pragma unroll
-                            for (int gh = 0; gh < 9; ++gh) { o[2 * gh] = cnt[gh][0]; o[2 * gh + 1] = cnt[gh][1]; }
+                            for (int c = 0; c < RR; ++c) {
+                                o[2 * c] = min(f2u_exact(v0[RR * q + c]), lt);
+                                o[2 * c + 1] = min(f2u_exact(v1[RR * q + c]), lt);
+                            }
                         }
                     }
                 }
@@ -329,7 +341,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     epi_bar();
                     const int fill_now = buf_count;
                     epi_bar();
-                    if (fill_now > Bcap - 3 * 128) {
+                    if (fill_now > Bcap - RPC * 128) {
                         const int nb = buf_count;
                         for (int x = L + nb + tid; x < a.P2; x += 128) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
                         epi_bitonic_desc(lscore, lrank, a.P2, tid);
@@ -343,7 +355,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     thr_r = lrank[L - 1];
                     const float gthr = from_ordered(*(volatile int *)a.gthr);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
+                    for (int q = 0; q < RPC; ++q) {
                         const bool cand = val[q] && sc[q] >= gthr && better(sc[q], rk[q], thr_s, thr_r);
                         const unsigned mk = __ballot_sync(FULL, cand);
                         int base = 0;
@@ -381,21 +393,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 }  // namespace
 
-cudaError_t launch_quad_rows(const uint4 *X, int64_t S_pad, int Wt, const uint32_t *pairs, int64_t nblocks,
-                             int64_t pitch, uint8_t *Q, cudaStream_t st)
+cudaError_t launch_tuple_rows(int T, const uint4 *X, int64_t S_pad, int Wt, const uint64_t *tuples, int64_t nblocks,
+                              int64_t pitch, uint8_t *Q, cudaStream_t st)
 {
     const int64_t n = nblocks * 128 * 8 * (int64_t)Wt;
     if (n == 0) return cudaSuccess;
-    k_quad_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S_pad, Wt, pairs, nblocks, pitch, Q);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (T == 2) k_tuple_rows<2><<<grid, 256, 0, st>>>(X, S_pad, Wt, tuples, nblocks, pitch, Q);
+    else k_tuple_rows<3><<<grid, 256, 0, st>>>(X, S_pad, Wt, tuples, nblocks, pitch, Q);
     return cudaGetLastError();
 }
 
-cudaError_t launch_quads_tc(int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
+cudaError_t launch_quads_tc(int k, int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
                             int grid, cudaStream_t st)
 {
     const size_t bytes = pairs_smem_bytes(a.stages, a.M, a.P2);
-    void *fn = mode == MODE_TOPN ? reinterpret_cast<void *>(&k_quads_tc<MODE_TOPN>)
-                                 : reinterpret_cast<void *>(&k_quads_tc<MODE_DUMP>);
+    void *fn = nullptr;
+    const bool top = mode == MODE_TOPN;
+    if (k == 4) fn = top ? reinterpret_cast<void *>(&k_quads_tc<2, 2, MODE_TOPN>) : reinterpret_cast<void *>(&k_quads_tc<2, 2, MODE_DUMP>);
+    if (k == 5) fn = top ? reinterpret_cast<void *>(&k_quads_tc<2, 3, MODE_TOPN>) : reinterpret_cast<void *>(&k_quads_tc<2, 3, MODE_DUMP>);
+    if (k == 6) fn = top ? reinterpret_cast<void *>(&k_quads_tc<3, 3, MODE_TOPN>) : reinterpret_cast<void *>(&k_quads_tc<3, 3, MODE_DUMP>);
+    if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     CUtensorMap mL = tmapL, mR = tmapR;

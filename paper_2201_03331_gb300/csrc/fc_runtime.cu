@@ -215,11 +215,7 @@ Dataset::~Dataset()
     cudaFree(PR);
     cudaFree(P3);
     cudaFree(xlogx);
-    cudaFree(QL);
-    cudaFree(QR);
-    cudaFree(lpairs4);
-    cudaFree(rpairs4);
-    cudaFree(tiles4);
+    for (int k = 4; k <= 6; ++k) release_tuples(k);
     cudaFree(tiles3);
     cudaFree(rowbase3);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
@@ -774,52 +770,93 @@ int Dataset::triples_dense(float *scores, uint32_t *tables)
     return FC_OK;
 }
 
-// ---- order-4 tensor-core operands ----------------------------------------------
+// ---- orders 4-6 on tensor cores: tuple operands ---------------------------------
 
 namespace {
-// Pairs usable on each side of an order-4 combination: left (i, j) needs
-// j <= S - 3, right (e, f) needs e >= 2; both counts are (S-3)(S-2)/2.
-int64_t quad_side_pairs(int64_t S) { return S < 4 ? 0 : (S - 3) * (S - 2) / 2; }
-int64_t quad_blocks(int64_t S) { return (quad_side_pairs(S) + Q4_PAIRS_PER_BLOCK - 1) / Q4_PAIRS_PER_BLOCK; }
-// Tiles of the plan below, about S^4 / 3456; bounded so the list stays small.
-constexpr int64_t Q4_MAX_TILES = (int64_t)1 << 25;
+constexpr int64_t TUP_MAX_TILES = (int64_t)1 << 25;
+
+// Left tuples (SNPs c_0 < .. < c_{LT-1} with c_{LT-1} <= S - 1 - RT) in order of
+// their last SNP, right tuples (c_0 >= LT) in lexicographic order; SNP t of a
+// tuple in bits [16 t, 16 t + 16).
+void enum_tuples(int64_t S, int T, bool left, int other, std::vector<uint64_t> &out)
+{
+    out.clear();
+    if (T == 2) {
+        if (left) {
+            for (int64_t j = 1; j <= S - 1 - other; ++j)
+                for (int64_t i = 0; i < j; ++i) out.push_back((uint64_t)i | ((uint64_t)j << 16));
+        } else {
+            for (int64_t e = other; e <= S - 2; ++e)
+                for (int64_t f = e + 1; f < S; ++f) out.push_back((uint64_t)e | ((uint64_t)f << 16));
+        }
+    } else {
+        if (left) {
+            for (int64_t l = 2; l <= S - 1 - other; ++l)
+                for (int64_t j = 1; j < l; ++j)
+                    for (int64_t i = 0; i < j; ++i)
+                        out.push_back((uint64_t)i | ((uint64_t)j << 16) | ((uint64_t)l << 32));
+        } else {
+            for (int64_t e = other; e <= S - 3; ++e)
+                for (int64_t f = e + 1; f <= S - 2; ++f)
+                    for (int64_t g = f + 1; g < S; ++g)
+                        out.push_back((uint64_t)e | ((uint64_t)f << 16) | ((uint64_t)g << 32));
+        }
+    }
+}
+
+int64_t tuple_count(int64_t S, int T, int other)
+{
+    // Left and right counts are equal: C(S - other, T).
+    return (int64_t)binom(S - other, T);
+}
 }  // namespace
 
-bool Dataset::quads_tc_eligible(int L)
+bool Dataset::tuples_tc_eligible(int k, int L)
 {
+    if (k < 4 || k > 6) return false;
     const char *mode = getenv("FC_QUADS_PATH");
     if (mode && strcmp(mode, "popc") == 0) return false;
     if (!allow_slabs) return false;
     const bool forced = mode && strcmp(mode, "tc") == 0;
-    if (!forced && S < 64) return false;
-    if (S < 4 || S > 65535 || L > 2048) return false;
+    const int64_t Smin = k == 4 ? 64 : k == 5 ? 48 : 32;
+    if (!forced && S < Smin) return false;
+    if (S < k || S > 65535 || L > 2048) return false;
     if (W0 == 0 || Wt == W0) return false;
-    if ((double)S * S * S * S / 3456.0 > (double)Q4_MAX_TILES) return false;
-    const double slab = 2.0 * (double)quad_blocks(S) * 128.0 * ((double)Wt * 128 + 128);
+    const int LT = tc_left_size(k), RT = k - LT;
+    const int64_t nl = tuple_count(S, LT, RT), nr = tuple_count(S, RT, LT);
+    const int64_t bl = (nl + tc_tuples_per_block(LT) - 1) / tc_tuples_per_block(LT);
+    const int64_t br = (nr + tc_tuples_per_block(RT) - 1) / tc_tuples_per_block(RT);
+    // Tiles: combinations over the combinations of a tile, plus the block
+    // diagonal; the list stays below 2^25 entries.
+    const double tiles = (double)binom(S, k) / (tc_tuples_per_block(LT) * tc_tuples_per_block(RT)) + (double)bl;
+    if (tiles > (double)TUP_MAX_TILES) return false;
+    const double slab = (double)(bl + br) * 128.0 * ((double)Wt * 128 + 128);
     size_t free_b = 0, total_b = 0;
-    double cap = 32.0 * 1024 * 1024 * 1024;
+    double cap = 64.0 * 1024 * 1024 * 1024;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, (double)free_b / 4);
-    if (!quads_ready && slab > cap) return false;
+    if (!tup[k - 4].ready && slab > cap) return false;
     const int Bcap = std::max(L, 1024);
     const int P2 = pow2_at_least(L + Bcap);
     return pairs_smem_bytes(2, (int)M, P2) <= (size_t)max_smem_optin;
 }
 
-QuadsArgs Dataset::quads_args(int L, float hy, float invN)
+QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
 {
+    const TupleTC &u = tup[k - 4];
     QuadsArgs qa{};
-    qa.tiles = tiles4;
-    qa.ntiles = (int)ntiles4;
+    qa.tiles = u.tiles;
+    qa.ntiles = (int)u.ntiles;
     qa.S = S;
     qa.W0 = W0;
     qa.Wt = Wt;
-    qa.lpairs = lpairs4;
-    qa.rpairs = rpairs4;
+    qa.ltup = u.lt;
+    qa.lrank = u.lr;
+    qa.rtup = u.rt;
+    qa.rrank = u.rr;
     qa.xlogx = xlogx;
     qa.M = (int)M;
     qa.hy = hy;
     qa.invN = invN;
-    qa.total = binom(S, 4);
     qa.L = L;
     qa.Bcap = L > 0 ? std::max(L, 1024) : 0;
     qa.P2 = L > 0 ? pow2_at_least(L + qa.Bcap) : 0;
@@ -830,13 +867,35 @@ QuadsArgs Dataset::quads_args(int L, float hy, float invN)
     return qa;
 }
 
-// Pair lists, tile plan, slabs and descriptors.  Tiles come in groups of 64
-// left blocks: for each right block with a usable pair (largest e above the
-// group's smallest j) the group's left blocks follow one another, so the
-// group stays in L2 while the right blocks stream.
-int Dataset::prepare_quads()
+void Dataset::release_tuples(int k)
 {
-    if (quads_ready) return FC_OK;
+    TupleTC &u = tup[k - 4];
+    if (!u.QL && !u.QR && !u.lt && !u.tiles) return;
+    if (stream) cudaStreamSynchronize(stream);
+    cudaFree(u.QL);
+    cudaFree(u.QR);
+    cudaFree(u.lt);
+    cudaFree(u.lr);
+    cudaFree(u.rt);
+    cudaFree(u.rr);
+    cudaFree(u.tiles);
+    u = TupleTC{};
+}
+
+// Tuples with their parts of the rank, the tile plan, slabs and descriptors.
+// The lexicographic rank of (left, right) is the sum over positions t of
+// C(S - c_{t-1} - 1, k - t) - C(S - c_t, k - t) (c_{-1} = -1): the terms of
+// the left SNPs plus C(S - c_{LT-1} - 1, k - LT) go with the left tuple, the
+// rest with the right tuple (modulo 2^64).  Tiles come in groups of left
+// blocks that fit in about 96 MB of L2: for each right block with a usable
+// tuple (largest first SNP above the group's smallest last SNP) the group's
+// left blocks follow one another while the right blocks stream.
+int Dataset::prepare_tuples(int k)
+{
+    TupleTC &u = tup[k - 4];
+    if (u.ready) return FC_OK;
+    for (int k2 = 4; k2 <= 6; ++k2)
+        if (k2 != k) release_tuples(k2);
     cudaError_t e;
     if (!xlogx) {
         if ((e = dev_alloc((void **)&xlogx, sizeof(float) * (size_t)(M + 1))) != cudaSuccess)
@@ -845,70 +904,98 @@ int Dataset::prepare_quads()
             return cuda_status(e, "x ln x table");
         note_launches(1);
     }
-    const int64_t nb = quad_blocks(S);
-    std::vector<uint32_t> lp((size_t)nb * Q4_PAIRS_PER_BLOCK, ~0u), rp((size_t)nb * Q4_PAIRS_PER_BLOCK, ~0u);
-    {
-        size_t n = 0;
-        for (int64_t j = 1; j <= S - 3; ++j)
-            for (int64_t i = 0; i < j; ++i) lp[n++] = (uint32_t)i | ((uint32_t)j << 16);
-        n = 0;
-        for (int64_t a0 = 2; a0 <= S - 2; ++a0)
-            for (int64_t f = a0 + 1; f < S; ++f) rp[n++] = (uint32_t)a0 | ((uint32_t)f << 16);
-    }
-    const int64_t npairs = quad_side_pairs(S);
-    auto jmin = [&](int64_t blk) { return (int64_t)(lp[(size_t)blk * Q4_PAIRS_PER_BLOCK] >> 16); };
-    auto emax = [&](int64_t blk) {
-        const int64_t last = std::min<int64_t>((blk + 1) * Q4_PAIRS_PER_BLOCK, npairs) - 1;
-        return (int64_t)(rp[(size_t)last] & 0xffffu);
-    };
-    std::vector<uint2> tiles;
-    const int64_t Gr = 64;
-    for (int64_t g0 = 0; g0 < nb; g0 += Gr) {
-        const int64_t g1 = std::min(nb, g0 + Gr);
-        // First right block whose largest e exceeds the group's smallest j.
-        int64_t lo = 0, hi = nb;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) / 2;
-            if (emax(mid) > jmin(g0)) hi = mid; else lo = mid + 1;
+    const int LT = tc_left_size(k), RT = k - LT;
+    const int LPB = tc_tuples_per_block(LT), RPB = tc_tuples_per_block(RT);
+    std::vector<uint64_t> lt, rt;
+    enum_tuples(S, LT, true, RT, lt);
+    enum_tuples(S, RT, false, LT, rt);
+    const int64_t nl = (int64_t)lt.size(), nr = (int64_t)rt.size();
+    const int64_t bl = (nl + LPB - 1) / LPB, br = (nr + RPB - 1) / RPB;
+    auto snp = [](uint64_t t, int i) { return (int64_t)((t >> (16 * i)) & 0xffffu); };
+    std::vector<uint64_t> lr(lt.size()), rr(rt.size());
+    for (size_t x = 0; x < lt.size(); ++x) {
+        uint64_t r = 0;
+        int64_t prev = -1;
+        for (int t = 0; t < LT; ++t) {
+            const int64_t c = snp(lt[x], t);
+            r += binom(S - prev - 1, k - t) - binom(S - c, k - t);
+            prev = c;
         }
-        for (int64_t b = lo; b < nb; ++b)
-            for (int64_t a = g0; a < g1; ++a)
-                if (emax(b) > jmin(a)) tiles.push_back(make_uint2((uint32_t)a, (uint32_t)b));
+        lr[x] = r + binom(S - prev - 1, k - LT);
     }
-    ntiles4 = (int64_t)tiles.size();
+    for (size_t x = 0; x < rt.size(); ++x) {
+        uint64_t r = 0 - binom(S - snp(rt[x], 0), k - LT);
+        int64_t prev = snp(rt[x], 0);
+        for (int t = LT + 1; t < k; ++t) {
+            const int64_t c = snp(rt[x], t - LT);
+            r += binom(S - prev - 1, k - t) - binom(S - c, k - t);
+            prev = c;
+        }
+        rr[x] = r;
+    }
+    lt.resize((size_t)bl * LPB, NO_TUPLE);
+    lr.resize((size_t)bl * LPB, 0);
+    rt.resize((size_t)br * RPB, NO_TUPLE);
+    rr.resize((size_t)br * RPB, 0);
+    auto lmin = [&](int64_t blk) { return snp(lt[(size_t)blk * LPB], LT - 1); };
+    auto rmax = [&](int64_t blk) {
+        const int64_t last = std::min<int64_t>((blk + 1) * RPB, nr) - 1;
+        return snp(rt[(size_t)last], 0);
+    };
     const uint64_t kbytes = (uint64_t)Wt * 128;
     const uint64_t pitch = kbytes + 128;
-    const size_t slab = (size_t)nb * 128 * pitch;
-    if ((e = dev_alloc((void **)&QL, std::max<size_t>(slab, 1))) != cudaSuccess) return cuda_status(e, "order-4 slab");
-    if ((e = dev_alloc((void **)&QR, std::max<size_t>(slab, 1))) != cudaSuccess) return cuda_status(e, "order-4 slab");
-    if ((e = dev_alloc((void **)&lpairs4, sizeof(uint32_t) * std::max<size_t>(lp.size(), 1))) != cudaSuccess ||
-        (e = dev_alloc((void **)&rpairs4, sizeof(uint32_t) * std::max<size_t>(rp.size(), 1))) != cudaSuccess ||
-        (e = dev_alloc((void **)&tiles4, sizeof(uint2) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
-        return cuda_status(e, "order-4 lists");
-    cudaMemcpyAsync(lpairs4, lp.data(), sizeof(uint32_t) * lp.size(), cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(rpairs4, rp.data(), sizeof(uint32_t) * rp.size(), cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(tiles4, tiles.data(), sizeof(uint2) * tiles.size(), cudaMemcpyHostToDevice, stream);
+    const int64_t Gr = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((96ull << 20) / (128 * pitch))));
+    std::vector<uint2> tiles;
+    for (int64_t g0 = 0; g0 < bl; g0 += Gr) {
+        const int64_t g1 = std::min(bl, g0 + Gr);
+        int64_t lo = 0, hi = br;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (rmax(mid) > lmin(g0)) hi = mid; else lo = mid + 1;
+        }
+        for (int64_t b = lo; b < br; ++b)
+            for (int64_t a = g0; a < g1; ++a)
+                if (rmax(b) > lmin(a)) tiles.push_back(make_uint2((uint32_t)a, (uint32_t)b));
+    }
+    if ((int64_t)tiles.size() > TUP_MAX_TILES) return set_error(FC_ERANGE, "tensor-core tile plan too large");
+    u.ntiles = (int64_t)tiles.size();
+    if ((e = dev_alloc((void **)&u.QL, std::max<size_t>((size_t)bl * 128 * pitch, 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&u.QR, std::max<size_t>((size_t)br * 128 * pitch, 1))) != cudaSuccess)
+        return cuda_status(e, "tuple-row slab allocation");
+    if ((e = dev_alloc((void **)&u.lt, sizeof(uint64_t) * std::max<size_t>(lt.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&u.lr, sizeof(uint64_t) * std::max<size_t>(lr.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&u.rt, sizeof(uint64_t) * std::max<size_t>(rt.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&u.rr, sizeof(uint64_t) * std::max<size_t>(rr.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&u.tiles, sizeof(uint2) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
+        return cuda_status(e, "tuple lists");
+    cudaMemcpyAsync(u.lt, lt.data(), sizeof(uint64_t) * lt.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(u.lr, lr.data(), sizeof(uint64_t) * lr.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(u.rt, rt.data(), sizeof(uint64_t) * rt.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(u.rr, rr.data(), sizeof(uint64_t) * rr.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(u.tiles, tiles.data(), sizeof(uint2) * tiles.size(), cudaMemcpyHostToDevice, stream);
     if ((e = launch_gate()) != cudaSuccess ||
-        (e = launch_quad_rows(X, S_pad, Wt, lpairs4, nb, (int64_t)pitch, QL, stream)) != cudaSuccess ||
-        (e = launch_quad_rows(X, S_pad, Wt, rpairs4, nb, (int64_t)pitch, QR, stream)) != cudaSuccess)
-        return cuda_status(e, "order-4 slab kernel");
+        (e = launch_tuple_rows(LT, X, S_pad, Wt, u.lt, bl, (int64_t)pitch, u.QL, stream)) != cudaSuccess ||
+        (e = launch_tuple_rows(RT, X, S_pad, Wt, u.rt, br, (int64_t)pitch, u.QR, stream)) != cudaSuccess)
+        return cuda_status(e, "tuple-row kernel");
     note_launches(2);
     int rc;
-    if ((rc = encode_tmap_u8(&tmapQL, QL, kbytes, pitch, (uint64_t)nb * 128)) != FC_OK) return rc;
-    if ((rc = encode_tmap_u8(&tmapQR, QR, kbytes, pitch, (uint64_t)nb * 128)) != FC_OK) return rc;
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "order-4 operands");
-    quads_ready = true;
+    if ((rc = encode_tmap_u8(&u.tmapL, u.QL, kbytes, pitch, (uint64_t)bl * 128)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br * 128)) != FC_OK) return rc;
+    // Host vectors go out of scope: the copies must have landed.
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tuple operands");
+    u.ready = true;
     return FC_OK;
 }
 
-int Dataset::quads_dense(float *scores, uint32_t *tables)
+int Dataset::tuples_dense(int k, float *scores, uint32_t *tables)
 {
-    int rc = prepare_quads();
+    int rc = prepare_tuples(k);
     if (rc) return rc;
-    const uint64_t total = binom(S, 4);
-    QuadsArgs qa = quads_args(0, (float)hy64(), (float)(1.0 / (double)M));
+    const uint64_t total = binom(S, k);
+    const int cells = pow3(k);
+    QuadsArgs qa = tuples_args(k, 0, (float)hy64(), (float)(1.0 / (double)M));
     const size_t ns = scores ? sizeof(float) * (size_t)total : 0;
-    const size_t nt = tables ? sizeof(uint32_t) * 162 * (size_t)total : 0;
+    const size_t nt = tables ? sizeof(uint32_t) * 2 * cells * (size_t)total : 0;
     Arena ar;
     ar.take(ns);
     ar.take(nt);
@@ -927,18 +1014,20 @@ int Dataset::quads_dense(float *scores, uint32_t *tables)
     cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
     if (ns) cudaMemsetAsync(qa.dump_scores, 0, ns, stream);
     if (nt) cudaMemsetAsync(qa.dump_tables, 0, nt, stream);
-    if (ntiles4 > 0) {
-        const int grid = (int)std::min<int64_t>(sms, ntiles4);
-        if ((e = launch_gate()) != cudaSuccess || (e = launch_quads_tc(MODE_DUMP, tmapQL, tmapQR, qa, grid, stream)) != cudaSuccess)
-            return cuda_status(e, "tensor-core quads kernel");
+    const TupleTC &u = tup[k - 4];
+    if (u.ntiles > 0) {
+        const int grid = (int)std::min<int64_t>(sms, u.ntiles);
+        if ((e = launch_gate()) != cudaSuccess ||
+            (e = launch_quads_tc(k, MODE_DUMP, u.tmapL, u.tmapR, qa, grid, stream)) != cudaSuccess)
+            return cuda_status(e, "tensor-core tuple kernel");
         note_launches(1);
     }
     uint32_t herr = 0;
     cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
     if (ns) cudaMemcpyAsync(scores, qa.dump_scores, ns, cudaMemcpyDeviceToHost, stream);
     if (nt) cudaMemcpyAsync(tables, qa.dump_tables, nt, cudaMemcpyDeviceToHost, stream);
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "quads dump");
-    if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the quads kernel");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tuple dump");
+    if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the tuple kernel");
     return FC_OK;
 }
 
@@ -970,8 +1059,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         // Order 3 on large SNP counts: tensor-core contraction of pair rows
         // with SNP rows, one launch per slab of pair rows.
         const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
-        // Order 4: tensor-core contraction of pair rows with pair rows.
-        const bool tc4 = k == 4 && quads_tc_eligible(L) && (!no_alloc || quads_ready);
+        // Orders 4-6: tensor-core contraction of tuple rows with tuple rows.
+        const bool tc4 = k >= 4 && k <= 6 && tuples_tc_eligible(k, L) && (!no_alloc || tup[k - 4].ready);
         TuneConfig cfg{};
         PairsArgs pa{};
         TriplesArgs ta{};
@@ -988,10 +1077,10 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             ta = triples_args(L, (float)hy, (float)(1.0 / Nd));
             grid = sms * (int)slabs3.size();   // every slab launch writes sms lists
         } else if (tc4) {
-            int rc = prepare_quads();
+            int rc = prepare_tuples(k);
             if (rc) return rc;
-            qa = quads_args(L, (float)hy, (float)(1.0 / Nd));
-            grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, ntiles4));
+            qa = tuples_args(k, L, (float)hy, (float)(1.0 / Nd));
+            grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, tup[k - 4].ntiles));
         } else {
             cfg = pick_config(k, L, MODE_TOPN, no_alloc);
             if (cfg.var == VAR_IE) {
@@ -1064,8 +1153,9 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             qa.err = err;
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
             cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
-            if ((e = launch_gate()) != cudaSuccess || (e = launch_quads_tc(MODE_TOPN, tmapQL, tmapQR, qa, grid, stream)) != cudaSuccess)
-                return cuda_status(e, "tensor-core quads kernel");
+            if ((e = launch_gate()) != cudaSuccess ||
+                (e = launch_quads_tc(k, MODE_TOPN, tup[k - 4].tmapL, tup[k - 4].tmapR, qa, grid, stream)) != cudaSuccess)
+                return cuda_status(e, "tensor-core tuple kernel");
         } else if (tc3) {
             ta.gthr = (int *)p[11];
             ta.tile_counter = (int *)p[11] + 1;
@@ -1436,20 +1526,24 @@ int fc_timing(fc_handle *h, int enable, double *sweep_ms, int64_t *sweeps, int64
     return FC_OK;
 }
 
-int fc_quads_dense(fc_handle *h, float *scores, uint32_t *tables)
+int fc_tuples_dense(fc_handle *h, int k, float *scores, uint32_t *tables)
 {
     return guarded([&]() -> int {
         if (!h) return set_error(FC_EINVAL, "NULL handle");
+        if (k < 4 || k > 6) return set_error(FC_EINVAL, "order %d outside 4..6", k);
         if (!scores && !tables) return set_error(FC_EINVAL, "no output requested");
-        if (h->ds.S < 4) return set_error(FC_EINVAL, "fewer than four SNPs");
-        if (scores && h->ds.S > 160) return set_error(FC_ERANGE, "dense order-4 scores need S <= 160");
-        if (tables && h->ds.S > 64) return set_error(FC_ERANGE, "dense order-4 tables need S <= 64");
+        if (h->ds.S < k) return set_error(FC_EINVAL, "fewer SNPs than the order");
+        if (h->ds.S > 65535) return set_error(FC_ERANGE, "too many SNPs for the dense output");
+        const uint64_t total = binom(h->ds.S, k);
+        if (scores && total > ((uint64_t)1 << 25)) return set_error(FC_ERANGE, "dense scores need C(S,k) <= 2^25");
+        if (tables && total * (uint64_t)pow3(k) > ((uint64_t)1 << 25))
+            return set_error(FC_ERANGE, "dense tables need C(S,k) * 3^k <= 2^25");
         if (h->ds.W0 == 0 || h->ds.Wt == h->ds.W0)
             return set_error(FC_EINVAL, "the tensor-core path needs both cases and controls");
         if ((size_t)pairs_smem_bytes(2, (int)h->ds.M, 0) > (size_t)h->ds.max_smem_optin)
             return set_error(FC_ERANGE, "too many samples for the tensor-core path");
         DeviceGuard g(h->ds.device);
-        return h->ds.quads_dense(scores, tables);
+        return h->ds.tuples_dense(k, scores, tables);
     });
 }
 

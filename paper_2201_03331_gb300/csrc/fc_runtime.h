@@ -88,16 +88,19 @@ struct Dataset {
     bool last_path_tc3 = false;
     bool allow_slabs = true;   // false for the jobs of a batch handle (no pair-row slabs)
 
-    // Order-4 tensor-core operands, built on first use and kept: left pairs
-    // (i, j) in (j, i) order and right pairs (e, f) in (e, f) order, 12 per
-    // 128-row block, as e4m3 pair-row slabs with all nine genotype pairs; the
-    // tile list (left block, right block) and the slabs' TMA descriptors.
-    uint8_t *QL = nullptr, *QR = nullptr;
-    uint32_t *lpairs4 = nullptr, *rpairs4 = nullptr;
-    uint2 *tiles4 = nullptr;
-    int64_t ntiles4 = 0;
-    CUtensorMap tmapQL{}, tmapQR{};
-    bool quads_ready = false;
+    // Tensor-core operands of orders 4-6, built on first use; one order's are
+    // kept at a time: left and right tuple-row slabs (all 3^T genotype rows,
+    // 128-row blocks), the tuples with their parts of the rank, the tile list
+    // (left block, right block) and the slabs' TMA descriptors.
+    struct TupleTC {
+        uint8_t *QL = nullptr, *QR = nullptr;
+        uint64_t *lt = nullptr, *lr = nullptr, *rt = nullptr, *rr = nullptr;
+        uint2 *tiles = nullptr;
+        int64_t ntiles = 0;
+        CUtensorMap tmapL{}, tmapR{};
+        bool ready = false;
+    };
+    TupleTC tup[3];            // k = 4, 5, 6
     bool last_path_tc4 = false;
 
     // Optional instrumentation (fc_timing): CUDA events around the sweep
@@ -132,10 +135,11 @@ struct Dataset {
     void release_triples();
     TriplesArgs triples_args(int L, float hy, float invN);
     int triples_dense(float *scores, uint32_t *tables);
-    bool quads_tc_eligible(int L);
-    int prepare_quads();
-    QuadsArgs quads_args(int L, float hy, float invN);
-    int quads_dense(float *scores, uint32_t *tables);
+    bool tuples_tc_eligible(int k, int L);
+    int prepare_tuples(int k);
+    void release_tuples(int k);
+    QuadsArgs tuples_args(int k, int L, float hy, float invN);
+    int tuples_dense(int k, float *scores, uint32_t *tables);
     double hy64() const;
     // Inclusion-exclusion sweep (k = 2, 3): per-SNP genotype counts and, for
     // k = 3, the restricted pair table, built on first use.

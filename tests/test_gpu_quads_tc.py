@@ -1,6 +1,6 @@
-"""Order-4 tensor-core path (tcgen05 contraction of 0/1 pair rows with pair
-rows, all 81 cells) against the CPU oracle and against the pair-extension
-sweep."""
+"""Tensor-core path of orders 4-6 (tcgen05 contraction of 0/1 tuple rows
+with tuple rows, all 3^k cells) against the CPU oracle and against the
+pair-extension sweep."""
 import itertools
 import math
 
@@ -47,7 +47,7 @@ def test_dense_tables_exact(fc, S, cases, controls, seed):
     blocks and ragged sample counts."""
     ds = make_dataset("q4", seed=800 + seed, S=S, cases=cases, controls=controls, k=4, top_n=5)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
-    _, tab = fc.fc_quads_dense(h, scores=False, tables=True)
+    _, tab = fc.fc_tuples_dense(h, 4, scores=False, tables=True)
     ref = oracle.tables(ds.genotypes, ds.phenotype, 4, all_quads(S))
     bad = np.nonzero(np.any(tab != ref, axis=(1, 2)))[0]
     assert len(bad) == 0, (len(bad), all_quads(S)[bad[:5]])
@@ -56,7 +56,7 @@ def test_dense_tables_exact(fc, S, cases, controls, seed):
 def test_dense_scores_within_fp32_bound(fc):
     ds = make_dataset("q4sc", seed=830, S=48, cases=1500, controls=1711, k=4, top_n=5, planted=(3, 17, 30, 44))
     h = fc.fc_load(ds.genotypes, ds.phenotype)
-    sc, _ = fc.fc_quads_dense(h, scores=True, tables=False)
+    sc, _ = fc.fc_tuples_dense(h, 4, scores=True, tables=False)
     ref = oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 4, all_quads(ds.S)), 4)
     assert np.abs(sc.astype(np.float64) - ref).max() <= fp32_bound(4, ds.M)
 
@@ -97,12 +97,71 @@ def test_tc_and_sweep_agree_full_size(fc, path):
     np.testing.assert_allclose(a[1], oracle.mi(o_tab, 4), rtol=1e-6, atol=1e-12)
 
 
-def test_quads_dense_rejects_bad_inputs(fc):
+def test_tuples_dense_rejects_bad_inputs(fc):
     ds = make_dataset("q4bad", seed=860, S=200, cases=100, controls=100, k=4, top_n=5)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     with pytest.raises(fc.FiunchoError):
-        fc.fc_quads_dense(h, scores=True)           # S > 160
+        fc.fc_tuples_dense(h, 4, scores=True)       # C(200, 4) > 2^25
     one = make_dataset("q4one", seed=861, S=12, cases=50, controls=0, k=4, top_n=5)
     h1 = fc.fc_load(one.genotypes, one.phenotype)
     with pytest.raises(fc.FiunchoError):
-        fc.fc_quads_dense(h1, scores=True)          # a single class
+        fc.fc_tuples_dense(h1, 4, scores=True)      # a single class
+    with pytest.raises(fc.FiunchoError):
+        fc.fc_tuples_dense(h1, 3, scores=True)      # order outside 4..6
+
+
+# ---- orders 5 and 6 ----------------------------------------------------------
+
+def all_k(S, k):
+    return np.array(list(itertools.combinations(range(S), k)), dtype=np.uint32)
+
+
+@pytest.mark.parametrize("k,S,cases,controls,seed", [(5, 5, 40, 50, 1), (5, 14, 700, 650, 2), (5, 29, 300, 290, 3),
+                                                     (6, 6, 60, 41, 4), (6, 13, 129, 600, 5), (6, 20, 1, 333, 6)])
+def test_high_order_dense_tables_exact(fc, k, S, cases, controls, seed):
+    ds = make_dataset("t56", seed=870 + seed, S=S, cases=cases, controls=controls, k=k, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    _, tab = fc.fc_tuples_dense(h, k, scores=False, tables=True)
+    ref = oracle.tables(ds.genotypes, ds.phenotype, k, all_k(S, k))
+    bad = np.nonzero(np.any(tab != ref, axis=(1, 2)))[0]
+    assert len(bad) == 0, (len(bad), all_k(S, k)[bad[:5]])
+
+
+@pytest.mark.parametrize("k,S", [(5, 26), (6, 19)])
+def test_high_order_dense_scores_within_fp32_bound(fc, k, S):
+    ds = make_dataset("t56sc", seed=890 + k, S=S, cases=1024, controls=1024, k=k, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    sc, _ = fc.fc_tuples_dense(h, k, scores=True, tables=False)
+    ref = oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, k, all_k(S, k)), k)
+    assert np.abs(sc.astype(np.float64) - ref).max() <= fp32_bound(k, ds.M)
+
+
+@pytest.mark.parametrize("k,S,planted", [(5, 30, (2, 9, 15, 22, 29)), (6, 22, (1, 5, 9, 13, 17, 21))])
+def test_high_order_search_tc_matches_oracle(fc, path, k, S, planted):
+    path("tc")
+    ds = make_dataset("t56s", seed=900 + k, S=S, cases=1024, controls=1024, k=k, top_n=40, planted=planted)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    g_idx, g_s = fc.fc_search(h, k, 40)
+    assert fc.fc_last_search_kind(h) == 7
+    o_idx, o_s, _ = oracle.search(ds.genotypes, ds.phenotype, k, 40)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, k, [c]), k)[0])
+    assert_topn_equal(g_idx, g_s, o_idx, o_s, score_of)
+    assert tuple(g_idx[0]) == planted
+
+
+@pytest.mark.parametrize("name,S", [("P5", 70), ("P6", 44)])
+def test_high_order_tc_and_sweep_agree(fc, path, name, S):
+    """The order-5 and order-6 workloads cut to their first SNPs: the
+    tensor-core path and the pair-extension sweep return the same list."""
+    ds = make_config(name, scale_snps=S)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    path("tc")
+    a = fc.fc_search(h, ds.k, ds.top_n)
+    assert fc.fc_last_search_kind(h) == 7
+    path("popc")
+    b = fc.fc_search(h, ds.k, ds.top_n)
+    assert fc.fc_last_search_kind(h) == 5
+    assert np.array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)

@@ -327,13 +327,21 @@ int orc_search(const uint8_t *G, int64_t S, int64_t M, const uint8_t *ph, int k,
  */
 int orc_distribution(int64_t n, int k, int p, uint64_t *counts)
 {
+    /* Section "Distribution strategy" (Fig. 4): the (k-1)-prefixes that have
+     * at least one extension are dealt round-robin in ascending lexicographic
+     * order; a prefix ending in SNP i brings its n - 1 - i extensions to its
+     * unit.  One pass over the prefixes. */
     if (n < 1 || k < 2 || k > ORC_KMAX || k > n || p < 1 || !counts) return ORC_EINVAL;
     memset(counts, 0, sizeof(uint64_t) * (size_t)p);
-    for (int u = 0; u < p; ++u) {
-        orc_task w = {.S = n, .k = k, .unit = u, .units = p, .pfx_begin = 0,
-                      .pfx_end = INT64_MAX, .count_only = counts};
-        w.list.k = k;
-        search_unit(&w);
+    const int plen = k - 1;
+    uint32_t pfx[ORC_KMAX];
+    for (int t = 0; t < plen; ++t) pfx[t] = (uint32_t)t;
+    int64_t ordinal = 0;
+    int more = (int64_t)plen <= n - 1;
+    while (more) {
+        counts[ordinal % p] += (uint64_t)(n - 1 - (int64_t)pfx[plen - 1]);
+        ordinal += 1;
+        more = next_prefix(pfx, plen, n);
     }
     return ORC_OK;
 }

@@ -45,6 +45,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target duration of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--shard", action="store_true",
+                   help="with several ranks: shard one search by rank range (strong scaling) instead of "
+                        "one data set per rank (weak scaling)")
     p.add_argument("--snps", type=int, default=None,
                    help="keep only the workload's first N SNPs (smaller cases for profiler captures)")
     return p.parse_args()
@@ -299,11 +302,21 @@ def run_ours(args):
     if args.snps:
         S = min(S, args.snps)
         cfg["planted"] = tuple(p for p in cfg["planted"] if p < S)
-    if world > 1:
+    shard = args.shard and world > 1
+    if world > 1 and not shard:
         cfg["seed"] = cfg["seed"] + 1000 * rank      # independent data set per rank
     ds = make_dataset(args.workload, S=S, **cfg) if world > 1 else make_config(args.workload, args.snps)
     k, top_n = ds.k, ds.top_n
     total = math.comb(ds.S, k)
+    if shard:
+        # This rank's share of the one search: a contiguous rank range.
+        from paper_2201_03331_gb300.shard import shard_ranges
+        r0, r1 = shard_ranges(total, world)[rank]
+
+    def one_search(handle):
+        if shard:
+            return fc.fc_search_range(handle, k, top_n, r0, r1)
+        return fc.fc_search(handle, k, top_n)
 
     stream = torch.cuda.Stream()
     h = fc.fc_load(ds.genotypes, ds.phenotype)
@@ -311,7 +324,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
     for _ in range(max(3, args.warmup)):
-        fc.fc_search(h, k, top_n)
+        one_search(h)
     torch.cuda.synchronize()
 
     fc.fc_timing(h, 1)
@@ -326,14 +339,23 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 flush.zero_()                       # L2 flush between timed steps
             ev[i][0].record(stream)
-            idx, score = fc.fc_search(h, k, top_n)
+            idx, score = one_search(h)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     barrier(dist)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     sweep_ms, sweeps, launches = fc.fc_timing(h, 0)
-    value, ms_per_step = aggregate(dist, world, total, args.steps, sum(step_ms))
+    if shard:
+        # One search over all ranks: every rank's range ends the step; the
+        # merged list (rank 0) is the search's answer.
+        from paper_2201_03331_gb300.shard import gather_and_merge
+        merged = gather_and_merge(ds.S, k, (idx, score), top_n, dist)
+        if rank == 0:
+            idx, score = merged
+        value, ms_per_step = aggregate(dist, 1, total, args.steps, sum(step_ms))
+    else:
+        value, ms_per_step = aggregate(dist, world, total, args.steps, sum(step_ms))
 
     # End to end through the public API: pinned host inputs -> fc_load ->
     # fc_search -> host results, every step.
@@ -345,7 +367,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2 = fc.fc_load(Gn, Pn)
-        idx2, score2 = fc.fc_search(h2, k, top_n)
+        idx2, score2 = one_search(h2)
         fc.fc_free(h2)
         torch.cuda.synchronize()
         if i > 0:
@@ -365,13 +387,14 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
     sweep_avg_s = (sweep_ms / max(sweeps, 1)) / 1e3
     kind = fc.fc_last_search_kind(h)
+    share = (r1 - r0) / total if shard and total else 1.0   # this rank's part of the work
     if kind in (2, 6, 7):
         # Tensor-core contraction: contracted cells x M samples x 2 FLOP per
         # combination (orders 2, 3: the 2^k cells with genotypes in {0,1};
         # orders 4-6: all 3^k cells); fp8 peak = measured dense bf16 x 2
         # (nominal ratio).
         cells = {2: 4, 6: 8, 7: 3 ** k}[kind]
-        flops = math.comb(ds.S, k) * cells * 2 * (ds.cases + ds.controls)
+        flops = math.comb(ds.S, k) * cells * 2 * (ds.cases + ds.controls) * share
         bf16 = peaks.get("bf16_tflops")
         peak = 2.0 * float(bf16) if bf16 else 2.0 * 1900.0
         achieved = flops / sweep_avg_s / 1e12 if sweeps else None
@@ -392,9 +415,9 @@ def run_ours(args):
         # clock.  The paper's method (3^k cells, one POPC per 32-bit word)
         # is reported beside it as an equivalent rate.
         peak = props.multi_processor_count * POPC_PER_CLK_PER_SM * sm_max * 1e6 / 1e12
-        paper_popc = algorithmic_popc(ds, k)
+        paper_popc = algorithmic_popc(ds, k) * share
         cells, variant = counted_cells(kind, k)
-        popc = executed_popc(ds, k, cells)
+        popc = executed_popc(ds, k, cells) * share
         achieved = popc / sweep_avg_s / 1e12 if sweeps else None
         kernel_key = f"k_search<{k},{variant},TOPN> {args.workload}"
         roofline = {"bound": "alu", "kernel": kernel_key, "achieved": achieved, "peak": peak,
@@ -409,14 +432,16 @@ def run_ours(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": workload_title(args.workload) if not args.snps else
                    f"{args.workload} cut to its first {ds.S} SNPs (profiling case)",
                    "k": k, "snps": ds.S, "samples": ds.M,
                    "cases": ds.cases, "controls": ds.controls, "top_n": top_n,
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": "one independent data set per GPU" if world > 1 else "single GPU"},
+                   "parallelism": ("one search sharded by rank range over the GPUs" if shard else
+                                   "one independent data set per GPU" if world > 1 else "single GPU")},
         "sample_combinations_per_s": value * ds.M,
         "roofline": roofline,
         "e2e": e2e,

@@ -113,6 +113,23 @@ int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out
 #define FC_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
 
 /*
+ * fc_search_range - fc_search restricted to the combinations whose
+ * lexicographic rank lies in [rank_begin, rank_end) (rank of (i_1..i_k) as in
+ * fc_rank).  The returned list is the exact top min(top_n, rank_end -
+ * rank_begin) of that range, in the order of fc_search, so the lists of
+ * disjoint ranges that cover [0, C(S,k)) merge, by (score desc, rank asc),
+ * into exactly fc_search's list.  This is the unit of work for sharding one
+ * search over several devices or processes by rank range (the paper's
+ * distribution of the combinations over processing units, Section
+ * "Distribution strategy", with contiguous rank ranges instead of a
+ * round-robin of prefixes).  A proper sub-range always runs the
+ * prefix-table sweep.  Errors as fc_search; FC_EINVAL if rank_begin >
+ * rank_end or rank_end > C(S,k).
+ */
+int fc_search_range(fc_handle *h, int k, int64_t top_n, uint64_t rank_begin, uint64_t rank_end, uint32_t *out_idx,
+                    double *out_score, int64_t *out_count);
+
+/*
  * fc_search_static - fc_search that allocates no device memory.
  *
  * The paper has no counterpart: this entry point exists for callers that

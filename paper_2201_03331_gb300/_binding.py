@@ -47,6 +47,7 @@ _SIGNATURES = {
     "fc_pairs_dense": ([P, P, P], i32),
     "fc_triples_dense": ([P, P, P], i32),
     "fc_tuples_dense": ([P, i32, P, P], i32),
+    "fc_search_range": ([P, i32, i64, u64, u64, P, P, P], i32),
     "fc_load_batch": ([i32, P, P, P, P, i32, P], i32),
     "fc_search_batch": ([P, i32, i64, P, P, P], i32),
     "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
@@ -209,6 +210,18 @@ def fc_triples_dense(h: Handle, scores: bool = True, tables: bool = False):
     _check(library().fc_triples_dense(h.ptr, _ptr(sc) if sc is not None else None,
                                       _ptr(tb) if tb is not None else None), "fc_triples_dense")
     return sc, tb
+
+
+def fc_search_range(h: Handle, k: int, top_n: int, rank_begin: int, rank_end: int):
+    """Exact top-N among the combinations of lexicographic ranks
+    [rank_begin, rank_end): ``(indices uint32[n][k], scores float64[n])``."""
+    n_max = max(0, min(top_n, rank_end - rank_begin))
+    idx = np.zeros((max(n_max, 1), k), dtype=np.uint32)
+    sc = np.zeros(max(n_max, 1), dtype=np.float64)
+    cnt = ctypes.c_int64(0)
+    _check(library().fc_search_range(h.ptr, k, top_n, rank_begin, rank_end, _ptr(idx), _ptr(sc),
+                                     ctypes.byref(cnt)), "fc_search_range")
+    return idx[:cnt.value], sc[:cnt.value]
 
 
 def fc_tuples_dense(h: Handle, k: int, scores: bool = True, tables: bool = False):

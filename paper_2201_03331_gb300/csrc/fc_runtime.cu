@@ -1034,10 +1034,13 @@ int Dataset::tuples_dense(int k, float *scores, uint32_t *tables)
 // ---- search ----------------------------------------------------------------
 
 int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
-                    void *ext_scratch, size_t ext_cap)
+                    void *ext_scratch, size_t ext_cap, uint64_t rank_begin, uint64_t rank_end)
 {
     const int64_t total = (int64_t)binom(S, k);
-    const int64_t N = std::min<int64_t>(top_n, total);
+    const uint64_t r0 = std::min<uint64_t>(rank_begin, (uint64_t)total);
+    const uint64_t r1 = std::max(r0, std::min<uint64_t>(rank_end, (uint64_t)total));
+    const bool whole = r0 == 0 && r1 == (uint64_t)total;
+    const int64_t N = std::min<int64_t>(top_n, (int64_t)(r1 - r0));
     if (N == 0) { *out_count = 0; return FC_OK; }
     int L = list_capacity(N);
     if (L > FC_MAX_LIST) return set_error(FC_ERANGE, "top_n %lld too large", (long long)top_n);
@@ -1055,12 +1058,12 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
     for (;;) {
         // Order 2 on large SNP counts: tensor-core contraction; else the
         // prefix-table AND/POPC sweep.
-        const bool tc = k == 2 && pairs_tc_eligible(L) && (!no_alloc || pairs_ready);
+        const bool tc = whole && k == 2 && pairs_tc_eligible(L) && (!no_alloc || pairs_ready);
         // Order 3 on large SNP counts: tensor-core contraction of pair rows
         // with SNP rows, one launch per slab of pair rows.
-        const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
+        const bool tc3 = whole && k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
         // Orders 4-6: tensor-core contraction of tuple rows with tuple rows.
-        const bool tc4 = k >= 4 && k <= 6 && tuples_tc_eligible(k, L) && (!no_alloc || tup[k - 4].ready);
+        const bool tc4 = whole && k >= 4 && k <= 6 && tuples_tc_eligible(k, L) && (!no_alloc || tup[k - 4].ready);
         TuneConfig cfg{};
         PairsArgs pa{};
         TriplesArgs ta{};
@@ -1129,7 +1132,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
         SearchArgs sa{};
         fill_search_args(sa);
-        sa.rank_begin = 0; sa.rank_end = (uint64_t)total;
+        sa.rank_begin = r0; sa.rank_end = r1;
         sa.L = L;
         sa.list_score = (float *)p[0];
         sa.list_rank = (uint64_t *)p[1];
@@ -1203,7 +1206,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         RescoreArgs ra{};
         ra.X = X; ra.S = S; ra.S_pad = S_pad; ra.W0 = W0; ra.Wt = Wt; ra.k = k;
         ra.N = (int)N; ra.L = L; ra.cand_s = src_s; ra.cand_r = src_r; ra.eps = eps;
-        ra.total = (uint64_t)total;
+        ra.total = r1 - r0;
         ra.res_s = (double *)p[6]; ra.res_r = (uint64_t *)p[7]; ra.res_tab = (uint32_t *)p[8];
         ra.err = err;
         if ((e = launch_rescore(ra, stream)) != cudaSuccess) return cuda_status(e, "rescore kernel");
@@ -1407,6 +1410,26 @@ int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out
             return set_error(FC_ERANGE, "C(S, k) >= 2^60");
         DeviceGuard g(h->ds.device);
         return h->ds.search(k, top_n, out_idx, out_score, out_count);
+    });
+}
+
+int fc_search_range(fc_handle *h, int k, int64_t top_n, uint64_t rank_begin, uint64_t rank_end, uint32_t *out_idx,
+                    double *out_score, int64_t *out_count)
+{
+    return guarded([&]() -> int {
+        if (!h || !out_count) return set_error(FC_EINVAL, "NULL handle or out_count");
+        if (k < 1 || k > FC_KMAX_SEARCH || k > h->ds.S)
+            return set_error(FC_EINVAL, "order k=%d outside [1, min(%d, S)]", k, FC_KMAX_SEARCH);
+        if (top_n < 0) return set_error(FC_EINVAL, "top_n < 0");
+        if (top_n > FC_MAX_LIST / 2) return set_error(FC_ERANGE, "top_n above %d", FC_MAX_LIST / 2);
+        if (top_n > 0 && (!out_idx || !out_score)) return set_error(FC_EINVAL, "NULL output");
+        const int64_t total = fc_num_combinations(h->ds.S, k);
+        if (total < 0 || total >= ((int64_t)1 << 60)) return set_error(FC_ERANGE, "C(S, k) >= 2^60");
+        if (rank_begin > rank_end || rank_end > (uint64_t)total)
+            return set_error(FC_EINVAL, "rank range [%llu, %llu) outside [0, %lld]", (unsigned long long)rank_begin,
+                             (unsigned long long)rank_end, (long long)total);
+        DeviceGuard g(h->ds.device);
+        return h->ds.search(k, top_n, out_idx, out_score, out_count, nullptr, 0, rank_begin, rank_end);
     });
 }
 

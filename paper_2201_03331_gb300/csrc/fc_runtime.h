@@ -121,8 +121,11 @@ struct Dataset {
                            bool allow_px = true);
     // ext_scratch: if non-null, a device work area of ext_cap bytes used instead
     // of the handle's own (grown-on-demand) scratch allocation.
+    // [rank_begin, rank_end): search only the combinations of these
+    // lexicographic ranks (a proper sub-range always takes the sweep).
     int search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, int64_t *out_count,
-               void *ext_scratch = nullptr, size_t ext_cap = 0);
+               void *ext_scratch = nullptr, size_t ext_cap = 0, uint64_t rank_begin = 0,
+               uint64_t rank_end = ~0ull);
     int scores(int k, uint64_t rank_begin, int64_t n, float *out);
     int tables(int k, const uint32_t *combos, int64_t n, uint32_t *out);
     bool pairs_tc_eligible(int L);

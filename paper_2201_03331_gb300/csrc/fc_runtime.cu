@@ -887,7 +887,7 @@ void Dataset::release_tuples(int k)
 // C(S - c_{t-1} - 1, k - t) - C(S - c_t, k - t) (c_{-1} = -1): the terms of
 // the left SNPs plus C(S - c_{LT-1} - 1, k - LT) go with the left tuple, the
 // rest with the right tuple (modulo 2^64).  Tiles come in groups of left
-// blocks that fit in about 96 MB of L2: for each right block with a usable
+// blocks that fit in about 48 MB of L2: for each right block with a usable
 // tuple (largest first SNP above the group's smallest last SNP) the group's
 // left blocks follow one another while the right blocks stream.
 int Dataset::prepare_tuples(int k)
@@ -944,7 +944,9 @@ int Dataset::prepare_tuples(int k)
     };
     const uint64_t kbytes = (uint64_t)Wt * 128;
     const uint64_t pitch = kbytes + 128;
-    const int64_t Gr = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((96ull << 20) / (128 * pitch))));
+    // ~48 MB of left blocks per group: about a third of L2 (two dies share
+    // the 129 MB), so the group stays resident while the right blocks stream.
+    const int64_t Gr = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((48ull << 20) / (128 * pitch))));
     std::vector<uint2> tiles;
     for (int64_t g0 = 0; g0 < bl; g0 += Gr) {
         const int64_t g1 = std::min(bl, g0 + Gr);

@@ -64,6 +64,54 @@ cudaError_t dev_alloc(void **p, size_t bytes)
     return cudaMalloc(p, bytes);
 }
 
+namespace {
+struct PoolEntry {
+    int dev;
+    void *p;
+    size_t bytes;
+};
+std::mutex g_pool_mu;
+std::vector<PoolEntry> g_pool;
+constexpr size_t POOL_MIN_BYTES = (size_t)64 << 20;
+constexpr size_t POOL_MAX_BYTES = (size_t)32 << 30;   // kept in total, per process
+constexpr int POOL_MAX_PER_DEVICE = 2;
+}  // namespace
+
+cudaError_t dev_alloc_big(void **p, size_t bytes, int dev)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        for (size_t i = 0; i < g_pool.size(); ++i) {
+            const PoolEntry &q = g_pool[i];
+            if (q.dev == dev && q.bytes >= bytes && q.bytes <= 2 * bytes) {
+                *p = q.p;
+                g_pool.erase(g_pool.begin() + (long)i);
+                return cudaSuccess;
+            }
+        }
+    }
+    return dev_alloc(p, bytes);
+}
+
+void dev_free_big(void *p, size_t bytes, int dev)
+{
+    if (!p) return;
+    if (bytes >= POOL_MIN_BYTES) {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        size_t total = 0;
+        int on_dev = 0;
+        for (const PoolEntry &q : g_pool) {
+            total += q.bytes;
+            on_dev += q.dev == dev;
+        }
+        if (on_dev < POOL_MAX_PER_DEVICE && total + bytes <= POOL_MAX_BYTES) {
+            g_pool.push_back(PoolEntry{dev, p, bytes});
+            return;
+        }
+    }
+    cudaFree(p);
+}
+
 cudaError_t launch_gate()
 {
     const long n = ++g_launch_count;
@@ -213,7 +261,7 @@ Dataset::~Dataset()
     cudaFree(marg);
     cudaFree(tiles);
     cudaFree(PR);
-    cudaFree(P3);
+    dev_free_big(P3, p3_bytes, device);
     cudaFree(xlogx);
     for (int k = 4; k <= 6; ++k) release_tuples(k);
     cudaFree(tiles3);
@@ -677,7 +725,8 @@ int Dataset::prepare_triples()
         slabs3.push_back(cur);
         max_rows = std::max(max_rows, cur.rows);
     }
-    if ((e = dev_alloc((void **)&P3, (size_t)max_rows * pitch)) != cudaSuccess)
+    p3_bytes = (size_t)max_rows * pitch;
+    if ((e = dev_alloc_big((void **)&P3, p3_bytes, device)) != cudaSuccess)
         return cuda_status(e, "pair-row slab allocation");
     if ((e = dev_alloc((void **)&tiles3, sizeof(uint4) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
         return cuda_status(e, "triple tile list allocation");
@@ -696,7 +745,7 @@ int Dataset::prepare_triples()
 void Dataset::release_triples()
 {
     if (stream) cudaStreamSynchronize(stream);
-    cudaFree(P3);
+    dev_free_big(P3, p3_bytes, device);
     cudaFree(tiles3);
     cudaFree(rowbase3);
     P3 = nullptr;
@@ -872,8 +921,8 @@ void Dataset::release_tuples(int k)
     TupleTC &u = tup[k - 4];
     if (!u.QL && !u.QR && !u.lt && !u.tiles) return;
     if (stream) cudaStreamSynchronize(stream);
-    cudaFree(u.QL);
-    cudaFree(u.QR);
+    dev_free_big(u.QL, u.ql_bytes, device);
+    dev_free_big(u.QR, u.qr_bytes, device);
     cudaFree(u.lt);
     cudaFree(u.lr);
     cudaFree(u.rt);
@@ -961,8 +1010,10 @@ int Dataset::prepare_tuples(int k)
     }
     if ((int64_t)tiles.size() > TUP_MAX_TILES) return set_error(FC_ERANGE, "tensor-core tile plan too large");
     u.ntiles = (int64_t)tiles.size();
-    if ((e = dev_alloc((void **)&u.QL, std::max<size_t>((size_t)bl * 128 * pitch, 1))) != cudaSuccess ||
-        (e = dev_alloc((void **)&u.QR, std::max<size_t>((size_t)br * 128 * pitch, 1))) != cudaSuccess)
+    u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
+    u.qr_bytes = std::max<size_t>((size_t)br * 128 * pitch, 1);
+    if ((e = dev_alloc_big((void **)&u.QL, u.ql_bytes, device)) != cudaSuccess ||
+        (e = dev_alloc_big((void **)&u.QR, u.qr_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tuple-row slab allocation");
     if ((e = dev_alloc((void **)&u.lt, sizeof(uint64_t) * std::max<size_t>(lt.size(), 1))) != cudaSuccess ||
         (e = dev_alloc((void **)&u.lr, sizeof(uint64_t) * std::max<size_t>(lr.size(), 1))) != cudaSuccess ||

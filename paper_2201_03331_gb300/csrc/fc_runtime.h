@@ -15,6 +15,13 @@ namespace fc {
 int set_error(int status, const char *fmt, ...);
 int cuda_status(cudaError_t e, const char *what);
 cudaError_t dev_alloc(void **p, size_t bytes);
+// Large operand buffers (pair-row and tuple-row slabs): a freed buffer is
+// kept in a small per-process pool and handed to the next request that it
+// fits (at most twice its size), so that loading, searching and freeing
+// data sets one after another does not map and unmap gigabytes each time.
+// The caller has synchronized every stream that used the buffer.
+cudaError_t dev_alloc_big(void **p, size_t bytes, int dev);
+void dev_free_big(void *p, size_t bytes, int dev);
 cudaError_t launch_gate();
 void fault_counters_reset();
 int check_device(int *dev, int *sms);
@@ -79,6 +86,7 @@ struct Dataset {
     };
     std::vector<TripleSlab> slabs3;
     uint8_t *P3 = nullptr;
+    size_t p3_bytes = 0;
     float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)
     uint4 *tiles3 = nullptr;
     int64_t *rowbase3 = nullptr;
@@ -94,6 +102,7 @@ struct Dataset {
     // (left block, right block) and the slabs' TMA descriptors.
     struct TupleTC {
         uint8_t *QL = nullptr, *QR = nullptr;
+        size_t ql_bytes = 0, qr_bytes = 0;
         uint64_t *lt = nullptr, *lr = nullptr, *rt = nullptr, *rr = nullptr;
         uint2 *tiles = nullptr;
         int64_t ntiles = 0;

@@ -200,6 +200,17 @@ int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doubl
 int fc_search_job(fc_handle *h, int job, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
                   int64_t *out_count);
 
+/*
+ * fc_batch_job_kind - the path the last fc_search_batch on h took for job
+ * `job` (values of fc_last_search_kind): the persistent batched sweep
+ * (1, 3 or 4), or, for order-3 jobs large enough for the tensor cores, the
+ * order-3 tensor-core search (6), run one job after another after the
+ * persistent launch (FC_BATCH_TC=0 keeps every job in the persistent
+ * launch).  0 before the first batched search.  FC_EINVAL for a bad handle
+ * or job.
+ */
+int fc_batch_job_kind(const fc_handle *h, int job);
+
 /* fc_batch_info - shape of a batch handle (any pointer may be NULL). */
 int fc_batch_info(const fc_handle *h, int *n_data, int *replicates, int *n_jobs);
 

@@ -52,6 +52,7 @@ _SIGNATURES = {
     "fc_search_batch": ([P, i32, i64, P, P, P], i32),
     "fc_search_job": ([P, i32, i32, i64, P, P, P], i32),
     "fc_batch_info": ([P, P, P, P], i32),
+    "fc_batch_job_kind": ([P, i32], i32),
     "fc_last_search_kind": ([P], i32),
     "fc_sweep_tables": ([P, i32, u64, i64, P], i32),
     "fc_timing": ([P, i32, P, P, P], i32),
@@ -259,6 +260,14 @@ def fc_load_batch(genotypes, phenotypes) -> Handle:
     h = Handle(out.value)
     h._n_jobs = n * R
     return h
+
+
+def fc_batch_job_kind(h: Handle, job: int) -> int:
+    """Path of the last batched search for ``job`` (fc_last_search_kind values)."""
+    r = library().fc_batch_job_kind(h.ptr, job)
+    if r < 0:
+        _check(r, "fc_batch_job_kind")
+    return r
 
 
 def fc_batch_info(h: Handle):

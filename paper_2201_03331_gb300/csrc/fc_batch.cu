@@ -109,6 +109,7 @@ void BatchState::release_plan()
     host = nullptr;
     k = 0;
     top_n = -1;
+    planned = false;
 }
 
 BatchState::~BatchState()
@@ -134,36 +135,62 @@ int pow2_ge(int v)
 int plan_batch(fc_handle *h, int k, int64_t top_n)
 {
     BatchState &B = *h->batch;
-    if (B.exec && B.k == k && B.top_n == top_n) return FC_OK;
+    if (B.planned && B.k == k && B.top_n == top_n) return FC_OK;
     B.release_plan();
     Dataset &lead = h->ds;
-    const int nj = (int)h->jobs.size();
+    const int n_all = (int)h->jobs.size();
     const int L = list_capacity(std::max<int64_t>(top_n, 1));
     if (L > FC_MAX_LIST) return set_error(FC_ERANGE, "top_n too large");
+    // Order-3 jobs that the tensor-core path takes (FC_BATCH_TC=0: none) are
+    // searched one by one after the persistent launch of the others.
+    B.sel.clear();
+    B.tc.assign(n_all, 0);
+    B.job_kind.assign(n_all, 0);
+    const char *btc = getenv("FC_BATCH_TC");
+    const bool tc_on = k == 3 && !(btc && strcmp(btc, "0") == 0);
+    for (int j = 0; j < n_all; ++j) {
+        Dataset &d = *h->jobs[j];
+        if (tc_on) {
+            d.allow_slabs = true;
+            B.tc[j] = d.triples_tc_eligible(L) ? 1 : 0;
+            d.allow_slabs = false;
+        }
+        if (!B.tc[j]) B.sel.push_back(j);
+    }
+    const int nj = (int)B.sel.size();
+    B.k = k;
+    B.top_n = top_n;
+    B.L = L;
+    if (nj == 0) {
+        B.planned = true;
+        return FC_OK;
+    }
+    // The jobs of the persistent launch, in plan order.
+    auto job = [&](int p) -> Dataset & { return *h->jobs[B.sel[p]]; };
 
     // Representative job (most combinations) for the autotuner.
     int rep = 0;
     uint64_t total_all = 0;
     for (int j = 0; j < nj; ++j) {
-        const uint64_t t = binom(h->jobs[j]->S, k);
+        const uint64_t t = binom(job(j).S, k);
         total_all += t;
-        if (t > binom(h->jobs[rep]->S, k)) rep = j;
+        if (t > binom(job(rep).S, k)) rep = j;
     }
-    Dataset &R = *h->jobs[rep];
+    Dataset &R = job(rep);
     // Counting variant for every job: inclusion-exclusion when each job may
     // build its tables and their total stays within 64 GiB, else the
     // extension-restricted count (k >= 2) or the full count.
     bool use_ie = (k == 2 || k == 3);
     double ie_bytes = 0.0;
     for (int j = 0; j < nj && use_ie; ++j) {
-        const Dataset &d = *h->jobs[j];
+        const Dataset &d = job(j);
         use_ie = d.ie_eligible(k);
         ie_bytes += 16.0 * (double)d.S + (k == 3 ? 16.0 * (double)d.S_pad * (double)d.S_pad : 0.0);
     }
     use_ie = use_ie && ie_bytes <= 64.0 * 1024 * 1024 * 1024;
     if (use_ie) {
         for (int j = 0; j < nj; ++j) {
-            const int rc = h->jobs[j]->prepare_ie(k);
+            const int rc = job(j).prepare_ie(k);
             if (rc) return rc;
         }
     }
@@ -190,7 +217,7 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
     std::vector<BatchItem> items;
     int max_items = 1;
     for (int j = 0; j < nj; ++j) {
-        Dataset &d = *h->jobs[j];
+        Dataset &d = job(j);
         JobDesc &jd = jobs[j];
         jd.X = d.X;
         jd.S = d.S;
@@ -261,9 +288,6 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e, "batch upload");
 
     B.jobs = jobs;
-    B.k = k;
-    B.top_n = top_n;
-    B.L = L;
     B.n_items = n_items;
     B.n2 = n2;
     B.cfg = cfg;
@@ -319,6 +343,7 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
     if (ce != cudaSuccess) return cuda_status(ce, "batched launch capture");
     if (e != cudaSuccess) return cuda_status(e, "graph capture");
     if ((e = cudaGraphInstantiate(&B.exec, B.graph, 0)) != cudaSuccess) return cuda_status(e, "graph instantiate");
+    B.planned = true;
     return FC_OK;
 }
 
@@ -426,35 +451,75 @@ int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doubl
         BatchState &B = *h->batch;
         cudaStream_t st = h->ds.stream;
         cudaError_t e;
-        if ((e = launch_gate()) != cudaSuccess || (e = cudaGraphLaunch(B.exec, st)) != cudaSuccess)
-            return cuda_status(e, "batched graph launch");
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e, "batched search");
         Dataset &lead = h->ds;
         lead.last_list = B.L;
         lead.last_path_tc = false;
-        lead.last_sweep_var = effective_variant(k, B.cfg.var, MODE_BATCH);
-        if (lead.timing) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, B.ev0, B.ev1) == cudaSuccess) {
-                lead.sweep_ms += ms;
-                lead.sweeps += 1;
+        const int ns = (int)B.sel.size();
+        if (ns > 0) {
+            if ((e = launch_gate()) != cudaSuccess || (e = cudaGraphLaunch(B.exec, st)) != cudaSuccess)
+                return cuda_status(e, "batched graph launch");
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_status(e, "batched search");
+            lead.last_sweep_var = effective_variant(k, B.cfg.var, MODE_BATCH);
+            if (lead.timing) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, B.ev0, B.ev1) == cudaSuccess) {
+                    lead.sweep_ms += ms;
+                    lead.sweeps += 1;
+                }
+                lead.launches += 4;
             }
-            lead.launches += 4;
+            const int sweep_kind = lead.last_sweep_var == VAR_IE ? 3 : lead.last_sweep_var == VAR_JR ? 4 : 1;
+            for (int p = 0; p < ns; ++p) {
+                const int j = B.sel[p];
+                const JobDesc &jd = B.jobs[p];
+                uint32_t *oi = out_idx + (size_t)j * top_n * k;
+                double *os = out_score + (size_t)j * top_n;
+                B.job_kind[j] = sweep_kind;
+                if (B.h_err[p] & ERR_LIST_SHORT) {
+                    // Rare: more candidates inside the FP32 window than the list
+                    // holds; this job is searched again alone with longer lists.
+                    rc = h->jobs[j]->search(k, top_n, oi, os, &out_count[j]);
+                    if (rc) return rc;
+                    B.job_kind[j] = h->jobs[j]->last_sweep_var == VAR_IE ? 3 : h->jobs[j]->last_sweep_var == VAR_JR ? 4 : 1;
+                    continue;
+                }
+                memcpy(oi, B.h_idx + (size_t)p * top_n * k, sizeof(uint32_t) * (size_t)jd.N * k);
+                memcpy(os, B.h_score + (size_t)p * top_n, sizeof(double) * (size_t)jd.N);
+                out_count[j] = jd.N;
+            }
         }
-        for (int j = 0; j < nj; ++j) {
-            const JobDesc &jd = B.jobs[j];
-            uint32_t *oi = out_idx + (size_t)j * top_n * k;
-            double *os = out_score + (size_t)j * top_n;
-            if (B.h_err[j] & ERR_LIST_SHORT) {
-                // Rare: more candidates inside the FP32 window than the list
-                // holds; this job is searched again alone with longer lists.
-                rc = h->jobs[j]->search(k, top_n, oi, os, &out_count[j]);
-                if (rc) return rc;
-                continue;
+        // The tensor-core jobs, one after another, largest slab first so
+        // that each slab buffer returned to the pool serves the next jobs
+        // (replicates of a data set share their S and their tile plan); each
+        // releases its operands before the next.
+        std::vector<int> order;
+        for (int j = 0; j < (int)h->jobs.size(); ++j)
+            if (B.tc[j]) order.push_back(j);
+        auto slab_key = [&](int j) { const Dataset &d = *h->jobs[j]; return (double)d.S * d.S * d.Wt; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return slab_key(a) > slab_key(b); });
+        for (const int j : order) {
+            Dataset &d = *h->jobs[j];
+            if (lead.timing && !d.ev_sweep0) {
+                if ((e = cudaEventCreate(&d.ev_sweep0)) != cudaSuccess) return cuda_status(e, "event");
+                if ((e = cudaEventCreate(&d.ev_sweep1)) != cudaSuccess) return cuda_status(e, "event");
             }
-            memcpy(oi, B.h_idx + (size_t)j * top_n * k, sizeof(uint32_t) * (size_t)jd.N * k);
-            memcpy(os, B.h_score + (size_t)j * top_n, sizeof(double) * (size_t)jd.N);
-            out_count[j] = jd.N;
+            d.timing = lead.timing;
+            d.sweep_ms = 0.0;
+            d.sweeps = 0;
+            d.launches = 0;
+            d.allow_slabs = true;
+            rc = d.search(k, top_n, out_idx + (size_t)j * top_n * k, out_score + (size_t)j * top_n, &out_count[j]);
+            d.allow_slabs = false;
+            d.release_triples();
+            d.release_pairs();
+            if (rc) return rc;
+            B.job_kind[j] = d.last_path_tc3 ? 6 : (d.last_sweep_var == VAR_IE ? 3 : d.last_sweep_var == VAR_JR ? 4 : 1);
+            if (lead.timing) {
+                lead.sweep_ms += d.sweep_ms;
+                lead.sweeps += d.sweeps;
+                lead.launches += d.launches;
+            }
+            d.timing = false;
         }
         return FC_OK;
     });
@@ -473,8 +538,28 @@ int fc_search_job(fc_handle *h, int job, int k, int64_t top_n, uint32_t *out_idx
         if (top_n > FC_MAX_LIST / 2) return set_error(FC_ERANGE, "top_n above %d", FC_MAX_LIST / 2);
         if (top_n > 0 && (!out_idx || !out_score)) return set_error(FC_EINVAL, "NULL output");
         DeviceGuard g(h->ds.device);
-        return d.search(k, top_n, out_idx, out_score, out_count);
+        // The same path as the batched search: a job that the batch plan of
+        // this order sends to the tensor cores goes there, and releases its
+        // operands afterwards.
+        const BatchState &B = *h->batch;
+        const bool tc = B.planned && B.k == k && job < (int)B.tc.size() && B.tc[job];
+        if (!tc) return d.search(k, top_n, out_idx, out_score, out_count);
+        d.allow_slabs = true;
+        const int rc = d.search(k, top_n, out_idx, out_score, out_count);
+        d.allow_slabs = false;
+        d.release_triples();
+        d.release_pairs();
+        return rc;
     });
+}
+
+int fc_batch_job_kind(const fc_handle *h, int job)
+{
+    if (!h || !h->batch) return set_error(FC_EINVAL, "not a batch handle");
+    if (job < 0 || job >= (int)h->jobs.size()) return set_error(FC_EINVAL, "job %d out of range", job);
+    const BatchState &B = *h->batch;
+    if (job >= (int)B.job_kind.size()) return 0;
+    return B.job_kind[job];
 }
 
 int fc_batch_info(const fc_handle *h, int *n_data, int *replicates, int *n_jobs)

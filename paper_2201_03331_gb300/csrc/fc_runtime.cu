@@ -72,12 +72,18 @@ struct PoolEntry {
 };
 std::mutex g_pool_mu;
 std::vector<PoolEntry> g_pool;
-constexpr size_t POOL_MIN_BYTES = (size_t)64 << 20;
-constexpr size_t POOL_MAX_BYTES = (size_t)32 << 30;   // kept in total, per process
-constexpr int POOL_MAX_PER_DEVICE = 2;
+// Two classes: slabs (>= 64 MB, at most 2 kept per device) and the smaller
+// per-search operand buffers (e4m3 rows, tile lists; at most 16 kept per
+// device).  At most 32 GiB are kept in total, per process.  A buffer freed
+// into a full class evicts the oldest of that class (the one least likely to
+// fit the next request when data sets come largest first).
+constexpr size_t POOL_BIG_BYTES = (size_t)64 << 20;
+constexpr size_t POOL_MAX_BYTES = (size_t)32 << 30;
+constexpr int POOL_MAX_BIG_PER_DEVICE = 2;
+constexpr int POOL_MAX_MID_PER_DEVICE = 16;
 }  // namespace
 
-cudaError_t dev_alloc_big(void **p, size_t bytes, int dev)
+cudaError_t dev_alloc_pooled(void **p, size_t bytes, int dev)
 {
     {
         std::lock_guard<std::mutex> lock(g_pool_mu);
@@ -93,23 +99,38 @@ cudaError_t dev_alloc_big(void **p, size_t bytes, int dev)
     return dev_alloc(p, bytes);
 }
 
-void dev_free_big(void *p, size_t bytes, int dev)
+void dev_free_pooled(void *p, size_t bytes, int dev)
 {
     if (!p) return;
-    if (bytes >= POOL_MIN_BYTES) {
-        std::lock_guard<std::mutex> lock(g_pool_mu);
-        size_t total = 0;
-        int on_dev = 0;
-        for (const PoolEntry &q : g_pool) {
-            total += q.bytes;
-            on_dev += q.dev == dev;
-        }
-        if (on_dev < POOL_MAX_PER_DEVICE && total + bytes <= POOL_MAX_BYTES) {
-            g_pool.push_back(PoolEntry{dev, p, bytes});
-            return;
-        }
+    if (bytes > POOL_MAX_BYTES) {
+        cudaFree(p);
+        return;
     }
-    cudaFree(p);
+    const bool big = bytes >= POOL_BIG_BYTES;
+    const int max_on_dev = big ? POOL_MAX_BIG_PER_DEVICE : POOL_MAX_MID_PER_DEVICE;
+    std::vector<void *> evict;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        auto same_class = [&](const PoolEntry &q) { return q.dev == dev && (q.bytes >= POOL_BIG_BYTES) == big; };
+        for (;;) {
+            size_t total = 0;
+            int on_dev = 0;
+            for (const PoolEntry &q : g_pool) {
+                total += q.bytes;
+                on_dev += same_class(q);
+            }
+            if (on_dev < max_on_dev && total + bytes <= POOL_MAX_BYTES) break;
+            // The oldest entry of this class if the class is full, else the
+            // oldest of any class (the total is over its cap).
+            size_t v = g_pool.size();
+            for (size_t i = 0; i < g_pool.size() && v == g_pool.size(); ++i)
+                if (on_dev >= max_on_dev ? same_class(g_pool[i]) : true) v = i;
+            evict.push_back(g_pool[v].p);
+            g_pool.erase(g_pool.begin() + (long)v);
+        }
+        g_pool.push_back(PoolEntry{dev, p, bytes});
+    }
+    for (void *q : evict) cudaFree(q);
 }
 
 cudaError_t launch_gate()
@@ -257,15 +278,15 @@ Dataset::~Dataset()
     cudaFree(logtab);
     cudaFree(err);
     cudaFree(scratch);
-    cudaFree(E);
+    dev_free_pooled(E, e_bytes, device);
     cudaFree(marg);
-    cudaFree(tiles);
+    dev_free_pooled(tiles, tiles_bytes, device);
     cudaFree(PR);
-    dev_free_big(P3, p3_bytes, device);
+    dev_free_pooled(P3, p3_bytes, device);
     cudaFree(xlogx);
     for (int k = 4; k <= 6; ++k) release_tuples(k);
-    cudaFree(tiles3);
-    cudaFree(rowbase3);
+    dev_free_pooled(tiles3, tiles3_bytes, device);
+    dev_free_pooled(rowbase3, rowbase3_bytes, device);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
     if (ev_sweep1) cudaEventDestroy(ev_sweep1);
     if (own_stream && own_stream_handle) cudaStreamDestroy(own_stream_handle);
@@ -545,7 +566,8 @@ int Dataset::prepare_pairs()
     // fall on a power-of-two stride (which concentrates them in few L2 sets).
     const uint64_t pitch = kbytes + 128;
     cudaError_t e;
-    if ((e = dev_alloc((void **)&E, (size_t)rows * pitch)) != cudaSuccess)
+    e_bytes = (size_t)rows * pitch;
+    if ((e = dev_alloc_pooled((void **)&E, e_bytes, device)) != cudaSuccess)
         return cuda_status(e, "e4m3 operand allocation");
     const bool need_marg = marg == nullptr;
     if (need_marg && (e = dev_alloc((void **)&marg, sizeof(uint16_t) * 8 * (size_t)S)) != cudaSuccess)
@@ -561,7 +583,8 @@ int Dataset::prepare_pairs()
             for (int I = g0; I < std::min(g0 + Gr, nb); ++I)
                 if (I <= J) t.push_back(((uint32_t)I << 16) | (uint32_t)J);
     ntiles = (int)t.size();
-    if ((e = dev_alloc((void **)&tiles, sizeof(uint32_t) * t.size())) != cudaSuccess)
+    tiles_bytes = sizeof(uint32_t) * t.size();
+    if ((e = dev_alloc_pooled((void **)&tiles, tiles_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tile list allocation");
     cudaMemcpyAsync(tiles, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice, stream);
     if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, Wt, rows, (int64_t)pitch, E, stream)) != cudaSuccess ||
@@ -661,6 +684,67 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     return ta;
 }
 
+namespace {
+// The last slab and tile plan of order 3; it depends on S and the slab
+// capacity only, so the phenotype replicates of one data set (and data sets
+// of equal S) share it.
+struct TriplePlan {
+    int64_t S = -1, cap_rows = -1, max_rows = 0;
+    std::vector<uint4> tiles;
+    std::vector<int64_t> rowbase;
+    std::vector<Dataset::TripleSlab> slabs;
+};
+std::mutex g_plan3_mu;
+std::shared_ptr<const TriplePlan> g_plan3;
+
+std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_plan3_mu);
+        if (g_plan3 && g_plan3->S == S && g_plan3->cap_rows == cap_rows) return g_plan3;
+    }
+    auto pl = std::make_shared<TriplePlan>();
+    pl->S = S;
+    pl->cap_rows = cap_rows;
+    const int64_t S32 = (S + 31) / 32 * 32;
+    const int64_t nLb = (S + 63) / 64;
+    std::vector<uint4> &tiles = pl->tiles;
+    std::vector<int64_t> &rowbase = pl->rowbase;
+    rowbase.assign((size_t)S, 0);
+    Dataset::TripleSlab cur;
+    for (int64_t i = 0; i + 2 < S; ++i) {
+        const int64_t Jlo = (i + 1) / 32;
+        const int64_t n = (S32 / 32 - Jlo) * 128;   // rows of the pairs of i
+        if (cur.rows + n > cap_rows && i > cur.i0) {
+            cur.i1 = i;
+            cur.t1 = (int64_t)tiles.size();
+            pl->slabs.push_back(cur);
+            pl->max_rows = std::max(pl->max_rows, cur.rows);
+            cur = Dataset::TripleSlab{};
+            cur.i0 = i;
+            cur.t0 = (int64_t)tiles.size();
+        }
+        rowbase[(size_t)i] = cur.rows;
+        for (int64_t J = Jlo; 32 * J <= S - 2; ++J) {
+            const int64_t jmin = std::max<int64_t>(32 * J, i + 1);
+            for (int64_t Lb = (jmin + 1) / 64; Lb < nLb; ++Lb)
+                tiles.push_back(make_uint4((uint32_t)(cur.rows + (J - Jlo) * 128), (uint32_t)i, (uint32_t)J,
+                                           (uint32_t)Lb));
+        }
+        cur.rows += n;
+    }
+    if (S >= 3) {
+        cur.i1 = S - 2;
+        cur.t1 = (int64_t)tiles.size();
+        pl->slabs.push_back(cur);
+        pl->max_rows = std::max(pl->max_rows, cur.rows);
+    }
+    std::lock_guard<std::mutex> lock(g_plan3_mu);
+    g_plan3 = pl;
+    return pl;
+}
+}  // namespace
+
 // Plans the slabs and tiles, allocates the slab buffer and builds the
 // first slab.  A slab holds at most min(16 GiB, a quarter of the free device
 // memory) of pair rows (FC_TRIPLES_SLAB_MB overrides the 16 GiB), and at
@@ -681,7 +765,6 @@ int Dataset::prepare_triples()
         note_launches(1);
     }
     const int64_t S32 = (S + 31) / 32 * 32;
-    const int64_t nLb = (S + 63) / 64;
     const uint64_t kbytes = (uint64_t)Wt * 128;
     const uint64_t pitch = kbytes + 128;
     size_t cap = (size_t)16 << 30;
@@ -693,48 +776,21 @@ int Dataset::prepare_triples()
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 4);
     // At least the rows of one first SNP (the largest, i = 0), whatever the cap.
     const int64_t cap_rows = std::max<int64_t>((int64_t)(cap / pitch), (S32 / 32) * 128);
-    std::vector<int64_t> rowbase((size_t)S, 0);
-    std::vector<uint4> tiles;
-    slabs3.clear();
-    TripleSlab cur;
-    int64_t max_rows = 0;
-    for (int64_t i = 0; i + 2 < S; ++i) {
-        const int64_t Jlo = (i + 1) / 32;
-        const int64_t n = (S32 / 32 - Jlo) * 128;   // rows of the pairs of i
-        if (cur.rows + n > cap_rows && i > cur.i0) {
-            cur.i1 = i;
-            cur.t1 = (int64_t)tiles.size();
-            slabs3.push_back(cur);
-            max_rows = std::max(max_rows, cur.rows);
-            cur = TripleSlab{};
-            cur.i0 = i;
-            cur.t0 = (int64_t)tiles.size();
-        }
-        rowbase[(size_t)i] = cur.rows;
-        for (int64_t J = Jlo; 32 * J <= S - 2; ++J) {
-            const int64_t jmin = std::max<int64_t>(32 * J, i + 1);
-            for (int64_t Lb = (jmin + 1) / 64; Lb < nLb; ++Lb)
-                tiles.push_back(make_uint4((uint32_t)(cur.rows + (J - Jlo) * 128), (uint32_t)i, (uint32_t)J,
-                                           (uint32_t)Lb));
-        }
-        cur.rows += n;
-    }
-    if (S >= 3) {
-        cur.i1 = S - 2;
-        cur.t1 = (int64_t)tiles.size();
-        slabs3.push_back(cur);
-        max_rows = std::max(max_rows, cur.rows);
-    }
-    p3_bytes = (size_t)max_rows * pitch;
-    if ((e = dev_alloc_big((void **)&P3, p3_bytes, device)) != cudaSuccess)
+    const std::shared_ptr<const TriplePlan> plan = plan_triples(S, cap_rows);
+    const std::vector<uint4> &tiles = plan->tiles;
+    slabs3 = plan->slabs;
+    p3_bytes = (size_t)plan->max_rows * pitch;
+    if ((e = dev_alloc_pooled((void **)&P3, p3_bytes, device)) != cudaSuccess)
         return cuda_status(e, "pair-row slab allocation");
-    if ((e = dev_alloc((void **)&tiles3, sizeof(uint4) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
+    tiles3_bytes = sizeof(uint4) * std::max<size_t>(tiles.size(), 1);
+    rowbase3_bytes = sizeof(int64_t) * (size_t)S;
+    if ((e = dev_alloc_pooled((void **)&tiles3, tiles3_bytes, device)) != cudaSuccess)
         return cuda_status(e, "triple tile list allocation");
-    if ((e = dev_alloc((void **)&rowbase3, sizeof(int64_t) * (size_t)S)) != cudaSuccess)
+    if ((e = dev_alloc_pooled((void **)&rowbase3, rowbase3_bytes, device)) != cudaSuccess)
         return cuda_status(e, "slab row table allocation");
     cudaMemcpyAsync(tiles3, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(rowbase3, rowbase.data(), sizeof(int64_t) * (size_t)S, cudaMemcpyHostToDevice, stream);
-    if ((rc = encode_tmap_u8(&tmap3, P3, kbytes, pitch, (uint64_t)max_rows)) != FC_OK) return rc;
+    cudaMemcpyAsync(rowbase3, plan->rowbase.data(), sizeof(int64_t) * (size_t)S, cudaMemcpyHostToDevice, stream);
+    if ((rc = encode_tmap_u8(&tmap3, P3, kbytes, pitch, (uint64_t)plan->max_rows)) != FC_OK) return rc;
     built_slab3 = -1;
     if ((rc = build_slab3(0)) != FC_OK) return rc;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair-row slab");
@@ -742,12 +798,24 @@ int Dataset::prepare_triples()
     return FC_OK;
 }
 
+void Dataset::release_pairs()
+{
+    if (!E && !tiles) return;
+    if (stream) cudaStreamSynchronize(stream);
+    dev_free_pooled(E, e_bytes, device);
+    dev_free_pooled(tiles, tiles_bytes, device);
+    E = nullptr;
+    tiles = nullptr;
+    ntiles = 0;
+    pairs_ready = false;
+}
+
 void Dataset::release_triples()
 {
     if (stream) cudaStreamSynchronize(stream);
-    dev_free_big(P3, p3_bytes, device);
-    cudaFree(tiles3);
-    cudaFree(rowbase3);
+    dev_free_pooled(P3, p3_bytes, device);
+    dev_free_pooled(tiles3, tiles3_bytes, device);
+    dev_free_pooled(rowbase3, rowbase3_bytes, device);
     P3 = nullptr;
     tiles3 = nullptr;
     rowbase3 = nullptr;
@@ -921,8 +989,8 @@ void Dataset::release_tuples(int k)
     TupleTC &u = tup[k - 4];
     if (!u.QL && !u.QR && !u.lt && !u.tiles) return;
     if (stream) cudaStreamSynchronize(stream);
-    dev_free_big(u.QL, u.ql_bytes, device);
-    dev_free_big(u.QR, u.qr_bytes, device);
+    dev_free_pooled(u.QL, u.ql_bytes, device);
+    dev_free_pooled(u.QR, u.qr_bytes, device);
     cudaFree(u.lt);
     cudaFree(u.lr);
     cudaFree(u.rt);
@@ -1012,8 +1080,8 @@ int Dataset::prepare_tuples(int k)
     u.ntiles = (int64_t)tiles.size();
     u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
     u.qr_bytes = std::max<size_t>((size_t)br * 128 * pitch, 1);
-    if ((e = dev_alloc_big((void **)&u.QL, u.ql_bytes, device)) != cudaSuccess ||
-        (e = dev_alloc_big((void **)&u.QR, u.qr_bytes, device)) != cudaSuccess)
+    if ((e = dev_alloc_pooled((void **)&u.QL, u.ql_bytes, device)) != cudaSuccess ||
+        (e = dev_alloc_pooled((void **)&u.QR, u.qr_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tuple-row slab allocation");
     if ((e = dev_alloc((void **)&u.lt, sizeof(uint64_t) * std::max<size_t>(lt.size(), 1))) != cudaSuccess ||
         (e = dev_alloc((void **)&u.lr, sizeof(uint64_t) * std::max<size_t>(lr.size(), 1))) != cudaSuccess ||

@@ -15,13 +15,15 @@ namespace fc {
 int set_error(int status, const char *fmt, ...);
 int cuda_status(cudaError_t e, const char *what);
 cudaError_t dev_alloc(void **p, size_t bytes);
-// Large operand buffers (pair-row and tuple-row slabs): a freed buffer is
+// Operand buffers rebuilt per data set or per search (pair-row and
+// tuple-row slabs, e4m3 rows, tile lists): a freed buffer of 4 KB or more is
 // kept in a small per-process pool and handed to the next request that it
-// fits (at most twice its size), so that loading, searching and freeing
-// data sets one after another does not map and unmap gigabytes each time.
-// The caller has synchronized every stream that used the buffer.
-cudaError_t dev_alloc_big(void **p, size_t bytes, int dev);
-void dev_free_big(void *p, size_t bytes, int dev);
+// fits (at most twice its size), so that searching data sets one after
+// another neither maps and unmaps gigabytes nor pays cudaFree's implicit
+// device synchronization each time.  The caller has synchronized every
+// stream that used the buffer; `bytes` is the size it asked for.
+cudaError_t dev_alloc_pooled(void **p, size_t bytes, int dev);
+void dev_free_pooled(void *p, size_t bytes, int dev);
 cudaError_t launch_gate();
 void fault_counters_reset();
 int check_device(int *dev, int *sms);
@@ -67,8 +69,10 @@ struct Dataset {
     // [2*S64][Wt*128] (rows 2s+g for genotypes g = 0, 1), per-SNP genotype
     // counts, the block-pair tile list and E's TMA descriptor.
     uint8_t *E = nullptr;
+    size_t e_bytes = 0;
     uint16_t *marg = nullptr;
     uint32_t *tiles = nullptr;
+    size_t tiles_bytes = 0;
     int ntiles = 0;
     CUtensorMap tmap{};
     bool pairs_ready = false;
@@ -89,7 +93,9 @@ struct Dataset {
     size_t p3_bytes = 0;
     float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)
     uint4 *tiles3 = nullptr;
+    size_t tiles3_bytes = 0;
     int64_t *rowbase3 = nullptr;
+    size_t rowbase3_bytes = 0;
     CUtensorMap tmap3{};
     int built_slab3 = -1;
     bool triples_ready = false;
@@ -145,6 +151,7 @@ struct Dataset {
     int prepare_triples();
     int build_slab3(int s);
     void release_triples();
+    void release_pairs();
     TriplesArgs triples_args(int L, float hy, float invN);
     int triples_dense(float *scores, uint32_t *tables);
     bool tuples_tc_eligible(int k, int L);
@@ -198,6 +205,14 @@ struct BatchState {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool planned = false;
+    // Jobs of the persistent launch (plan index -> job index); the others
+    // (order 3, enough SNPs for the tensor cores) are searched one by one on
+    // the tensor-core path.  job_kind: fc_last_search_kind of each job's last
+    // batched search.
+    std::vector<int> sel;
+    std::vector<char> tc;
+    std::vector<int> job_kind;
     ~BatchState();
     void release_plan();
 };

@@ -92,3 +92,38 @@ def test_batch_rejects_bad_order(fc):
     assert e.value.status == fc.FC_EINVAL
     with pytest.raises(fc.FiunchoError):
         fc.fc_search(h, 2, 3)          # a batch handle has no single data set
+
+
+def test_batch_hybrid_tensor_core_jobs(fc, monkeypatch):
+    """Order-3 jobs with enough SNPs for the tensor cores run on that path
+    after the persistent launch; the lists equal those of the all-sweep batch
+    and of per-job searches, and a tensor-core job matches the oracle."""
+    sets = [make_dataset("h0", seed=101, S=420, cases=700, controls=500, k=3, top_n=10, planted=(7, 200, 411)),
+            make_dataset("h1", seed=102, S=90, cases=800, controls=900, k=3, top_n=10),
+            make_dataset("h2", seed=103, S=390, cases=260, controls=1100, k=3, top_n=10)]
+    phs = [permuted_phenotypes(ds.phenotype, 2, seed=110 + i) for i, ds in enumerate(sets)]
+    gens = [ds.genotypes for ds in sets]
+    h = fc.fc_load_batch(gens, phs)
+    a = fc.fc_search_batch(h, 3, 10)
+    kinds = [fc.fc_batch_job_kind(h, j) for j in range(6)]
+    assert kinds[0] == kinds[1] == kinds[4] == kinds[5] == 6
+    assert kinds[2] == kinds[3] != 6
+    b = fc.fc_search_batch(h, 3, 10)   # replay: same lists
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    for j in (0, 3, 5):
+        idx, s = fc.fc_search_job(h, j, 3, 10)
+        assert np.array_equal(idx, a[0][j, :len(s)])
+        np.testing.assert_allclose(s, a[1][j, :len(s)], rtol=1e-12)
+    monkeypatch.setenv("FC_BATCH_TC", "0")
+    h2 = fc.fc_load_batch(gens, phs)
+    c = fc.fc_search_batch(h2, 3, 10)
+    assert all(fc.fc_batch_job_kind(h2, j) != 6 for j in range(6))
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[2], c[2])
+    np.testing.assert_allclose(a[1], c[1], rtol=1e-12)
+    assert tuple(a[0][0, 0]) == (7, 200, 411)
+    o_idx, o_s, _ = oracle.search(gens[2], phs[2][1], 3, 10)
+
+    def score_of(cmb):
+        return float(oracle.mi(oracle.tables(gens[2], phs[2][1], 3, [cmb]), 3)[0])
+    assert_topn_equal(a[0][5], a[1][5], o_idx, o_s, score_of)

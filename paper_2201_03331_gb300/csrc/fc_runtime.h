@@ -100,7 +100,10 @@ struct Dataset {
     int built_slab3 = -1;
     bool triples_ready = false;
     bool last_path_tc3 = false;
-    bool allow_slabs = true;   // false for the jobs of a batch handle (no pair-row slabs)
+    // False for the jobs of a batch handle: only the batched search lifts it,
+    // for the order-3 jobs it sends to the tensor cores, and releases their
+    // slabs after each one.
+    bool allow_slabs = true;
 
     // Tensor-core operands of orders 4-6, built on first use; one order's are
     // kept at a time: left and right tuple-row slabs (all 3^T genotype rows,

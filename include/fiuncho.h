@@ -73,6 +73,11 @@ typedef struct fc_handle fc_handle;
  *
  * The genotypes are packed into one bit per sample per genotype row, cases
  * and controls in separate word ranges (the genotype tables of Fig. 2).
+ * They are streamed to the device in chunks of SNP rows (about 256 MB;
+ * environment FC_LOAD_CHUNK_MB overrides): the copy of one chunk overlaps
+ * the packing of the previous one, and the device holds two chunks of the
+ * uint8 input at a time, never the whole matrix.  The host buffers are
+ * only read, and may be reused once fc_load returns.
  * Fails with FC_EINVAL on a null pointer, a size <= 0 or a value outside the
  * coding above; FC_ERANGE if cases or controls exceed FC_MAX_CLASS_SAMPLES;
  * FC_ENODEV without a CUDA device.

@@ -93,9 +93,10 @@ enum : uint32_t {
 // ---- kernel launch wrappers (defined in the .cu files) --------------------
 
 struct PackArgs {
-    const uint8_t *G;       // [S][M] device
+    const uint8_t *G;       // [S][M] device (k_pack: the rows of SNPs s_base .. s_base + S - 1)
     const uint8_t *ph;      // [M] device
     int64_t S, M, S_pad;
+    int64_t s_base;         // k_pack: first SNP of G within the table
     int W0, Wt;
     uint4 *X;               // [Wt][3][S_pad]
     int32_t *case_idx;      // [M1] sample index of the i-th case

@@ -92,7 +92,7 @@ __global__ void k_pack(PackArgs a, int64_t M1, int64_t M0)
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.err, ERR_GENOTYPE);
     if (lane < 3)
-        a.X[((size_t)w * 3 + lane) * a.S_pad + s] = make_uint4(mine[0], mine[1], mine[2], mine[3]);
+        a.X[((size_t)w * 3 + lane) * a.S_pad + a.s_base + s] = make_uint4(mine[0], mine[1], mine[2], mine[3]);
 }
 
 __global__ void k_logtab(float *t, int64_t M)

@@ -207,31 +207,30 @@ void *Arena::take(size_t bytes)
 
 // ---- loading ---------------------------------------------------------------
 
-int Dataset::load(const uint8_t *dG, const uint8_t *dph, int64_t S_, int64_t M_)
+int Dataset::load_begin(const uint8_t *dph, int64_t S_, int64_t M_)
 {
     S = S_;
     M = M_;
     S_pad = (S + 31) / 32 * 32;
     cudaError_t e;
     // Class index of every sample (cases first), phenotype validation.
-    int32_t *case_idx = nullptr, *ctrl_idx = nullptr;
     int64_t *cc = nullptr;
-    if ((e = dev_alloc((void **)&case_idx, sizeof(int32_t) * M)) != cudaSuccess) return cuda_status(e, "alloc");
-    if ((e = dev_alloc((void **)&ctrl_idx, sizeof(int32_t) * M)) != cudaSuccess) {
-        cudaFree(case_idx);
+    if ((e = dev_alloc((void **)&load_case_idx, sizeof(int32_t) * M)) != cudaSuccess) return cuda_status(e, "alloc");
+    if ((e = dev_alloc((void **)&load_ctrl_idx, sizeof(int32_t) * M)) != cudaSuccess) {
+        load_release();
         return cuda_status(e, "alloc");
     }
     if ((e = dev_alloc((void **)&cc, sizeof(int64_t) * 2)) != cudaSuccess) {
-        cudaFree(case_idx); cudaFree(ctrl_idx);
+        load_release();
         return cuda_status(e, "alloc");
     }
-    auto cleanup = [&]() { cudaFree(case_idx); cudaFree(ctrl_idx); cudaFree(cc); };
+    auto cleanup = [&]() { load_release(); cudaFree(cc); };
     if ((e = dev_alloc((void **)&err, sizeof(uint32_t) * 4)) != cudaSuccess) { cleanup(); return cuda_status(e, "alloc"); }
     cudaMemsetAsync(err, 0, sizeof(uint32_t) * 4, stream);
 
     PackArgs pa{};
-    pa.G = dG; pa.ph = dph; pa.S = S; pa.M = M; pa.S_pad = S_pad;
-    pa.case_idx = case_idx; pa.ctrl_idx = ctrl_idx; pa.err = err; pa.class_count = cc;
+    pa.ph = dph; pa.S = S; pa.M = M; pa.S_pad = S_pad;
+    pa.case_idx = load_case_idx; pa.ctrl_idx = load_ctrl_idx; pa.err = err; pa.class_count = cc;
     if ((e = launch_gate()) != cudaSuccess || (e = launch_class_index(pa, stream)) != cudaSuccess) {
         cleanup();
         return cuda_status(e, "class index kernel");
@@ -241,39 +240,77 @@ int Dataset::load(const uint8_t *dG, const uint8_t *dph, int64_t S_, int64_t M_)
     cudaMemcpyAsync(hcc, cc, sizeof hcc, cudaMemcpyDeviceToHost, stream);
     cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) { cleanup(); return cuda_status(e, "class index"); }
-    if (herr & ERR_PHENOTYPE) { cleanup(); return set_error(FC_EINVAL, "phenotype value outside {0,1}"); }
+    cudaFree(cc);
+    if (herr & ERR_PHENOTYPE) { load_release(); return set_error(FC_EINVAL, "phenotype value outside {0,1}"); }
     M1 = hcc[0];
     M0 = hcc[1];
     if (M1 > FC_MAX_CLASS_SAMPLES || M0 > FC_MAX_CLASS_SAMPLES) {
-        cleanup();
+        load_release();
         return set_error(FC_ERANGE, "cases (%lld) or controls (%lld) exceed %d", (long long)M1,
                          (long long)M0, FC_MAX_CLASS_SAMPLES);
     }
     W0 = (int)((M1 + 127) / 128);
     Wt = W0 + (int)((M0 + 127) / 128);
     const size_t xbytes = sizeof(uint4) * (size_t)std::max(Wt, 1) * 3 * S_pad;
-    if ((e = dev_alloc((void **)&X, xbytes)) != cudaSuccess) { cleanup(); return cuda_status(e, "bit table allocation"); }
+    if ((e = dev_alloc((void **)&X, xbytes)) != cudaSuccess) { load_release(); return cuda_status(e, "bit table allocation"); }
     cudaMemsetAsync(X, 0, xbytes, stream);
     if ((e = dev_alloc((void **)&logtab, sizeof(float) * (M + 1))) != cudaSuccess) {
-        cleanup();
+        load_release();
         return cuda_status(e, "log table allocation");
     }
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_logtab(logtab, M, stream)) != cudaSuccess) {
+        load_release();
+        return cuda_status(e, "log table kernel");
+    }
+    return FC_OK;
+}
+
+int Dataset::load_pack(const uint8_t *dG, int64_t s0, int64_t n)
+{
+    PackArgs pa{};
+    pa.G = dG; pa.S = n; pa.M = M; pa.S_pad = S_pad; pa.s_base = s0;
+    pa.case_idx = load_case_idx; pa.ctrl_idx = load_ctrl_idx; pa.err = err;
     pa.X = X; pa.W0 = W0; pa.Wt = Wt;
-    if ((e = launch_gate()) != cudaSuccess || (e = launch_pack(pa, M1, M0, stream)) != cudaSuccess ||
-        (e = launch_logtab(logtab, M, stream)) != cudaSuccess) {
-        cleanup();
+    cudaError_t e;
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_pack(pa, M1, M0, stream)) != cudaSuccess) {
+        load_release();
         return cuda_status(e, "pack kernel");
     }
+    return FC_OK;
+}
+
+int Dataset::load_end()
+{
+    uint32_t herr = 0;
     cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, stream);
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) { cleanup(); return cuda_status(e, "pack"); }
-    cleanup();
+    const cudaError_t e = cudaStreamSynchronize(stream);
+    load_release();
+    if (e != cudaSuccess) return cuda_status(e, "pack");
     if (herr & ERR_GENOTYPE) return set_error(FC_EINVAL, "genotype value outside {0,1,2}");
     return FC_OK;
+}
+
+void Dataset::load_release()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    cudaFree(load_case_idx);
+    cudaFree(load_ctrl_idx);
+    load_case_idx = load_ctrl_idx = nullptr;
+}
+
+int Dataset::load(const uint8_t *dG, const uint8_t *dph, int64_t S_, int64_t M_)
+{
+    int rc = load_begin(dph, S_, M_);
+    if (rc) return rc;
+    if ((rc = load_pack(dG, 0, S_)) != FC_OK) return rc;
+    return load_end();
 }
 
 Dataset::~Dataset()
 {
     if (stream) cudaStreamSynchronize(stream);
+    cudaFree(load_case_idx);
+    cudaFree(load_ctrl_idx);
     cudaFree(X);
     cudaFree(logtab);
     cudaFree(err);
@@ -1450,6 +1487,87 @@ int make_handle(fc_handle **out, int *dev)
     return FC_OK;
 }
 
+// Host genotypes reach the bit table in chunks of SNP rows (about
+// FC_LOAD_CHUNK_MB, default 256 MB): the copy of chunk c + 1 runs on its own
+// stream while chunk c is packed, through two device staging buffers, so the
+// device never holds the whole uint8 matrix and the copy engine and the SMs
+// work at the same time.
+int load_streamed(fc_handle *h, const uint8_t *genotypes, int64_t S, int64_t M, const uint8_t *phenotype,
+                  fc_handle **out)
+{
+    Dataset &d = h->ds;
+    size_t chunk_bytes = (size_t)256 << 20;
+    if (const char *mb = getenv("FC_LOAD_CHUNK_MB")) {
+        const long v = atol(mb);
+        if (v > 0) chunk_bytes = (size_t)v << 20;
+    }
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(S, (int64_t)(chunk_bytes / (size_t)M)));
+    const int64_t nchunks = (S + per - 1) / per;
+    const int nbuf = nchunks > 1 ? 2 : 1;
+    const size_t stage_bytes = (size_t)per * (size_t)M;
+    // Staging buffers as large as a slab are not kept: they would push slabs
+    // out of the pool.
+    const bool keep_stage = stage_bytes < ((size_t)64 << 20);
+    uint8_t *stage[2] = {nullptr, nullptr}, *dph = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr}, packed[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(d.stream);
+        if (cs) cudaStreamSynchronize(cs);
+        for (int b = 0; b < 2; ++b) {
+            if (keep_stage) dev_free_pooled(stage[b], stage_bytes, d.device);
+            else cudaFree(stage[b]);
+            if (copied[b]) cudaEventDestroy(copied[b]);
+            if (packed[b]) cudaEventDestroy(packed[b]);
+        }
+        if (cs) cudaStreamDestroy(cs);
+        dev_free_pooled(dph, (size_t)M, d.device);
+    };
+    auto fail = [&](int rc) {
+        cleanup();
+        delete h;
+        return rc;
+    };
+    cudaError_t e;
+    if ((e = dev_alloc_pooled((void **)&dph, (size_t)M, d.device)) != cudaSuccess)
+        return fail(cuda_status(e, "phenotype staging allocation"));
+    for (int b = 0; b < nbuf; ++b) {
+        if ((e = keep_stage ? dev_alloc_pooled((void **)&stage[b], stage_bytes, d.device)
+                            : dev_alloc((void **)&stage[b], stage_bytes)) != cudaSuccess)
+            return fail(cuda_status(e, "genotype staging allocation"));
+        if ((e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&packed[b], cudaEventDisableTiming)) != cudaSuccess)
+            return fail(cuda_status(e, "event"));
+    }
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(cuda_status(e, "copy stream"));
+    cudaMemcpyAsync(dph, phenotype, (size_t)M, cudaMemcpyHostToDevice, d.stream);
+    int rc = d.load_begin(dph, S, M);
+    if (rc) return fail(rc);
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int b = (int)(c % nbuf);
+        const int64_t s0 = c * per, n = std::min(per, S - s0);
+        // Staging buffer b is free once the pack of chunk c - nbuf is done.
+        if (c >= nbuf && (e = cudaStreamWaitEvent(cs, packed[b], 0)) != cudaSuccess)
+            return fail(cuda_status(e, "copy stream wait"));
+        if ((e = cudaMemcpyAsync(stage[b], genotypes + (size_t)s0 * (size_t)M, (size_t)n * (size_t)M,
+                                 cudaMemcpyHostToDevice, cs)) != cudaSuccess ||
+            (e = cudaEventRecord(copied[b], cs)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(d.stream, copied[b], 0)) != cudaSuccess)
+            return fail(cuda_status(e, "genotype copy"));
+        if ((rc = d.load_pack(stage[b], s0, n)) != FC_OK) return fail(rc);
+        if ((e = cudaEventRecord(packed[b], d.stream)) != cudaSuccess) return fail(cuda_status(e, "event"));
+    }
+    rc = d.load_end();
+    cleanup();
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return FC_OK;
+}
+
 }  // namespace fc
 
 extern "C" {
@@ -1466,26 +1584,7 @@ int fc_load(const uint8_t *genotypes, int64_t S, int64_t M, const uint8_t *pheno
         fc_handle *h = nullptr;
         int rc = make_handle(&h, &dev);
         if (rc) return rc;
-        uint8_t *dG = nullptr, *dph = nullptr;
-        cudaError_t e;
-        if ((e = dev_alloc((void **)&dG, (size_t)S * M)) != cudaSuccess) {
-            delete h;
-            return cuda_status(e, "genotype staging allocation");
-        }
-        if ((e = dev_alloc((void **)&dph, (size_t)M)) != cudaSuccess) {
-            cudaFree(dG);
-            delete h;
-            return cuda_status(e, "phenotype staging allocation");
-        }
-        cudaMemcpyAsync(dG, genotypes, (size_t)S * M, cudaMemcpyHostToDevice, h->ds.stream);
-        cudaMemcpyAsync(dph, phenotype, (size_t)M, cudaMemcpyHostToDevice, h->ds.stream);
-        rc = h->ds.load(dG, dph, S, M);
-        cudaStreamSynchronize(h->ds.stream);
-        cudaFree(dG);
-        cudaFree(dph);
-        if (rc) { delete h; return rc; }
-        *out = h;
-        return FC_OK;
+        return load_streamed(h, genotypes, S, M, phenotype, out);
     });
 }
 

@@ -130,7 +130,17 @@ struct Dataset {
     void note_launches(int64_t n) { if (timing) launches += n; }
 
     ~Dataset();
+    // Loading in three steps, so that the genotype rows can arrive in
+    // chunks: load_begin classifies the samples (phenotype dph, device) and
+    // allocates the bit table; load_pack packs the rows of SNPs
+    // [s0, s0 + n) (dG: their rows, device, read on `stream`); load_end waits
+    // and checks the genotype values.  load = all three over one block.
+    int load_begin(const uint8_t *dph, int64_t S, int64_t M);
+    int load_pack(const uint8_t *dG, int64_t s0, int64_t n);
+    int load_end();
     int load(const uint8_t *dG, const uint8_t *dph, int64_t S, int64_t M);
+    int32_t *load_case_idx = nullptr, *load_ctrl_idx = nullptr;   // between load_begin and load_end
+    void load_release();
     int reserve_scratch(size_t bytes);
     // no_alloc: choose only among variants whose operands already exist and
     // run no autotuning (which needs scratch).  allow_px = false keeps to the

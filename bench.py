@@ -20,6 +20,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -158,7 +159,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # The raw samples go to FC_CLOCKS_DIR (default: the temporary directory);
+        # the JSON line carries their summary.
+        self.path = os.path.join(os.environ.get("FC_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"fiuncho_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:

@@ -248,6 +248,7 @@ struct PairsArgs {
     int M;
     float hy, invN;
     uint64_t pair_base;     // C(S, 2)
+    uint64_t rank_begin, rank_end;   // only pairs with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2, stages;
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
@@ -279,6 +280,7 @@ struct TriplesArgs {
     int M;
     float hy, invN;
     uint64_t total;         // C(S, 3)
+    uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2, stages;
     float *list_score;      // [grid][L]
     uint64_t *list_rank;

@@ -300,7 +300,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                     }
                     const int jl = ch * 16 + 2 * q + g;
                     const int64_t j = (int64_t)J * TC_SNPS + jl;
-                    const bool valid = i < a.S && j < a.S && i < j;
+                    // Lexicographic rank of (i, j): C(S,2) - C(S-i,2) + (j-i-1).
+                    const uint64_t si = (uint64_t)(a.S - i);
+                    const uint64_t rank0 = a.pair_base - si * (si - 1) / 2 + (uint64_t)(j - i - 1);
+                    const bool valid = i < a.S && j < a.S && i < j && rank0 >= a.rank_begin && rank0 < a.rank_end;
                     uint32_t mj[2][3] = {{0, 0, 0}, {0, 0, 0}};
                     if (j < a.S) {
                         const uint4 m4 = *reinterpret_cast<const uint4 *>(a.marg + j * 8);
@@ -336,9 +339,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                         }
                     }
                     const float score = fmaf(-hsum, a.invN, a.hy);
-                    // Lexicographic rank of (i, j): C(S,2) - C(S-i,2) + (j-i-1).
-                    const uint64_t si = (uint64_t)(a.S - i);
-                    const uint64_t rank = valid ? (a.pair_base - si * (si - 1) / 2 + (uint64_t)(j - i - 1)) : NO_RANK;
+                    const uint64_t rank = valid ? rank0 : NO_RANK;
                     sc[q] = score;
                     rk[q] = rank;
                     val[q] = valid;

@@ -574,6 +574,8 @@ PairsArgs Dataset::pairs_args(int L, float hy, float invN)
     PairsArgs pa{};
     pa.tiles = tiles;
     pa.ntiles = ntiles;
+    pa.rank_begin = 0;
+    pa.rank_end = ~0ull;
     pa.S = S;
     pa.W0 = W0;
     pa.Wt = Wt;
@@ -620,6 +622,7 @@ int Dataset::prepare_pairs()
             for (int I = g0; I < std::min(g0 + Gr, nb); ++I)
                 if (I <= J) t.push_back(((uint32_t)I << 16) | (uint32_t)J);
     ntiles = (int)t.size();
+    tiles_host = t;
     tiles_bytes = sizeof(uint32_t) * t.size();
     if ((e = dev_alloc_pooled((void **)&tiles, tiles_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tile list allocation");
@@ -711,6 +714,8 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.hy = hy;
     ta.invN = invN;
     ta.total = binom(S, 3);
+    ta.rank_begin = 0;
+    ta.rank_end = ~0ull;
     ta.L = L;
     ta.Bcap = L > 0 ? std::max(L, 1024) : 0;
     ta.P2 = L > 0 ? pow2_at_least(L + ta.Bcap) : 0;
@@ -728,6 +733,7 @@ namespace {
 struct TriplePlan {
     int64_t S = -1, cap_rows = -1, max_rows = 0;
     std::vector<uint4> tiles;
+    std::vector<int64_t> first_tile;   // [S + 1]: tiles of first SNP i are [first_tile[i], first_tile[i + 1])
     std::vector<int64_t> rowbase;
     std::vector<Dataset::TripleSlab> slabs;
 };
@@ -748,6 +754,7 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
     std::vector<uint4> &tiles = pl->tiles;
     std::vector<int64_t> &rowbase = pl->rowbase;
     rowbase.assign((size_t)S, 0);
+    pl->first_tile.assign((size_t)S + 1, 0);
     Dataset::TripleSlab cur;
     for (int64_t i = 0; i + 2 < S; ++i) {
         const int64_t Jlo = (i + 1) / 32;
@@ -762,6 +769,7 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
             cur.t0 = (int64_t)tiles.size();
         }
         rowbase[(size_t)i] = cur.rows;
+        pl->first_tile[(size_t)i] = (int64_t)tiles.size();
         for (int64_t J = Jlo; 32 * J <= S - 2; ++J) {
             const int64_t jmin = std::max<int64_t>(32 * J, i + 1);
             for (int64_t Lb = (jmin + 1) / 64; Lb < nLb; ++Lb)
@@ -770,6 +778,7 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
         }
         cur.rows += n;
     }
+    for (int64_t i = std::max<int64_t>(S - 2, 0); i <= S; ++i) pl->first_tile[(size_t)i] = (int64_t)tiles.size();
     if (S >= 3) {
         cur.i1 = S - 2;
         cur.t1 = (int64_t)tiles.size();
@@ -816,6 +825,7 @@ int Dataset::prepare_triples()
     const std::shared_ptr<const TriplePlan> plan = plan_triples(S, cap_rows);
     const std::vector<uint4> &tiles = plan->tiles;
     slabs3 = plan->slabs;
+    first_tile3 = plan->first_tile;
     p3_bytes = (size_t)plan->max_rows * pitch;
     if ((e = dev_alloc_pooled((void **)&P3, p3_bytes, device)) != cudaSuccess)
         return cuda_status(e, "pair-row slab allocation");
@@ -844,6 +854,7 @@ void Dataset::release_pairs()
     E = nullptr;
     tiles = nullptr;
     ntiles = 0;
+    tiles_host.clear();
     pairs_ready = false;
 }
 
@@ -1216,27 +1227,55 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
     for (;;) {
         // Order 2 on large SNP counts: tensor-core contraction; else the
         // prefix-table AND/POPC sweep.
-        const bool tc = whole && k == 2 && pairs_tc_eligible(L) && (!no_alloc || pairs_ready);
+        // A rank range takes the tiles of the row blocks of its first SNPs,
+        // and the kernel drops the pairs outside the range.
+        const bool tc = k == 2 && pairs_tc_eligible(L) && (!no_alloc || pairs_ready);
         // Order 3 on large SNP counts: tensor-core contraction of pair rows
         // with SNP rows, one launch per slab of pair rows.
-        const bool tc3 = whole && k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
+        // A rank range takes the tiles of its first SNPs, and the kernel
+        // drops the combinations outside the range.
+        const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
         // Orders 4-6: tensor-core contraction of tuple rows with tuple rows.
         const bool tc4 = whole && k >= 4 && k <= 6 && tuples_tc_eligible(k, L) && (!no_alloc || tup[k - 4].ready);
         TuneConfig cfg{};
         PairsArgs pa{};
         TriplesArgs ta{};
         QuadsArgs qa{};
+        std::vector<uint32_t> range_tiles;   // order 2, rank range: the tiles of its row blocks
+        struct SlabLaunch { int si; int64_t t0, t1; };
+        std::vector<SlabLaunch> launches3;
         int grid = 0;
         if (tc) {
             int rc = prepare_pairs();
             if (rc) return rc;
             pa = pairs_args(L, (float)hy, (float)(1.0 / Nd));
-            grid = std::min(sms, ntiles);
+            if (!whole) {
+                uint32_t c_lo[2], c_hi[2];
+                unrank(S, 2, r0, c_lo);
+                unrank(S, 2, r1 - 1, c_hi);
+                const uint32_t I_lo = c_lo[0] / 64, I_hi = c_hi[0] / 64;   // 64-SNP row blocks
+                for (const uint32_t t : tiles_host)
+                    if ((t >> 16) >= I_lo && (t >> 16) <= I_hi) range_tiles.push_back(t);
+                pa.ntiles = (int)range_tiles.size();
+                pa.rank_begin = r0;
+                pa.rank_end = r1;
+            }
+            grid = std::min(sms, pa.ntiles);
         } else if (tc3) {
             int rc = prepare_triples();
             if (rc) return rc;
             ta = triples_args(L, (float)hy, (float)(1.0 / Nd));
-            grid = sms * (int)slabs3.size();   // every slab launch writes sms lists
+            ta.rank_begin = r0;
+            ta.rank_end = r1;
+            uint32_t c_lo[3], c_hi[3];
+            unrank(S, 3, r0, c_lo);
+            unrank(S, 3, r1 - 1, c_hi);
+            const int64_t t_lo = first_tile3[c_lo[0]], t_hi = first_tile3[(size_t)c_hi[0] + 1];
+            for (int si = 0; si < (int)slabs3.size(); ++si) {
+                const int64_t a0 = std::max(slabs3[(size_t)si].t0, t_lo), a1 = std::min(slabs3[(size_t)si].t1, t_hi);
+                if (a0 < a1) launches3.push_back(SlabLaunch{si, a0, a1});
+            }
+            grid = sms * (int)launches3.size();   // every slab launch writes sms lists
         } else if (tc4) {
             int rc = prepare_tuples(k);
             if (rc) return rc;
@@ -1268,8 +1307,9 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             p[9] = A.take(sizeof(uint32_t) * (size_t)N * k);
             p[10] = A.take(sizeof(double) * (size_t)N);
             p[11] = A.take(sizeof(int) * 4);
+            p[12] = A.take(sizeof(uint32_t) * range_tiles.size());
         };
-        void *p[12];
+        void *p[13];
         plan(ar, p);
         Arena A2;
         if (ext_scratch) {
@@ -1301,6 +1341,11 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             pa.gthr = (int *)p[11];
             pa.tile_counter = (int *)p[11] + 1;
             pa.err = err;
+            if (!range_tiles.empty()) {
+                cudaMemcpyAsync(p[12], range_tiles.data(), sizeof(uint32_t) * range_tiles.size(),
+                                cudaMemcpyHostToDevice, stream);
+                pa.tiles = (const uint32_t *)p[12];
+            }
             // 0x80808080 is below the ordered image of every finite score.
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
             cudaMemsetAsync(pa.tile_counter, 0, sizeof(int), stream);
@@ -1322,20 +1367,20 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             ta.tile_counter = (int *)p[11] + 1;
             ta.err = err;
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
-            for (int si = 0; si < (int)slabs3.size(); ++si) {
-                int rc = build_slab3(si);
+            for (size_t x = 0; x < launches3.size(); ++x) {
+                const SlabLaunch &sl = launches3[x];
+                int rc = build_slab3(sl.si);
                 if (rc) return rc;
-                const TripleSlab &sl = slabs3[(size_t)si];
                 TriplesArgs a = ta;
                 a.tiles = tiles3 + sl.t0;
                 a.ntiles = (int)(sl.t1 - sl.t0);
-                a.list_score = (float *)p[0] + (size_t)si * sms * L;
-                a.list_rank = (uint64_t *)p[1] + (size_t)si * sms * L;
+                a.list_score = (float *)p[0] + x * sms * L;
+                a.list_rank = (uint64_t *)p[1] + x * sms * L;
                 cudaMemsetAsync(ta.tile_counter, 0, sizeof(int), stream);
                 if ((e = launch_gate()) != cudaSuccess ||
                     (e = launch_triples_tc(MODE_TOPN, tmap, tmap3, a, sms, stream)) != cudaSuccess)
                     return cuda_status(e, "tensor-core triples kernel");
-                if (si > 0) note_launches(1);
+                if (x > 0) note_launches(1);
             }
         } else {
             if ((e = launch_gate()) != cudaSuccess || (e = launch_search(k, cfg, MODE_TOPN, sa, stream, nullptr)) != cudaSuccess)

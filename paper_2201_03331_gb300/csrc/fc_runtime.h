@@ -73,6 +73,7 @@ struct Dataset {
     uint16_t *marg = nullptr;
     uint32_t *tiles = nullptr;
     size_t tiles_bytes = 0;
+    std::vector<uint32_t> tiles_host;   // the same tile list on the host
     int ntiles = 0;
     CUtensorMap tmap{};
     bool pairs_ready = false;
@@ -89,6 +90,7 @@ struct Dataset {
         int64_t rows = 0;         // pair rows
     };
     std::vector<TripleSlab> slabs3;
+    std::vector<int64_t> first_tile3;   // [S + 1] first tile of each first SNP
     uint8_t *P3 = nullptr;
     size_t p3_bytes = 0;
     float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)

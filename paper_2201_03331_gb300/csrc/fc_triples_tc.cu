@@ -353,7 +353,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                     const int q = ch * 4 + 2 * m + g;
                     const int64_t j = (int64_t)J * 32 + q;
-                    const bool valid = has && i < j && j < l && l < a.S;
+                    // Lexicographic rank of (i, j, l).
+                    const uint64_t rank0 = base_i - c2((uint64_t)(a.S - j)) + (uint64_t)(l - j - 1);
+                    const bool valid = has && i < j && j < l && l < a.S && rank0 >= a.rank_begin &&
+                                       rank0 < a.rank_end;
                     uint32_t T[27];
                     float hsum = 0.f;
                     if (valid) {
@@ -374,9 +377,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         }
                     }
                     const float score = fmaf(-hsum, a.invN, a.hy);
-                    // Lexicographic rank of (i, j, l).
-                    const uint64_t rank =
-                        valid ? base_i - c2((uint64_t)(a.S - j)) + (uint64_t)(l - j - 1) : NO_RANK;
+                    const uint64_t rank = valid ? rank0 : NO_RANK;
                     sc[m] = score;
                     rk[m] = rank;
                     val[m] = valid;

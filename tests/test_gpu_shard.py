@@ -53,3 +53,56 @@ def test_range_list_is_exact_top_n_of_the_range(fc):
     assert np.array_equal(w[0], f[0])
     with pytest.raises(fc.FiunchoError):
         fc.fc_search_range(h, 3, 30, 10, total + 1)
+
+
+@pytest.mark.parametrize("slab_mb", [None, "20"])
+def test_order3_tensor_core_ranges(fc, monkeypatch, slab_mb):
+    """Rank ranges on the order-3 tensor-core path (one slab, and four slabs
+    of pair rows): each range list is the exact top-N of its combinations,
+    and the shards merge to the whole search."""
+    from paper_2201_03331_gb300.shard import merge_shard_lists, search_shard
+    monkeypatch.setenv("FC_TRIPLES_PATH", "tc")
+    if slab_mb:
+        monkeypatch.setenv("FC_TRIPLES_SLAB_MB", slab_mb)
+    ds = make_dataset("rng3", seed=975, S=130, cases=600, controls=700, k=3, top_n=25, planted=(9, 64, 121))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    full = fc.fc_search(h, 3, 25)
+    assert fc.fc_last_search_kind(h) == 6
+    for r0, r1 in [(5, 50), (1000, 9000), (150000, 150001), (300000, math.comb(130, 3))]:
+        idx, sc = fc.fc_search_range(h, 3, 25, r0, r1)
+        assert fc.fc_last_search_kind(h) == 6
+        combos = np.array([fc.fc_unrank(ds.S, 3, r) for r in range(r0, r1)], dtype=np.uint32)
+        mi = oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 3, combos), 3)
+        order = sorted(range(r1 - r0), key=lambda i: (-mi[i], i))[:25]
+        assert np.array_equal(idx, combos[order]), (r0, r1)
+        np.testing.assert_allclose(sc, mi[order], rtol=1e-6)
+    lists = [search_shard(h, 3, 25, s, 3) for s in range(3)]
+    m_idx, m_sc = merge_shard_lists(ds.S, 3, lists, 25)
+    assert np.array_equal(m_idx, full[0])
+    np.testing.assert_allclose(m_sc, full[1], rtol=1e-12)
+    assert tuple(full[0][0]) == (9, 64, 121)
+
+
+def test_order2_tensor_core_ranges(fc, monkeypatch):
+    """Rank ranges on the order-2 tensor-core path: the tiles of the range's
+    row blocks, pairs outside the range dropped in the epilogue."""
+    from paper_2201_03331_gb300.shard import merge_shard_lists, search_shard
+    monkeypatch.setenv("FC_PAIRS_PATH", "tc")
+    ds = make_dataset("rng2", seed=976, S=300, cases=900, controls=1100, k=2, top_n=40, planted=(17, 250))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    full = fc.fc_search(h, 2, 40)
+    assert fc.fc_last_search_kind(h) == 2
+    total = math.comb(300, 2)
+    for r0, r1 in [(5, 50), (1000, 9000), (20000, 20001), (44000, total)]:
+        idx, sc = fc.fc_search_range(h, 2, 40, r0, r1)
+        assert fc.fc_last_search_kind(h) == 2
+        combos = np.array([fc.fc_unrank(ds.S, 2, r) for r in range(r0, r1)], dtype=np.uint32)
+        mi = oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 2, combos), 2)
+        order = sorted(range(r1 - r0), key=lambda i: (-mi[i], i))[:40]
+        assert np.array_equal(idx, combos[order]), (r0, r1)
+        np.testing.assert_allclose(sc, mi[order], rtol=1e-6)
+    lists = [search_shard(h, 2, 40, s, 4) for s in range(4)]
+    m_idx, m_sc = merge_shard_lists(ds.S, 2, lists, 40)
+    assert np.array_equal(m_idx, full[0])
+    np.testing.assert_allclose(m_sc, full[1], rtol=1e-12)
+    assert tuple(full[0][0]) == (17, 250)

@@ -317,6 +317,7 @@ struct QuadsArgs {
     const float *xlogx;     // x ln x for x = 0..M
     int M;
     float hy, invN;
+    uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2, stages;
     float *list_score;      // [grid][L]
     uint64_t *list_rank;

@@ -317,9 +317,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     float tot = 0.f;
 #pragma unroll
                     for (int k2 = 0; k2 < RL; ++k2) tot += __shfl_sync(FULL, part, min(seg0 + k2, 31));
-                    const bool valid = p < LPQ && ltp != NO_TUPLE && rtp != NO_TUPLE && llast < rfirst;
+                    const bool real = p < LPQ && ltp != NO_TUPLE && rtp != NO_TUPLE && llast < rfirst;
+                    const uint64_t rank0 = real ? lrk + a.rrank[ri] : 0;   // modulo 2^64
+                    const bool valid = real && rank0 >= a.rank_begin && rank0 < a.rank_end;
                     const float score = fmaf(-tot, a.invN, a.hy);
-                    const uint64_t rank = valid ? lrk + a.rrank[ri] : NO_RANK;   // modulo 2^64
+                    const uint64_t rank = valid ? rank0 : NO_RANK;
                     sc[q] = score;
                     rk[q] = rank;
                     val[q] = valid && cell_l == 0;

@@ -1022,6 +1022,8 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
     qa.M = (int)M;
     qa.hy = hy;
     qa.invN = invN;
+    qa.rank_begin = 0;
+    qa.rank_end = ~0ull;
     qa.L = L;
     qa.Bcap = L > 0 ? std::max(L, 1024) : 0;
     qa.P2 = L > 0 ? pow2_at_least(L + qa.Bcap) : 0;
@@ -1055,6 +1057,30 @@ void Dataset::release_tuples(int k)
 // blocks that fit in about 48 MB of L2: for each right block with a usable
 // tuple (largest first SNP above the group's smallest last SNP) the group's
 // left blocks follow one another while the right blocks stream.
+namespace {
+// Tiles (left block, right block) of the orders 4-6 tensor-core kernel:
+// left blocks in groups of `group` (a group's operands stay in L2 while the
+// right blocks stream), pairs where some right tuple starts after some left
+// tuple ends.  include: the left blocks to take (all if null).
+void tuple_tiles(int64_t group, const std::vector<int64_t> &lmin, const std::vector<int64_t> &rmax,
+                 const std::vector<char> *include, std::vector<uint2> &tiles)
+{
+    const int64_t bl = (int64_t)lmin.size(), br = (int64_t)rmax.size();
+    for (int64_t g0 = 0; g0 < bl; g0 += group) {
+        const int64_t g1 = std::min(bl, g0 + group);
+        int64_t lo = 0, hi = br;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (rmax[(size_t)mid] > lmin[(size_t)g0]) hi = mid; else lo = mid + 1;
+        }
+        for (int64_t b = lo; b < br; ++b)
+            for (int64_t a = g0; a < g1; ++a)
+                if ((!include || (*include)[(size_t)a]) && rmax[(size_t)b] > lmin[(size_t)a])
+                    tiles.push_back(make_uint2((uint32_t)a, (uint32_t)b));
+    }
+}
+}  // namespace
+
 int Dataset::prepare_tuples(int k)
 {
     TupleTC &u = tup[k - 4];
@@ -1102,28 +1128,18 @@ int Dataset::prepare_tuples(int k)
     lr.resize((size_t)bl * LPB, 0);
     rt.resize((size_t)br * RPB, NO_TUPLE);
     rr.resize((size_t)br * RPB, 0);
-    auto lmin = [&](int64_t blk) { return snp(lt[(size_t)blk * LPB], LT - 1); };
-    auto rmax = [&](int64_t blk) {
-        const int64_t last = std::min<int64_t>((blk + 1) * RPB, nr) - 1;
-        return snp(rt[(size_t)last], 0);
-    };
+    u.lmin_host.resize((size_t)bl);
+    u.rmax_host.resize((size_t)br);
+    for (int64_t blk = 0; blk < bl; ++blk) u.lmin_host[(size_t)blk] = snp(lt[(size_t)blk * LPB], LT - 1);
+    for (int64_t blk = 0; blk < br; ++blk)
+        u.rmax_host[(size_t)blk] = snp(rt[(size_t)(std::min<int64_t>((blk + 1) * RPB, nr) - 1)], 0);
     const uint64_t kbytes = (uint64_t)Wt * 128;
     const uint64_t pitch = kbytes + 128;
     // ~48 MB of left blocks per group: about a third of L2 (two dies share
     // the 129 MB), so the group stays resident while the right blocks stream.
-    const int64_t Gr = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((48ull << 20) / (128 * pitch))));
+    u.group = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((48ull << 20) / (128 * pitch))));
     std::vector<uint2> tiles;
-    for (int64_t g0 = 0; g0 < bl; g0 += Gr) {
-        const int64_t g1 = std::min(bl, g0 + Gr);
-        int64_t lo = 0, hi = br;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) / 2;
-            if (rmax(mid) > lmin(g0)) hi = mid; else lo = mid + 1;
-        }
-        for (int64_t b = lo; b < br; ++b)
-            for (int64_t a = g0; a < g1; ++a)
-                if (rmax(b) > lmin(a)) tiles.push_back(make_uint2((uint32_t)a, (uint32_t)b));
-    }
+    tuple_tiles(u.group, u.lmin_host, u.rmax_host, nullptr, tiles);
     if ((int64_t)tiles.size() > TUP_MAX_TILES) return set_error(FC_ERANGE, "tensor-core tile plan too large");
     u.ntiles = (int64_t)tiles.size();
     u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
@@ -1152,6 +1168,7 @@ int Dataset::prepare_tuples(int k)
     if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br * 128)) != FC_OK) return rc;
     // Host vectors go out of scope: the copies must have landed.
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tuple operands");
+    u.lt_host = std::move(lt);
     u.ready = true;
     return FC_OK;
 }
@@ -1236,12 +1253,16 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         // drops the combinations outside the range.
         const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
         // Orders 4-6: tensor-core contraction of tuple rows with tuple rows.
-        const bool tc4 = whole && k >= 4 && k <= 6 && tuples_tc_eligible(k, L) && (!no_alloc || tup[k - 4].ready);
+        // A rank range takes the tiles of the left blocks holding a left
+        // tuple whose combinations meet the range, and the kernel drops the
+        // combinations outside it.
+        const bool tc4 = k >= 4 && k <= 6 && tuples_tc_eligible(k, L) && (!no_alloc || tup[k - 4].ready);
         TuneConfig cfg{};
         PairsArgs pa{};
         TriplesArgs ta{};
         QuadsArgs qa{};
         std::vector<uint32_t> range_tiles;   // order 2, rank range: the tiles of its row blocks
+        std::vector<uint2> range_tiles4;     // orders 4-6, rank range: the tiles of its left blocks
         struct SlabLaunch { int si; int64_t t0, t1; };
         std::vector<SlabLaunch> launches3;
         int grid = 0;
@@ -1280,7 +1301,32 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             int rc = prepare_tuples(k);
             if (rc) return rc;
             qa = tuples_args(k, L, (float)hy, (float)(1.0 / Nd));
-            grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, tup[k - 4].ntiles));
+            int64_t nt = tup[k - 4].ntiles;
+            if (!whole) {
+                const TupleTC &u = tup[k - 4];
+                const int LT = tc_left_size(k), LPB = tc_tuples_per_block(LT);
+                std::vector<char> include(u.lmin_host.size(), 0);
+                for (size_t x = 0; x < u.lt_host.size(); ++x) {
+                    const uint64_t t = u.lt_host[x];
+                    if (t == NO_TUPLE) continue;
+                    // The combinations that extend left tuple t form the rank
+                    // range [first, first + count): t followed by its smallest
+                    // right tuple, and every right tuple after its last SNP.
+                    uint32_t c[FC_KMAX_SEARCH];
+                    for (int q = 0; q < LT; ++q) c[q] = (uint32_t)((t >> (16 * q)) & 0xffffu);
+                    for (int q = LT; q < k; ++q) c[q] = c[q - 1] + 1;
+                    const uint64_t count = binom(S - (int64_t)c[LT - 1] - 1, k - LT);
+                    if (count == 0) continue;
+                    const uint64_t first = rank_of(S, k, c);
+                    if (first < r1 && first + count > r0) include[x / (size_t)LPB] = 1;
+                }
+                tuple_tiles(u.group, u.lmin_host, u.rmax_host, &include, range_tiles4);
+                nt = (int64_t)range_tiles4.size();
+                qa.ntiles = (int)nt;
+                qa.rank_begin = r0;
+                qa.rank_end = r1;
+            }
+            grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, nt));
         } else {
             cfg = pick_config(k, L, MODE_TOPN, no_alloc);
             if (cfg.var == VAR_IE) {
@@ -1307,7 +1353,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             p[9] = A.take(sizeof(uint32_t) * (size_t)N * k);
             p[10] = A.take(sizeof(double) * (size_t)N);
             p[11] = A.take(sizeof(int) * 4);
-            p[12] = A.take(sizeof(uint32_t) * range_tiles.size());
+            p[12] = A.take(sizeof(uint32_t) * range_tiles.size() + sizeof(uint2) * range_tiles4.size());
         };
         void *p[13];
         plan(ar, p);
@@ -1357,6 +1403,11 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             qa.gthr = (int *)p[11];
             qa.tile_counter = (int *)p[11] + 1;
             qa.err = err;
+            if (!range_tiles4.empty()) {
+                cudaMemcpyAsync(p[12], range_tiles4.data(), sizeof(uint2) * range_tiles4.size(),
+                                cudaMemcpyHostToDevice, stream);
+                qa.tiles = (const uint2 *)p[12];
+            }
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
             cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
             if ((e = launch_gate()) != cudaSuccess ||

@@ -119,6 +119,12 @@ struct Dataset {
         int64_t ntiles = 0;
         CUtensorMap tmapL{}, tmapR{};
         bool ready = false;
+        // Host copies for rank-range searches: the left tuples, each left
+        // block's smallest last SNP, each right block's largest first SNP,
+        // and the left blocks per tile group.
+        std::vector<uint64_t> lt_host;
+        std::vector<int64_t> lmin_host, rmax_host;
+        int64_t group = 0;
     };
     TupleTC tup[3];            // k = 4, 5, 6
     bool last_path_tc4 = false;

@@ -106,3 +106,29 @@ def test_order2_tensor_core_ranges(fc, monkeypatch):
     assert np.array_equal(m_idx, full[0])
     np.testing.assert_allclose(m_sc, full[1], rtol=1e-12)
     assert tuple(full[0][0]) == (17, 250)
+
+
+@pytest.mark.parametrize("k,S,seed", [(4, 40, 1), (5, 24, 2), (6, 20, 3)])
+def test_high_order_tensor_core_ranges(fc, monkeypatch, k, S, seed):
+    """Rank ranges on the orders 4-6 tensor-core path: the left blocks whose
+    tuples start combinations in the range, the rest dropped in the
+    epilogue."""
+    from paper_2201_03331_gb300.shard import merge_shard_lists, search_shard
+    monkeypatch.setenv("FC_QUADS_PATH", "tc")
+    ds = make_dataset("rngq", seed=980 + seed, S=S, cases=500, controls=620, k=k, top_n=30)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    full = fc.fc_search(h, k, 30)
+    assert fc.fc_last_search_kind(h) == 7
+    total = math.comb(S, k)
+    for r0, r1 in [(0, 40), (777, 5555), (total // 2, total // 2 + 1), (total - 3000, total)]:
+        idx, sc = fc.fc_search_range(h, k, 30, r0, r1)
+        assert fc.fc_last_search_kind(h) == 7
+        combos = np.array([fc.fc_unrank(S, k, r) for r in range(r0, r1)], dtype=np.uint32)
+        mi = oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, k, combos), k)
+        order = sorted(range(r1 - r0), key=lambda i: (-mi[i], i))[:30]
+        assert np.array_equal(idx, combos[order]), (r0, r1)
+        np.testing.assert_allclose(sc, mi[order], rtol=1e-6)
+    lists = [search_shard(h, k, 30, s, 3) for s in range(3)]
+    m_idx, m_sc = merge_shard_lists(S, k, lists, 30)
+    assert np.array_equal(m_idx, full[0])
+    np.testing.assert_allclose(m_sc, full[1], rtol=1e-12)

@@ -127,9 +127,9 @@ int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out
  * search over several devices or processes by rank range (the paper's
  * distribution of the combinations over processing units, Section
  * "Distribution strategy", with contiguous rank ranges instead of a
- * round-robin of prefixes).  Orders 2 and 3 take the same path as a whole
- * search (tensor cores where eligible: only the tiles of the range's first
- * SNPs run); a proper sub-range of orders 4-6 runs the prefix-table sweep.
+ * round-robin of prefixes).  A range takes the same path as a whole search
+ * (tensor cores where eligible: only the tiles whose combinations can fall
+ * in the range run, the others are dropped in the epilogue).
  * Errors as fc_search; FC_EINVAL if rank_begin >
  * rank_end or rank_end > C(S,k).
  */

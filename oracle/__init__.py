@@ -18,7 +18,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+# FC_ORACLE_LIB names another build of oracle.c to load instead (the pin
+# strength tests load copies with planted mistakes this way).
+_LIB = os.environ.get("FC_ORACLE_LIB") or os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -27,6 +29,8 @@ KMAX = 10
 
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` next to the source (gcc, -O2, pthreads)."""
+    if os.environ.get("FC_ORACLE_LIB"):
+        return _LIB
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread",

@@ -260,6 +260,28 @@ def test_search_matches_brute_force(seed, S, M, k):
             assert s <= cutoff + 1e-12
 
 
+def test_exact_ties_keep_the_smaller_index_tuples():
+    """Reading of the tie rule: equal scores rank by the index tuple, smallest
+    first, also where the list cuts through a group of equal scores.  Copies
+    of one SNP give bit-identical tables, hence bit-equal scores."""
+    ds = random_small(11, S=4, M=60)
+    b = ds.genotypes
+    G = np.ascontiguousarray(np.stack([b[0], b[1], b[2], b[1], b[3], b[1]]))   # SNPs 1, 3, 5 equal
+    ph = ds.phenotype
+    mi1 = oracle.mi(oracle.tables(G, ph, 1, [[s] for s in range(6)]), 1)
+    assert mi1[1] == mi1[3] == mi1[5]
+    for top_n in range(1, 7):
+        idx, _, _ = oracle.search(G, ph, 1, top_n, nthreads=3)
+        assert [int(i[0]) for i in idx] == sorted(range(6), key=lambda s: (-mi1[s], s))[:top_n]
+    combos = list(itertools.combinations(range(6), 2))
+    mi2 = oracle.mi(oracle.tables(G, ph, 2, combos), 2)
+    assert mi2[combos.index((0, 1))] == mi2[combos.index((0, 3))] == mi2[combos.index((0, 5))]
+    for top_n in (1, 2, 4, 8, 15):
+        idx, _, _ = oracle.search(G, ph, 2, top_n, nthreads=2)
+        want = sorted(range(len(combos)), key=lambda c: (-mi2[c], combos[c]))[:top_n]
+        assert [tuple(int(x) for x in r) for r in idx] == [combos[c] for c in want]
+
+
 def test_search_top_n_larger_than_combinations_returns_all():
     ds = random_small(9, S=5, M=20)
     idx, score, tested = oracle.search(ds.genotypes, ds.phenotype, 3, 100, nthreads=2)

@@ -6,8 +6,6 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <string>
-#include <thread>
 #include <tuple>
 
 #include "fc_internal.cuh"
@@ -490,91 +488,38 @@ int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doubl
                 out_count[j] = jd.N;
             }
         }
-        // The tensor-core jobs, largest slab first so that each slab buffer
-        // returned to the pool serves the next jobs (replicates of a data set
-        // share their S and their tile plan).  Two host threads take the jobs
-        // in turn, each on its own stream, so that one job's host work
-        // (planning, uploads, waits) overlaps the other's kernels; each job
-        // releases its operands before its thread takes the next.
+        // The tensor-core jobs, one after another, largest slab first so
+        // that each slab buffer returned to the pool serves the next jobs
+        // (replicates of a data set share their S and their tile plan); each
+        // releases its operands before the next.
         std::vector<int> order;
         for (int j = 0; j < (int)h->jobs.size(); ++j)
             if (B.tc[j]) order.push_back(j);
         auto slab_key = [&](int j) { const Dataset &d = *h->jobs[j]; return (double)d.S * d.S * d.Wt; };
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return slab_key(a) > slab_key(b); });
-        if (order.empty()) return FC_OK;
-        const int nworkers = order.size() > 1 ? 2 : 1;
-        struct Worker {
-            cudaStream_t stream = nullptr;
-            int rc = FC_OK;
-            std::string msg;
-            double sweep_ms = 0.0;
-            int64_t sweeps = 0, launches = 0;
-        };
-        std::vector<Worker> W((size_t)nworkers);
-        for (auto &w : W)
-            if ((e = cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking)) != cudaSuccess) {
-                for (auto &v : W)
-                    if (v.stream) cudaStreamDestroy(v.stream);
-                return cuda_status(e, "job stream");
+        for (const int j : order) {
+            Dataset &d = *h->jobs[j];
+            if (lead.timing && !d.ev_sweep0) {
+                if ((e = cudaEventCreate(&d.ev_sweep0)) != cudaSuccess) return cuda_status(e, "event");
+                if ((e = cudaEventCreate(&d.ev_sweep1)) != cudaSuccess) return cuda_status(e, "event");
             }
-        const bool timing = lead.timing;
-        auto run = [&](int wi) {
-            Worker &w = W[(size_t)wi];
-            for (size_t x = (size_t)wi; x < order.size() && w.rc == FC_OK; x += (size_t)nworkers) {
-                const int j = order[x];
-                Dataset &d = *h->jobs[j];
-                try {
-                    DeviceGuard dg(d.device);
-                    if (timing && !d.ev_sweep0) {
-                        cudaError_t ce;
-                        if ((ce = cudaEventCreate(&d.ev_sweep0)) != cudaSuccess ||
-                            (ce = cudaEventCreate(&d.ev_sweep1)) != cudaSuccess) {
-                            w.rc = cuda_status(ce, "event");
-                            break;
-                        }
-                    }
-                    d.stream = w.stream;
-                    d.timing = timing;
-                    d.sweep_ms = 0.0;
-                    d.sweeps = 0;
-                    d.launches = 0;
-                    d.allow_slabs = true;
-                    w.rc = d.search(k, top_n, out_idx + (size_t)j * top_n * k, out_score + (size_t)j * top_n,
-                                    &out_count[j]);
-                    d.allow_slabs = false;
-                    d.release_triples();
-                    d.release_pairs();
-                    d.stream = st;
-                    d.timing = false;
-                    B.job_kind[j] = d.last_path_tc3 ? 6 : (d.last_sweep_var == VAR_IE ? 3 : d.last_sweep_var == VAR_JR ? 4 : 1);
-                    w.sweep_ms += d.sweep_ms;
-                    w.sweeps += d.sweeps;
-                    w.launches += d.launches;
-                } catch (...) {
-                    w.rc = set_error(FC_ENOMEM, "host exception");
-                    d.stream = st;
-                }
-                if (w.rc != FC_OK) w.msg = fc_last_error();
-            }
-        };
-        if (nworkers == 1) {
-            run(0);
-        } else {
-            std::thread t1(run, 1);
-            run(0);
-            t1.join();
-        }
-        for (auto &w : W) {
-            cudaStreamSynchronize(w.stream);
-            cudaStreamDestroy(w.stream);
-        }
-        for (auto &w : W) {
-            if (w.rc != FC_OK) return set_error(w.rc, "%s", w.msg.c_str());
+            d.timing = lead.timing;
+            d.sweep_ms = 0.0;
+            d.sweeps = 0;
+            d.launches = 0;
+            d.allow_slabs = true;
+            rc = d.search(k, top_n, out_idx + (size_t)j * top_n * k, out_score + (size_t)j * top_n, &out_count[j]);
+            d.allow_slabs = false;
+            d.release_triples();
+            d.release_pairs();
+            if (rc) return rc;
+            B.job_kind[j] = d.last_path_tc3 ? 6 : (d.last_sweep_var == VAR_IE ? 3 : d.last_sweep_var == VAR_JR ? 4 : 1);
             if (lead.timing) {
-                lead.sweep_ms += w.sweep_ms;
-                lead.sweeps += w.sweeps;
-                lead.launches += w.launches;
+                lead.sweep_ms += d.sweep_ms;
+                lead.sweeps += d.sweeps;
+                lead.launches += d.launches;
             }
+            d.timing = false;
         }
         return FC_OK;
     });

@@ -120,3 +120,22 @@ def test_null_arguments_are_rejected(lib):
     assert lib.fc_search(None, 2, 10, None, None, None) == -1
     assert lib.fc_tables(None, 2, None, 0, None) == -1
     lib.fc_free(None)
+
+
+@pytest.mark.parametrize("S,k", [(9, 2), (9, 3), (11, 4), (10, 5), (9, 6)])
+def test_extensions_of_a_prefix_form_one_rank_range(lib, S, k):
+    """The rank-range searches rest on this: the combinations that begin
+    with a given tuple t (of 1 to 3 SNPs) are the contiguous ranks
+    [rank(t, last+1, last+2, ...), + C(S - last - 1, k - |t|))."""
+    import paper_2201_03331_gb300 as fc
+    ranks = {c: r for r, c in enumerate(itertools.combinations(range(S), k))}
+    for T in range(1, min(3, k - 1) + 1):
+        for t in itertools.combinations(range(S), T):
+            last = t[-1]
+            count = math.comb(S - last - 1, k - T)
+            got = sorted(r for c, r in ranks.items() if c[:T] == t)
+            assert len(got) == count
+            if count == 0:
+                continue
+            first = fc.fc_rank(S, k, list(t) + [last + 1 + q for q in range(k - T)])
+            assert got == list(range(first, first + count))

@@ -30,6 +30,9 @@
  *     returned.
  *   - Work runs on the handle's CUDA stream (fc_set_stream); every entry
  *     point returns after its results are in the caller's buffers.
+ *   - Threads: calls on different handles may run concurrently (the
+ *     library's shared state, a pool of freed operand buffers and a cached
+ *     tile plan, is locked); calls on one handle must not overlap.
  */
 #ifndef FIUNCHO_H
 #define FIUNCHO_H

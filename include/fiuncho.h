@@ -161,10 +161,21 @@ int fc_search_range(fc_handle *h, int k, int64_t top_n, uint64_t rank_begin, uin
  *   - a search whose work area (per-CTA candidate lists, merge and
  *     rescoring buffers, device results) exceeds FC_STATIC_SCRATCH_BYTES
  *     fails with FC_ERANGE and a message giving the size it needed; this
- *     happens for large top_n (e.g. top_n = 2000 needs about 15 MiB);
+ *     happens for large top_n (e.g. top_n = 2000 needs about 15 MiB), and
+ *     can also happen for a smaller top_n on data with many near-tied
+ *     scores: when more candidates than the list holds fall within the FP32
+ *     error window, the search retries with a list four times longer, and
+ *     that retry may not fit (fc_last_error says which of the two refused);
+ *   - operands that fc_search builds on first use and keeps in the handle
+ *     (tensor-core operands, inclusion-exclusion tables) are used only if
+ *     an earlier fc_search on the handle built them; otherwise the search
+ *     takes a sweep that needs none, with the same results;
  *   - the first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture;
+ *     before any stream capture.  The address is kept for the life of the
+ *     process, so the library must run in the device's primary context (the
+ *     one the CUDA runtime uses) and must not be used across a
+ *     cudaDeviceReset of that device;
  *   - all calls share the one array and each overwrites what the previous
  *     one left there (every byte read is written first in the same call, so
  *     nothing needs clearing); calls whose GPU work overlaps in time, from

@@ -237,6 +237,11 @@ cudaError_t launch_final_sort_batch(const JobDesc *jobs, int n_jobs, double *res
 
 constexpr int TC_MAX_STAGES = 6;
 enum { MODE_DUMP = 2 };
+// Time budget of one mbarrier wait in the tensor-core kernels, in clock64
+// ticks (about 2 s).  The pipeline waits of the order-2 kernel take theirs
+// from PairsArgs::wait_ticks (a test shortens it so that the waits run out);
+// the drain waits before the kernel exits always take this one.
+constexpr long long TC_WAIT_TICKS = 4000000000ll;
 
 struct PairsArgs {
     const uint32_t *tiles;  // (I << 16 | J) 64-SNP block pairs, I <= J
@@ -250,6 +255,7 @@ struct PairsArgs {
     uint64_t pair_base;     // C(S, 2)
     uint64_t rank_begin, rank_end;   // only pairs with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2, stages;
+    long long wait_ticks;   // budget of each pipeline wait (clock64 ticks)
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
     int *gthr;              // global score threshold (ordered int)

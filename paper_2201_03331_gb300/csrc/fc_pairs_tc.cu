@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                 // the MMA and epilogue warps through the scheduling ring.
                 const int slot = it % TC_SCHED;
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
-                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err, a.wait_ticks)) break;
                 int t = atomicAdd(a.tile_counter, 1);
                 if (t >= a.ntiles) t = -1;
                 sched_tile[slot] = t;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                     for (int kc = 0; kc < nk; ++kc, ++fill) {
                         const int s = fill % stages;
                         const uint32_t n = fill / stages;
-                        if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err, a.wait_ticks)) { ok = false; break; }
                         mbar_expect_tx(&bar_full[s], TC_A_BYTES + TC_B_BYTES);
                         tma_load_2d(&tmap, &bar_full[s], stA + (size_t)s * TC_A_BYTES, xbase + kc * TC_BK, I * TC_BM);
                         tma_load_2d(&tmap, &bar_full[s], stB + (size_t)s * TC_B_BYTES, xbase + kc * TC_BK, J * TC_BN);
@@ -196,13 +196,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
             for (int it = 0; ok; ++it) {
                 const int slot = it % TC_SCHED;
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
-                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, a.wait_ticks)) break;
                 const int t = sched_tile[slot];
                 mbar_arrive(&bar_sempty[slot]);
                 if (t < 0) break;
                 const int b = it & 1;
                 const uint32_t u = (uint32_t)(it >> 1);
-                if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err, a.wait_ticks)) break;
                 tc_fence_after();
                 for (int c = 0; c < 2 && ok; ++c) {
                     const int nk = c ? kc1 : kc0;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
                     for (int kc = 0; kc < nk; ++kc, ++fill) {
                         const int s = fill % stages;
                         const uint32_t n = fill / stages;
-                        if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err, a.wait_ticks)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t aaddr = smem_u32(stA + (size_t)s * TC_A_BYTES);
                         const uint32_t baddr = smem_u32(stB + (size_t)s * TC_B_BYTES);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
         for (int it = 0;; ++it) {
             const int slot = it % TC_SCHED;
             const uint32_t sn = (uint32_t)(it / TC_SCHED);
-            const bool ok = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err);
+            const bool ok = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, a.wait_ticks);
             const int t = ok ? sched_tile[slot] : -1;
             if (ok) {
                 __syncwarp();
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_pairs_tc(const __grid_constan
             }
             const int b = it & 1;
             const uint32_t u = (uint32_t)(it >> 1);
-            if (t >= 0) mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
+            if (t >= 0) mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err, a.wait_ticks);
             // One stop decision for all four epilogue warps (they meet at
             // named barriers, which have no timeout); t is the same for all.
             epi_bar();

@@ -44,8 +44,10 @@ int cuda_status(cudaError_t e, const char *what)
 
 // ---- fault injection (host side only) --------------------------------------
 // FC_FAULT_ALLOC=n makes the n-th device allocation of the process report
-// cudaErrorMemoryAllocation without calling CUDA; FC_FAULT_LAUNCH=n makes the
-// n-th kernel launch sequence report cudaErrorLaunchFailure before launching.
+// cudaErrorMemoryAllocation without calling CUDA, and FC_FAULT_ALLOC_ALL=1
+// makes every device allocation report it while the variable is set;
+// FC_FAULT_LAUNCH=n makes the n-th kernel launch sequence report
+// cudaErrorLaunchFailure before launching.
 
 namespace {
 std::atomic<long> g_alloc_count{0}, g_launch_count{0};
@@ -60,7 +62,10 @@ cudaError_t dev_alloc(void **p, size_t bytes)
 {
     const long n = ++g_alloc_count;
     const long f = env_long("FC_FAULT_ALLOC");
-    if (f > 0 && n == f) { *p = nullptr; return cudaErrorMemoryAllocation; }
+    if ((f > 0 && n == f) || env_long("FC_FAULT_ALLOC_ALL") > 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc(p, bytes);
 }
 
@@ -341,10 +346,14 @@ int list_capacity(int64_t N)
 
 float score_error_bound(int k, int64_t M)
 {
-    // FP32 sweep: log table entries within 2^-24 relative, differences,
-    // products and 2*3^k accumulations each within 2^-24 relative of a
-    // partial sum bounded by N ln 2; see the design notes.  Doubled for
-    // margin.
+    // FP32 sweep score H(Y) - (1/N) sum_x [a (ln n - ln a) + b (ln n - ln b)]
+    // with u = 2^-24: each ln table entry errs by <= u ln M, so each
+    // difference by <= 2u ln M + u d; each product adds u a d; each of the
+    // 2*3^k accumulations adds <= u N ln 2 (partial sums are bounded by
+    // N H(Y|X) <= N ln 2); the final scaling and subtraction <= 3u ln 2.
+    // Divided by N: |MI32 - MI| <= u (2 ln M + (2*3^k + 6) ln 2).  The
+    // tensor-core epilogues' x ln x form has the smaller bound
+    // u (3 ln M + (3^k + 4) ln 2) for every M used here.  Doubled for margin.
     const double u = std::ldexp(1.0, -24);
     const double terms = 2.0 * pow3(k);
     const double e = u * (2.0 * std::log((double)std::max<int64_t>(M, 2)) + (terms + 6.0) * std::log(2.0));
@@ -591,6 +600,13 @@ PairsArgs Dataset::pairs_args(int L, float hy, float invN)
     pa.stages = 2;
     for (int st = TC_MAX_STAGES; st >= 2; --st) {
         if (pairs_smem_bytes(st, (int)M, pa.P2) <= (size_t)max_smem_optin) { pa.stages = st; break; }
+    }
+    // FC_TEST_WAIT_TICKS (tests only) shortens the pipeline waits so that
+    // they run out and the kernel reports FC_ETIMEOUT.
+    pa.wait_ticks = TC_WAIT_TICKS;
+    if (const char *w = getenv("FC_TEST_WAIT_TICKS")) {
+        const long long v = atoll(w);
+        if (v > 0 && v < TC_WAIT_TICKS) pa.wait_ticks = v;
     }
     return pa;
 }
@@ -1360,10 +1376,17 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         Arena A2;
         if (ext_scratch) {
             // Caller-provided scratch (the allocation-free entry point).
-            if (ar.off > ext_cap)
+            if (ar.off > ext_cap) {
+                if (L > list_capacity(N))
+                    return set_error(FC_ERANGE,
+                                     "search needs %zu bytes of scratch after widening its candidate list to "
+                                     "%d for near-tied scores; the static scratch area holds %zu",
+                                     ar.off, L, ext_cap);
                 return set_error(FC_ERANGE,
-                                 "search needs %zu bytes of scratch; the static scratch area holds %zu",
-                                 ar.off, ext_cap);
+                                 "search needs %zu bytes of scratch for top_n %lld; the static scratch area "
+                                 "holds %zu",
+                                 ar.off, (long long)top_n, ext_cap);
+            }
             A2.base = ext_scratch;
         } else {
             int rc = reserve_scratch(ar.off);

@@ -21,7 +21,7 @@ constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;   // 16 KiB
 constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK;   // 16 KiB
 constexpr unsigned FULL = 0xffffffffu;
-constexpr long long WAIT_BUDGET = 4000000000ll;  // clock64 ticks (~2 s) per wait
+constexpr long long WAIT_BUDGET = TC_WAIT_TICKS;  // clock64 ticks (~2 s) per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -60,13 +60,13 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 // Bounded wait for the phase of the given parity.  On timeout it raises the
 // CTA abort flag and the device error word; every role then leaves its loop.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          uint32_t *err)
+                                          uint32_t *err, long long budget = WAIT_BUDGET)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_BUDGET) {
+        if (clock64() - t0 > budget) {
             *abort_flag = 1;
             atomicOr(err, ERR_TIMEOUT);
             return false;

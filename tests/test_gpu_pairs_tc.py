@@ -120,3 +120,30 @@ def test_all_pairs_full_size(fc, path):
     p_idx, p_s = fc.fc_search(h, 2, ds.top_n)
     assert np.array_equal(p_idx, g_idx)
     np.testing.assert_allclose(p_s, g_s, rtol=1e-12)
+
+
+def test_bounded_wait_runs_out_and_the_handle_recovers(fc, path, monkeypatch):
+    """Failure detection on the device: every mbarrier wait of the
+    tensor-core kernel has a time budget.  FC_TEST_WAIT_TICKS shrinks the
+    budget of the pipeline waits to a few hundred clock ticks, so that they
+    run out on the first tile; the kernel then raises its abort flag, lets
+    its copies and MMAs finish (the drain waits keep the full budget), frees
+    TMEM and returns, and the search reports FC_ETIMEOUT.  The next search on
+    the same handle, with the normal budget, matches the oracle."""
+    ds = make_dataset("tmo", seed=330, S=300, cases=1100, controls=1237, k=2, top_n=20, planted=(30, 250))
+    path("tc")
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    monkeypatch.setenv("FC_TEST_WAIT_TICKS", "200")
+    with pytest.raises(fc.FiunchoError) as e:
+        fc.fc_search(h, 2, 20)
+    assert e.value.status == fc.FC_ETIMEOUT
+    assert fc.fc_last_search_kind(h) == 2
+    monkeypatch.delenv("FC_TEST_WAIT_TICKS")
+    idx, s = fc.fc_search(h, 2, 20)
+    assert fc.fc_last_search_kind(h) == 2
+    o_idx, o_s, _ = oracle.search(ds.genotypes, ds.phenotype, 2, 20)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 2, [c]), 2)[0])
+    assert_topn_equal(idx, s, o_idx, o_s, score_of)
+    assert tuple(idx[0]) == (30, 250)

@@ -23,8 +23,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def fp32_bound(k, M):
     """Bound on |FP32 sweep score - exact MI| in nats: 2 * 2^-24 *
-    (2 ln M + (2*3^k + 6) ln 2) (log-table, subtraction, product and
-    accumulation rounding; see the design notes)."""
+    (2 ln M + (2*3^k + 6) ln 2).  With u = 2^-24: each ln table entry errs
+    by u ln M, each difference of two by 2u ln M plus its own rounding, each
+    product and each of the 2*3^k accumulations by u times a partial sum
+    bounded by N ln 2, the final scaling and subtraction by 3u ln 2; divided
+    by N and doubled for margin."""
     u = 2.0 ** -24
     return 2.0 * u * (2.0 * math.log(max(M, 2)) + (2.0 * 3 ** k + 6.0) * math.log(2.0))
 

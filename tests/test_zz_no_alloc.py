@@ -12,11 +12,14 @@ search too large for the array is refused.
 This file is collected last so that a run stopping at the first failure
 has already run every other test.
 """
+import os
+
 import numpy as np
 import pytest
 
+import oracle
 from synth import make_dataset
-from tests.parity_util import SCORE_REL
+from tests.parity_util import SCORE_REL, assert_topn_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -67,3 +70,48 @@ def test_static_search_rejects_work_beyond_the_array(fc):
     # The regular entry point still serves it.
     idx, _ = fc.fc_search(h, 2, 2000)
     assert len(idx) == 2000
+
+
+def test_static_search_first_on_a_fresh_handle_matches_oracle(fc):
+    # No fc_search has run on this handle, so the operands fc_search builds
+    # on first use (inclusion-exclusion tables) do not exist: the static
+    # search takes a sweep that needs none, with the same results.
+    ds = make_dataset("na-fresh", seed=95, S=120, cases=800, controls=900, k=3, top_n=40,
+                      planted=(11, 60, 101))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    idx, s = fc.fc_search_static(h, 3, 40)
+    o_idx, o_s, _ = oracle.search(ds.genotypes, ds.phenotype, 3, 40)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, 3, [c]), 3)[0])
+    assert_topn_equal(idx, s, o_idx, o_s, score_of)
+    assert tuple(idx[0]) == (11, 60, 101)
+
+
+def test_static_search_allocates_nothing(fc):
+    """With every device allocation of the library made to fail
+    (FC_FAULT_ALLOC_ALL), fc_search_static still succeeds, and the device's
+    free memory is the same before and after it."""
+    import torch
+    ds = make_dataset("na-none", seed=96, S=110, cases=600, controls=700, k=3, top_n=30)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    ref = fc.fc_search(h, 3, 30)
+    fc.fc_search_static(h, 3, 30)          # the array's module is loaded by now
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    os.environ["FC_FAULT_ALLOC_ALL"] = "1"
+    try:
+        # The switch is live: a fresh handle's fc_search must grow scratch.
+        h2 = None
+        with pytest.raises(fc.FiunchoError) as e:
+            h2 = fc.fc_load(ds.genotypes, ds.phenotype)
+        assert e.value.status == fc.FC_ENOMEM
+        assert h2 is None
+        for _ in range(2):
+            idx, s = fc.fc_search_static(h, 3, 30)
+            assert np.array_equal(idx, ref[0])
+            np.testing.assert_allclose(s, ref[1], rtol=SCORE_REL, atol=1e-12)
+    finally:
+        del os.environ["FC_FAULT_ALLOC_ALL"]
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0

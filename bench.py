@@ -444,9 +444,9 @@ def run_ours(args):
                    "k": k, "snps": ds.S, "samples": ds.M,
                    "cases": ds.cases, "controls": ds.controls, "top_n": top_n,
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "resident": "packed bit table and the data set's tensor-core operands (e4m3 rows, "
-                               "pair-row or tuple-row slabs when they fit one slab), built by fc_load and "
-                               "the first search; e2e rebuilds all of them every step",
+                   "resident": "packed bit table and the data set's tensor-core operands (e4m3 rows and "
+                               "inclusion-exclusion tables; orders 4-6: tuple-row slabs), built by fc_load "
+                               "and the first search; e2e rebuilds all of them every step",
                    "parallelism": ("one search sharded by rank range over the GPUs" if shard else
                                    "one independent data set per GPU" if world > 1 else "single GPU")},
         "sample_combinations_per_s": value * ds.M,

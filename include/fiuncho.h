@@ -308,6 +308,17 @@ int fc_triples_dense(fc_handle *h, float *scores, uint32_t *tables);
  */
 int fc_tuples_dense(fc_handle *h, int k, float *scores, uint32_t *tables);
 
+/*
+ * fc_triples_form - the form the order-3 tensor-core kernel takes for this
+ * data set: 1 = one FP32 accumulator per cell holding n_case + 4096 n_ctrl
+ * (control samples enter the contraction with the e4m3 value 64; exact
+ * while both classes have at most 4095 samples and the kernel's shared
+ * memory fits), 0 = one accumulator per class, -1 = the kernel does not
+ * fit (the order-3 search takes the sweep).  Environment FC_TRIPLES_ENC=0
+ * forces form 0.  A parity hook; FC_EINVAL for a NULL handle.
+ */
+int fc_triples_form(const fc_handle *h);
+
 /* fc_last_search_kind - which sweep the last fc_search on h ran:
  * 0 none yet, 1 prefix-table AND/POPC sweep counting all 3^k cells,
  * 2 tensor-core order-2 pairs, 3 prefix-table sweep counting the 2^k cells

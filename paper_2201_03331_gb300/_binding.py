@@ -54,6 +54,7 @@ _SIGNATURES = {
     "fc_batch_info": ([P, P, P, P], i32),
     "fc_batch_job_kind": ([P, i32], i32),
     "fc_last_search_kind": ([P], i32),
+    "fc_triples_form": ([P], i32),
     "fc_sweep_tables": ([P, i32, u64, i64, P], i32),
     "fc_timing": ([P, i32, P, P, P], i32),
     "fc_free": ([P], None),
@@ -304,6 +305,15 @@ def fc_sweep_tables(h: Handle, k: int, rank_begin: int, n: int) -> np.ndarray:
     out = np.zeros((n, 3 ** k, 2), dtype=np.uint32)
     _check(library().fc_sweep_tables(h.ptr, k, rank_begin, n, _ptr(out)), "fc_sweep_tables")
     return out
+
+
+def fc_triples_form(h: Handle) -> int:
+    """Form of the order-3 tensor-core kernel for this data set: 1 one
+    accumulator (cases + 4096 controls), 0 one per class, -1 none."""
+    r = library().fc_triples_form(h.ptr)
+    if r < -1:
+        _check(r, "fc_triples_form")
+    return int(r)
 
 
 def fc_last_search_kind(h: Handle) -> int:

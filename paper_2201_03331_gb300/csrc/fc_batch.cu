@@ -151,9 +151,9 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
     for (int j = 0; j < n_all; ++j) {
         Dataset &d = *h->jobs[j];
         if (tc_on) {
-            d.allow_slabs = true;
+            d.allow_tc = true;
             B.tc[j] = d.triples_tc_eligible(L) ? 1 : 0;
-            d.allow_slabs = false;
+            d.allow_tc = false;
         }
         if (!B.tc[j]) B.sel.push_back(j);
     }
@@ -402,7 +402,7 @@ int fc_load_batch(int n_data, const uint8_t *const *genotypes, const int64_t *S,
                 // Jobs are searched by the batched sweep; the per-job path
                 // runs the same sweep, and no job keeps a pair-row slab
                 // (many resident jobs could not each hold one).
-                job->allow_slabs = false;
+                job->allow_tc = false;
                 rc = job->load(dG, dph + (size_t)r * M[d], S[d], M[d]);
                 if (rc) {
                     rc = set_error(rc, "data set %d replicate %d: %s", d, r, fc_last_error());
@@ -507,9 +507,9 @@ int fc_search_batch(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, doubl
             d.sweep_ms = 0.0;
             d.sweeps = 0;
             d.launches = 0;
-            d.allow_slabs = true;
+            d.allow_tc = true;
             rc = d.search(k, top_n, out_idx + (size_t)j * top_n * k, out_score + (size_t)j * top_n, &out_count[j]);
-            d.allow_slabs = false;
+            d.allow_tc = false;
             d.release_triples();
             d.release_pairs();
             if (rc) return rc;
@@ -544,9 +544,9 @@ int fc_search_job(fc_handle *h, int job, int k, int64_t top_n, uint32_t *out_idx
         const BatchState &B = *h->batch;
         const bool tc = B.planned && B.k == k && job < (int)B.tc.size() && B.tc[job];
         if (!tc) return d.search(k, top_n, out_idx, out_score, out_count);
-        d.allow_slabs = true;
+        d.allow_tc = true;
         const int rc = d.search(k, top_n, out_idx, out_score, out_count);
-        d.allow_slabs = false;
+        d.allow_tc = false;
         d.release_triples();
         d.release_pairs();
         return rc;

@@ -266,18 +266,23 @@ struct PairsArgs {
 };
 
 size_t pairs_smem_bytes(int stages, int M, int P2);
-cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch, uint8_t *E,
-                               cudaStream_t st);
+// ctrl_byte: the e4m3 byte of a control sample's set bit (0x38 = 1.0, or
+// 0x68 = 64.0 for the order-3 kernel's one-accumulator encoding); case
+// samples (words below W0) always carry 0x38.
+cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, int64_t rows, int64_t pitch,
+                               uint8_t *E, uint8_t ctrl_byte, cudaStream_t st);
 cudaError_t launch_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, uint16_t *marg,
                              cudaStream_t st);
 cudaError_t launch_pairs_tc(int mode, const CUtensorMap &tmap, const PairsArgs &a, int grid, cudaStream_t st);
 
 // Order-3 tensor-core search (fc_triples_tc.cu).  A tile pairs the 64 SNPs
-// l of block Lb (128 e4m3 rows 2 l + g) with the 32 pairs (i, 32 J + q) of
-// slab rows [rowP, rowP + 128) (four rows (a, b) per pair).
+// l of block Lb (128 e4m3 rows 2 l + g) with the NP pairs (i, NP J + q),
+// q < NP, of slab rows [rowP, rowP + 4 NP) (pair row (a, q, b) at
+// rowP + 2 NP a + 2 q + b); NP = triples_pairs_per_tile(enc).
 struct TriplesArgs {
     const uint4 *tiles;     // {rowP, i, J, Lb} per tile of this launch
     int ntiles;
+    int enc;                // 1: one accumulator n_case + 4096 n_ctrl (operand with controls = 64)
     int64_t S, S_pad;
     int W0, Wt;             // 128-sample chunks: cases [0, W0), controls [W0, Wt)
     const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
@@ -287,7 +292,8 @@ struct TriplesArgs {
     float hy, invN;
     uint64_t total;         // C(S, 3)
     uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count
-    int L, Bcap, P2, stages;
+    int L, Bcap, P2;        // list, candidate buffer (>= 2048), pow2 >= L + Bcap
+    long long wait_ticks;   // budget of each pipeline wait (clock64 ticks)
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
     int *gthr;              // global score threshold (ordered int)
@@ -297,9 +303,15 @@ struct TriplesArgs {
     uint32_t *dump_tables;  // MODE_DUMP: [C(S,3)][27][2]
 };
 
-cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int64_t S32, int64_t i0, int64_t i1,
+int triples_pairs_per_tile(int enc);
+size_t triples_smem_bytes(int enc, int M, int P2);
+// Slab rows of the first SNPs [i0, i1) from the e4m3 rows E (pitch bytes per
+// row); rowbase[i - i0] is the first slab row of SNP i.
+cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int NP, int64_t i0, int64_t i1,
                              const int64_t *rowbase, uint8_t *P, cudaStream_t st);
-cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapE, const CUtensorMap &tmapP, const TriplesArgs &a,
+// tmapA: the e4m3 rows in 128 x 128-byte boxes; tmapP: the slab in 4 NP x
+// 128-byte boxes (both with the 128-byte swizzle).
+cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapA, const CUtensorMap &tmapP, const TriplesArgs &a,
                               int grid, cudaStream_t st);
 
 // Orders 4 to 6 on tensor cores (fc_quads_tc.cu): left tuples of LT SNPs

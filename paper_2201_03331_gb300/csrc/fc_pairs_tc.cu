@@ -29,9 +29,11 @@ namespace {
 
 // ---- data preparation ------------------------------------------------------
 
-// E[2s + g][w*128 + b] = 0x38 (e4m3 1.0) if bit b of word w of genotype row
-// g of SNP s is set, else 0; rows of padding SNPs are zero.
-__global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch, uint8_t *E)
+// E[2s + g][w*128 + b] = 0x38 (e4m3 1.0), or ctrl_byte for the control words
+// w >= W0, if bit b of word w of genotype row g of SNP s is set, else 0;
+// rows of padding SNPs are zero.
+__global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, int64_t rows, int64_t pitch,
+                              uint8_t *E, uint32_t ctrl_byte)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= rows * Wt) return;
@@ -52,8 +54,9 @@ __global__ void k_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, 
             const uint32_t word = b32[bit0 >> 5];
             const int sh = bit0 & 31;
             uint32_t v = 0;
+            const uint32_t one = w < W0 ? 0x38u : ctrl_byte;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) v |= (((word >> (sh + e)) & 1u) ? 0x38u : 0u) << (8 * e);
+            for (int e = 0; e < 4; ++e) v |= (((word >> (sh + e)) & 1u) ? one : 0u) << (8 * e);
             o[u] = v;
         }
         dst[q] = make_uint4(o[0], o[1], o[2], o[3]);
@@ -417,11 +420,11 @@ size_t pairs_smem_bytes(int stages, int M, int P2)
            (size_t)P2 * (8 + 4);
 }
 
-cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch, uint8_t *E,
-                               cudaStream_t st)
+cudaError_t launch_expand_e4m3(const uint4 *X, int64_t S, int64_t S_pad, int W0, int Wt, int64_t rows, int64_t pitch,
+                               uint8_t *E, uint8_t ctrl_byte, cudaStream_t st)
 {
     const int64_t n = rows * Wt;
-    k_expand_e4m3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S, S_pad, Wt, rows, pitch, E);
+    k_expand_e4m3<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S, S_pad, W0, Wt, rows, pitch, E, ctrl_byte);
     return cudaGetLastError();
 }
 

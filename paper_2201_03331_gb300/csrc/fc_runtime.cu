@@ -324,11 +324,12 @@ Dataset::~Dataset()
     cudaFree(marg);
     dev_free_pooled(tiles, tiles_bytes, device);
     cudaFree(PR);
-    dev_free_pooled(P3, p3_bytes, device);
     cudaFree(xlogx);
     for (int k = 4; k <= 6; ++k) release_tuples(k);
     dev_free_pooled(tiles3, tiles3_bytes, device);
     dev_free_pooled(rowbase3, rowbase3_bytes, device);
+    dev_free_pooled(P3, p3_bytes, device);
+    dev_free_pooled(E3, e3_bytes, device);
     if (ev_sweep0) cudaEventDestroy(ev_sweep0);
     if (ev_sweep1) cudaEventDestroy(ev_sweep1);
     if (own_stream && own_stream_handle) cudaStreamDestroy(own_stream_handle);
@@ -528,7 +529,8 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                    CUtensorMapFloatOOBfill);
 
-int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t pitch, uint64_t rows)
+int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t pitch, uint64_t rows,
+                   uint32_t box_rows, bool swizzle128)
 {
     static EncodeTiledFn fn = nullptr;
     static std::mutex mu;
@@ -546,11 +548,11 @@ int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t 
     }
     const cuuint64_t dims[2] = {inner_bytes, rows};
     const cuuint64_t strides[1] = {pitch};
-    const cuuint32_t box[2] = {128, 128};
+    const cuuint32_t box[2] = {128, box_rows};
     const cuuint32_t elem[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, elem,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return FC_OK;
 }
@@ -643,11 +645,11 @@ int Dataset::prepare_pairs()
     if ((e = dev_alloc_pooled((void **)&tiles, tiles_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tile list allocation");
     cudaMemcpyAsync(tiles, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice, stream);
-    if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, Wt, rows, (int64_t)pitch, E, stream)) != cudaSuccess ||
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_expand_e4m3(X, S, S_pad, W0, Wt, rows, (int64_t)pitch, E, 0x38, stream)) != cudaSuccess ||
         (need_marg && (e = launch_marginals(X, S, S_pad, W0, Wt, marg, stream)) != cudaSuccess))
         return cuda_status(e, "pair operand preparation");
     note_launches(need_marg ? 2 : 1);
-    int rc = encode_tmap_u8(&tmap, E, kbytes, pitch, (uint64_t)rows);
+    int rc = encode_tmap_u8(&tmap, E, kbytes, pitch, (uint64_t)rows, 128, true);
     if (rc) return rc;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair operand preparation");
     pairs_ready = true;
@@ -699,26 +701,48 @@ int Dataset::pairs_dense(float *scores, uint32_t *tables)
 
 // ---- order-3 tensor-core operands --------------------------------------------
 
+// The order-3 tensor-core form for this data set: 1 (one accumulator
+// n_case + 4096 n_ctrl) while both classes have at most 4095 samples and
+// its shared memory fits, else 0 (one accumulator per class), else -1 (no
+// tensor-core search).  FC_TRIPLES_ENC=0 forces the per-class form.
+int Dataset::triples_form(int L) const
+{
+    const int P2 = triples_list_size(L);
+    const char *f = getenv("FC_TRIPLES_ENC");
+    const bool enc_ok = !(f && strcmp(f, "0") == 0) && M1 <= 4095 && M0 <= 4095;
+    if (enc_ok && triples_smem_bytes(1, (int)M, P2) <= (size_t)max_smem_optin) return 1;
+    if (triples_smem_bytes(0, (int)M, P2) <= (size_t)max_smem_optin) return 0;
+    return -1;
+}
+
+// Candidate list of the order-3 kernel: L entries and a buffer of at least
+// 2048 (two rounds of its epilogue insert at most 1536).
+int Dataset::triples_list_size(int L)
+{
+    return pow2_at_least(std::max(L, 1) + 2048);
+}
+
 bool Dataset::triples_tc_eligible(int L)
 {
     const char *mode = getenv("FC_TRIPLES_PATH");
     if (mode && strcmp(mode, "popc") == 0) return false;
-    if (!allow_slabs) return false;
+    if (!allow_tc) return false;
     const bool forced = mode && strcmp(mode, "tc") == 0;
     if (!forced && S < 384) return false;
     if (S < 3 || S > 65535 || L > 2048) return false;
-    // Each class needs at least one K chunk, or its accumulator is never written.
+    // Both classes need samples (each accumulator is written by its chunks).
     if (W0 == 0 || Wt == W0) return false;
     // The restricted pair table of the epilogue holds S_pad^2 x 16 bytes.
     if ((double)S_pad * (double)S_pad * 16.0 > 2.0 * 1024 * 1024 * 1024) return false;
-    const int Bcap = std::max(L, 1024);
-    const int P2 = pow2_at_least(L + Bcap);
-    return pairs_smem_bytes(2, (int)M, P2) <= (size_t)max_smem_optin;
+    return triples_form(L) >= 0;
 }
 
 TriplesArgs Dataset::triples_args(int L, float hy, float invN)
 {
     TriplesArgs ta{};
+    ta.tiles = tiles3;
+    ta.ntiles = (int)ntiles3;
+    ta.enc = enc3;
     ta.S = S;
     ta.S_pad = S_pad;
     ta.W0 = W0;
@@ -732,49 +756,52 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.total = binom(S, 3);
     ta.rank_begin = 0;
     ta.rank_end = ~0ull;
-    ta.L = L;
-    ta.Bcap = L > 0 ? std::max(L, 1024) : 0;
-    ta.P2 = L > 0 ? pow2_at_least(L + ta.Bcap) : 0;
-    ta.stages = 2;
-    for (int st = TC_MAX_STAGES; st >= 2; --st) {
-        if (pairs_smem_bytes(st, (int)M, ta.P2) <= (size_t)max_smem_optin) { ta.stages = st; break; }
-    }
+    ta.L = std::max(L, 1);
+    ta.P2 = triples_list_size(L);
+    ta.Bcap = ta.P2 - ta.L;
+    ta.wait_ticks = TC_WAIT_TICKS;
     return ta;
 }
 
 namespace {
-// The last slab and tile plan of order 3; it depends on S and the slab
-// capacity only, so the phenotype replicates of one data set (and data sets
-// of equal S) share it.
+// The last order-3 slab and tile plan; it depends on S, the pairs per tile
+// and the slab capacity only, so the phenotype replicates of one data set
+// (and data sets of equal S) share it.
 struct TriplePlan {
     int64_t S = -1, cap_rows = -1, max_rows = 0;
+    int NP = 0;
     std::vector<uint4> tiles;
     std::vector<int64_t> first_tile;   // [S + 1]: tiles of first SNP i are [first_tile[i], first_tile[i + 1])
-    std::vector<int64_t> rowbase;
+    std::vector<int64_t> rowbase;      // [S]: first slab row of SNP i within its slab
     std::vector<Dataset::TripleSlab> slabs;
 };
 std::mutex g_plan3_mu;
 std::shared_ptr<const TriplePlan> g_plan3;
 
-std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
+// Tiles {rowP, i, J, Lb}: first SNP i, block J of NP second SNPs j (from the
+// block of i + 1; slab rows [rowP, rowP + 4 NP)), 64-SNP block Lb of the
+// third SNPs l, for every block that holds some l > j; in order of i, so that
+// a rank range is a contiguous run of tiles.  Slabs hold the rows of
+// consecutive first SNPs up to cap_rows rows (at least one SNP's).
+std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_rows)
 {
     {
         std::lock_guard<std::mutex> lock(g_plan3_mu);
-        if (g_plan3 && g_plan3->S == S && g_plan3->cap_rows == cap_rows) return g_plan3;
+        if (g_plan3 && g_plan3->S == S && g_plan3->NP == NP && g_plan3->cap_rows == cap_rows) return g_plan3;
     }
     auto pl = std::make_shared<TriplePlan>();
     pl->S = S;
+    pl->NP = NP;
     pl->cap_rows = cap_rows;
-    const int64_t S32 = (S + 31) / 32 * 32;
+    const int64_t nJ = (S + NP - 1) / NP;
     const int64_t nLb = (S + 63) / 64;
     std::vector<uint4> &tiles = pl->tiles;
-    std::vector<int64_t> &rowbase = pl->rowbase;
-    rowbase.assign((size_t)S, 0);
+    pl->rowbase.assign((size_t)S, 0);
     pl->first_tile.assign((size_t)S + 1, 0);
     Dataset::TripleSlab cur;
     for (int64_t i = 0; i + 2 < S; ++i) {
-        const int64_t Jlo = (i + 1) / 32;
-        const int64_t n = (S32 / 32 - Jlo) * 128;   // rows of the pairs of i
+        const int64_t Jlo = (i + 1) / NP;
+        const int64_t n = (nJ - Jlo) * 4 * NP;   // rows of the pairs of i
         if (cur.rows + n > cap_rows && i > cur.i0) {
             cur.i1 = i;
             cur.t1 = (int64_t)tiles.size();
@@ -784,12 +811,12 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
             cur.i0 = i;
             cur.t0 = (int64_t)tiles.size();
         }
-        rowbase[(size_t)i] = cur.rows;
+        pl->rowbase[(size_t)i] = cur.rows;
         pl->first_tile[(size_t)i] = (int64_t)tiles.size();
-        for (int64_t J = Jlo; 32 * J <= S - 2; ++J) {
-            const int64_t jmin = std::max<int64_t>(32 * J, i + 1);
+        for (int64_t J = Jlo; NP * J <= S - 2; ++J) {
+            const int64_t jmin = std::max<int64_t>(NP * J, i + 1);
             for (int64_t Lb = (jmin + 1) / 64; Lb < nLb; ++Lb)
-                tiles.push_back(make_uint4((uint32_t)(cur.rows + (J - Jlo) * 128), (uint32_t)i, (uint32_t)J,
+                tiles.push_back(make_uint4((uint32_t)(cur.rows + (J - Jlo) * 4 * NP), (uint32_t)i, (uint32_t)J,
                                            (uint32_t)Lb));
         }
         cur.rows += n;
@@ -807,14 +834,18 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int64_t cap_rows)
 }
 }  // namespace
 
-// Plans the slabs and tiles, allocates the slab buffer and builds the
-// first slab.  A slab holds at most min(16 GiB, a quarter of the free device
-// memory) of pair rows (FC_TRIPLES_SLAB_MB overrides the 16 GiB), and at
-// least the rows of one first SNP.  A single slab is kept for later
-// searches; with several, the buffer is released after each search.
+// The e4m3 rows (those of the order-2 path, or a copy with controls = 64 for
+// the one-accumulator form), the inclusion-exclusion tables, the x ln x
+// table, the slab and tile plan, the slab buffer with its first slab and the
+// kernel's two TMA descriptors.  A slab holds at most min(16 GiB, a quarter
+// of the free device memory) of pair rows (FC_TRIPLES_SLAB_MB overrides the
+// 16 GiB), and at least the rows of one first SNP.  A single slab is kept for
+// later searches; with several, the buffer is released after each search.
 int Dataset::prepare_triples()
 {
     if (triples_ready) return FC_OK;
+    const int form = triples_form(2048);
+    if (form < 0) return set_error(FC_ERANGE, "order-3 tensor-core kernel does not fit in shared memory");
     int rc = prepare_pairs();
     if (rc) return rc;
     if ((rc = prepare_ie(3)) != FC_OK) return rc;
@@ -826,9 +857,25 @@ int Dataset::prepare_triples()
             return cuda_status(e, "x ln x table");
         note_launches(1);
     }
-    const int64_t S32 = (S + 31) / 32 * 32;
+    const int64_t S64 = (S + 63) / 64 * 64;
+    const int64_t rows = 2 * S64;
     const uint64_t kbytes = (uint64_t)Wt * 128;
     const uint64_t pitch = kbytes + 128;
+    enc3 = form;
+    uint8_t *ops = E;
+    if (enc3) {
+        if (!E3) {
+            e3_bytes = e_bytes;
+            if ((e = dev_alloc_pooled((void **)&E3, e3_bytes, device)) != cudaSuccess)
+                return cuda_status(e, "encoded e4m3 operand allocation");
+            if ((e = launch_gate()) != cudaSuccess ||
+                (e = launch_expand_e4m3(X, S, S_pad, W0, Wt, rows, (int64_t)pitch, E3, 0x68, stream)) != cudaSuccess)
+                return cuda_status(e, "encoded e4m3 operand");
+            note_launches(1);
+        }
+        ops = E3;
+    }
+    const int NP = triples_pairs_per_tile(enc3);
     size_t cap = (size_t)16 << 30;
     if (const char *mb = getenv("FC_TRIPLES_SLAB_MB")) {
         const long v = atol(mb);
@@ -836,12 +883,14 @@ int Dataset::prepare_triples()
     }
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 4);
-    // At least the rows of one first SNP (the largest, i = 0), whatever the cap.
-    const int64_t cap_rows = std::max<int64_t>((int64_t)(cap / pitch), (S32 / 32) * 128);
-    const std::shared_ptr<const TriplePlan> plan = plan_triples(S, cap_rows);
+    const int64_t nJ = (S + NP - 1) / NP;
+    const int64_t cap_rows = std::max<int64_t>((int64_t)(cap / pitch), nJ * 4 * NP);
+    const std::shared_ptr<const TriplePlan> plan = plan_triples(S, NP, cap_rows);
     const std::vector<uint4> &tiles = plan->tiles;
     slabs3 = plan->slabs;
     first_tile3 = plan->first_tile;
+    ntiles3 = (int64_t)tiles.size();
+    if (ntiles3 >= ((int64_t)1 << 31)) return set_error(FC_ERANGE, "order-3 tile plan too large");
     p3_bytes = (size_t)plan->max_rows * pitch;
     if ((e = dev_alloc_pooled((void **)&P3, p3_bytes, device)) != cudaSuccess)
         return cuda_status(e, "pair-row slab allocation");
@@ -853,11 +902,28 @@ int Dataset::prepare_triples()
         return cuda_status(e, "slab row table allocation");
     cudaMemcpyAsync(tiles3, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(rowbase3, plan->rowbase.data(), sizeof(int64_t) * (size_t)S, cudaMemcpyHostToDevice, stream);
-    if ((rc = encode_tmap_u8(&tmap3, P3, kbytes, pitch, (uint64_t)plan->max_rows)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&tmap3A, ops, kbytes, pitch, (uint64_t)rows, 128, true)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&tmap3P, P3, kbytes, pitch, (uint64_t)plan->max_rows, (uint32_t)(4 * NP), true)) != FC_OK)
+        return rc;
     built_slab3 = -1;
     if ((rc = build_slab3(0)) != FC_OK) return rc;
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "pair-row slab");
     triples_ready = true;
+    return FC_OK;
+}
+
+int Dataset::build_slab3(int s)
+{
+    if (built_slab3 == s || s >= (int)slabs3.size()) return FC_OK;
+    const TripleSlab &sl = slabs3[(size_t)s];
+    const int64_t pitch = (int64_t)Wt * 128 + 128;
+    cudaError_t e;
+    if ((e = launch_gate()) != cudaSuccess ||
+        (e = launch_pair_rows(enc3 ? E3 : E, pitch, Wt, S, triples_pairs_per_tile(enc3), sl.i0, sl.i1, rowbase3 + sl.i0,
+                              P3, stream)) != cudaSuccess)
+        return cuda_status(e, "pair-row kernel");
+    note_launches(1);
+    built_slab3 = s;
     return FC_OK;
 }
 
@@ -872,6 +938,7 @@ void Dataset::release_pairs()
     ntiles = 0;
     tiles_host.clear();
     pairs_ready = false;
+    triples_ready = false;   // its TMA descriptors point into E
 }
 
 void Dataset::release_triples()
@@ -880,27 +947,16 @@ void Dataset::release_triples()
     dev_free_pooled(P3, p3_bytes, device);
     dev_free_pooled(tiles3, tiles3_bytes, device);
     dev_free_pooled(rowbase3, rowbase3_bytes, device);
+    dev_free_pooled(E3, e3_bytes, device);
     P3 = nullptr;
     tiles3 = nullptr;
     rowbase3 = nullptr;
+    E3 = nullptr;
+    ntiles3 = 0;
     slabs3.clear();
+    first_tile3.clear();
     built_slab3 = -1;
     triples_ready = false;
-}
-
-int Dataset::build_slab3(int s)
-{
-    if (built_slab3 == s || s >= (int)slabs3.size()) return FC_OK;
-    const TripleSlab &sl = slabs3[(size_t)s];
-    const int64_t S32 = (S + 31) / 32 * 32;
-    const int64_t pitch = (int64_t)Wt * 128 + 128;
-    cudaError_t e;
-    if ((e = launch_gate()) != cudaSuccess ||
-        (e = launch_pair_rows(E, pitch, Wt, S, S32, sl.i0, sl.i1, rowbase3 + sl.i0, P3, stream)) != cudaSuccess)
-        return cuda_status(e, "pair-row kernel");
-    note_launches(1);
-    built_slab3 = s;
-    return FC_OK;
 }
 
 int Dataset::triples_dense(float *scores, uint32_t *tables)
@@ -928,16 +984,16 @@ int Dataset::triples_dense(float *scores, uint32_t *tables)
     cudaMemsetAsync(err, 0, sizeof(uint32_t), stream);
     if (ns) cudaMemsetAsync(ta.dump_scores, 0, ns, stream);
     if (nt) cudaMemsetAsync(ta.dump_tables, 0, nt, stream);
-    for (int s = 0; s < (int)slabs3.size(); ++s) {
-        if ((rc = build_slab3(s)) != FC_OK) return rc;
-        const TripleSlab &sl = slabs3[(size_t)s];
+    for (int si = 0; si < (int)slabs3.size(); ++si) {
+        if ((rc = build_slab3(si)) != FC_OK) return rc;
+        const TripleSlab &sl = slabs3[(size_t)si];
         TriplesArgs a = ta;
         a.tiles = tiles3 + sl.t0;
         a.ntiles = (int)(sl.t1 - sl.t0);
         if (a.ntiles == 0) continue;
         cudaMemsetAsync(a.tile_counter, 0, sizeof(int), stream);
-        const int grid = std::min<int64_t>(sms, a.ntiles);
-        if ((e = launch_gate()) != cudaSuccess || (e = launch_triples_tc(MODE_DUMP, tmap, tmap3, a, grid, stream)) != cudaSuccess)
+        const int grid = (int)std::min<int64_t>(sms, a.ntiles);
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_triples_tc(MODE_DUMP, tmap3A, tmap3P, a, grid, stream)) != cudaSuccess)
             return cuda_status(e, "tensor-core triples kernel");
         note_launches(1);
     }
@@ -997,7 +1053,7 @@ bool Dataset::tuples_tc_eligible(int k, int L)
     if (k < 4 || k > 6) return false;
     const char *mode = getenv("FC_QUADS_PATH");
     if (mode && strcmp(mode, "popc") == 0) return false;
-    if (!allow_slabs) return false;
+    if (!allow_tc) return false;
     const bool forced = mode && strcmp(mode, "tc") == 0;
     const int64_t Smin = k == 4 ? 64 : k == 5 ? 48 : 32;
     if (!forced && S < Smin) return false;
@@ -1180,8 +1236,8 @@ int Dataset::prepare_tuples(int k)
         return cuda_status(e, "tuple-row kernel");
     note_launches(2);
     int rc;
-    if ((rc = encode_tmap_u8(&u.tmapL, u.QL, kbytes, pitch, (uint64_t)bl * 128)) != FC_OK) return rc;
-    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br * 128)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&u.tmapL, u.QL, kbytes, pitch, (uint64_t)bl * 128, 128, true)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br * 128, 128, true)) != FC_OK) return rc;
     // Host vectors go out of scope: the copies must have landed.
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tuple operands");
     u.lt_host = std::move(lt);
@@ -1451,8 +1507,10 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                 a.list_score = (float *)p[0] + x * sms * L;
                 a.list_rank = (uint64_t *)p[1] + x * sms * L;
                 cudaMemsetAsync(ta.tile_counter, 0, sizeof(int), stream);
+                // A launch with fewer tiles than SMs still writes sms lists:
+                // the CTAs without a tile write empty ones.
                 if ((e = launch_gate()) != cudaSuccess ||
-                    (e = launch_triples_tc(MODE_TOPN, tmap, tmap3, a, sms, stream)) != cudaSuccess)
+                    (e = launch_triples_tc(MODE_TOPN, tmap3A, tmap3P, a, sms, stream)) != cudaSuccess)
                     return cuda_status(e, "tensor-core triples kernel");
                 if (x > 0) note_launches(1);
             }
@@ -1506,6 +1564,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         last_list = L;
         last_grid = grid;
         if (herr & ERR_TIMEOUT) return set_error(FC_ETIMEOUT, "a bounded device wait ran out in the sweep");
+        // Several slabs are rebuilt by every search anyway: do not keep them.
+        if (tc3 && slabs3.size() > 1) release_triples();
         if (herr & ERR_LIST_SHORT) {
             L *= 4;
             if (L > FC_MAX_LIST)
@@ -1513,8 +1573,6 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                                  FC_MAX_LIST);
             continue;
         }
-        // Several slabs are rebuilt by every search anyway: do not keep them.
-        if (tc3 && slabs3.size() > 1) release_triples();
         *out_count = N;
         return FC_OK;
     }
@@ -1906,6 +1964,15 @@ int fc_tuples_dense(fc_handle *h, int k, float *scores, uint32_t *tables)
             return set_error(FC_ERANGE, "too many samples for the tensor-core path");
         DeviceGuard g(h->ds.device);
         return h->ds.tuples_dense(k, scores, tables);
+    });
+}
+
+int fc_triples_form(const fc_handle *h)
+{
+    return guarded([&]() -> int {
+        if (!h) return set_error(FC_EINVAL, "NULL handle");
+        DeviceGuard g(h->ds.device);
+        return h->ds.triples_form(2048);
     });
 }
 

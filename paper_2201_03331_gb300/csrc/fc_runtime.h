@@ -79,11 +79,13 @@ struct Dataset {
     bool pairs_ready = false;
 
     // Order-3 tensor-core operands, built on first use: slabs of pair rows
-    // (E[2i + a] AND E[2j + b], four rows per pair (i, j) with j in
-    // [32 floor((i + 1) / 32), S32)) for consecutive ranges of first SNPs i,
-    // the tiles of every slab, each i's first row within its slab, and the
-    // slab buffer's TMA descriptor.  One slab is built once and kept; with
-    // several, each search rebuilds them in turn in the same buffer.
+    // (E[2i + a] AND E[2j + b], four rows per pair (i, j), in blocks of NP
+    // pairs from the block of i + 1) for consecutive ranges of first SNPs i,
+    // the tiles of every slab, each i's first row within its slab, the x ln x
+    // table, for the one-accumulator form a copy of E whose control samples
+    // carry 64, and the kernel's two TMA descriptors (SNP rows, slab).  One
+    // slab is built once and kept; with several, each search rebuilds them
+    // in turn in the same buffer.
     struct TripleSlab {
         int64_t i0 = 0, i1 = 0;   // first SNPs [i0, i1)
         int64_t t0 = 0, t1 = 0;   // tiles [t0, t1) of tiles3
@@ -91,21 +93,25 @@ struct Dataset {
     };
     std::vector<TripleSlab> slabs3;
     std::vector<int64_t> first_tile3;   // [S + 1] first tile of each first SNP
+    float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)
     uint8_t *P3 = nullptr;
     size_t p3_bytes = 0;
-    float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)
     uint4 *tiles3 = nullptr;
     size_t tiles3_bytes = 0;
+    int64_t ntiles3 = 0;
     int64_t *rowbase3 = nullptr;
     size_t rowbase3_bytes = 0;
-    CUtensorMap tmap3{};
     int built_slab3 = -1;
+    int enc3 = 0;             // form of the order-3 kernel (triples_form)
+    uint8_t *E3 = nullptr;    // E with controls = 64 (form 1 only)
+    size_t e3_bytes = 0;
+    CUtensorMap tmap3A{}, tmap3P{};
     bool triples_ready = false;
     bool last_path_tc3 = false;
     // False for the jobs of a batch handle: only the batched search lifts it,
-    // for the order-3 jobs it sends to the tensor cores, and releases their
-    // slabs after each one.
-    bool allow_slabs = true;
+    // for the order-3 jobs it sends to the tensor cores (the batch's other
+    // orders stay on its persistent sweep).
+    bool allow_tc = true;
 
     // Tensor-core operands of orders 4-6, built on first use; one order's are
     // kept at a time: left and right tuple-row slabs (all 3^T genotype rows,
@@ -169,6 +175,8 @@ struct Dataset {
     int prepare_pairs();
     int pairs_dense(float *scores, uint32_t *tables);
     bool triples_tc_eligible(int L);
+    int triples_form(int L) const;
+    static int triples_list_size(int L);
     int prepare_triples();
     int build_slab3(int s);
     void release_triples();

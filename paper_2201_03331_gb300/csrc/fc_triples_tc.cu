@@ -6,15 +6,40 @@
 //     n_c(a, b, g) = sum_{m in c} [G_i(m) = a] [G_j(m) = b] [G_l(m) = g]
 //                  = < P_c[(i, j), (a, b)], E_c[l, g] >,
 // the dot product over the samples of a pair row P = E[i, a] AND E[j, b]
-// with a SNP row E[l, g] (0/1 e4m3 bytes).  For one block of 64 SNPs l and
-// one block of 32 pairs (i, j) with a fixed i these 128 x 128 dot products
-// are one tcgen05.mma kind::f8f6f4 tile per class: exact, since products of
-// 0/1 are 0/1 and FP32 sums of integers below 2^24 are exact.  The other 19
-// cells of the 3 x 3 x 3 table follow exactly by inclusion-exclusion from
-// the restricted pair table and the per-SNP genotype counts (the three rows
-// of a SNP's table partition the samples), as in the order-3 sweep.  The
-// epilogue scores every combination with the same FP32 mutual information
-// as the sweep and keeps a CTA top list; no count is written to memory.
+// with a SNP row E[l, g] (e4m3 bytes).  For one block of 64 SNPs l and one
+// block of NP pairs (i, j) with a fixed i these dot products are one
+// tcgen05.mma kind::f8f6f4 tile (M = 128 SNP rows, N = 4 NP pair rows).
+// Products of e4m3 powers of two are exact, and the tensor cores' FP32
+// accumulation of integers below 2^24 is exact (measured on GB300 up to
+// 2^24, with addends of 1 and of 4096).  The other 19 cells of the
+// 3 x 3 x 3 table follow exactly by inclusion-exclusion from the restricted
+// pair table and the per-SNP genotype counts (the three rows of a SNP's
+// table partition the samples), as in the order-3 sweep.  The epilogue
+// scores every combination with the same FP32 mutual information as the
+// sweep and keeps a CTA top list; no count is written to memory.
+//
+// Two encodings of the classes (template ENC):
+//   ENC = 1: control samples carry the e4m3 value 64 instead of 1, so one
+//            accumulator holds n_case + 4096 n_ctrl (exact while both
+//            classes have at most 4095 samples); NP = 64 pairs per tile,
+//            N = 256, one MMA chain over all samples;
+//   ENC = 0: both classes carry 1, and the case and control samples
+//            accumulate into two accumulators (N = 128 each); NP = 32.
+// Either way a tile takes 256 TMEM columns, and two tiles are in flight.
+//
+// The pair rows live in a slab in device memory, the paper's `combine` of
+// two genotype tables done once per data set (k_pair_rows): for each first
+// SNP i, the rows of its pairs (i, j) with j in [NP floor((i + 1) / NP), S_NP)
+// in blocks of NP pairs, pair row (a, q, b) of a block at row
+// 2 NP a + 2 q + b, zero where j <= i or j >= S.  Forming them on chip
+// instead (TMA of the rows of the SNPs j, AND with the rows of SNP i in
+// shared memory) was measured slower: the 48 KiB of shared-memory traffic
+// per 128-sample chunk of the builder cost more than the slab's one-time
+// write.
+//
+// TMA loads issued by one thread complete about one stage at a time, so the
+// three load stages are owned by three producer warps that each issue the
+// copies of their own stage (fill f by warp f mod 3).
 //
 // The epilogue scores with a table of x ln x instead of ln x: per cell
 // t = (xl[n] - xl[a]) - xl[b] = a ln(n/a) + b ln(n/b), MI = H(Y) - sum t / N.
@@ -26,19 +51,13 @@
 // u (2 ln M + 60 ln 2) for every M < 2^29, so the same FP64 rescoring window
 // applies.
 //
-// The pair rows live in a slab in device memory, built by k_pair_rows for a
-// range of first SNPs i: for each i the rows of the pairs (i, j) with j in
-// [32 floor((i + 1) / 32), S32), four rows (a, b) per pair, zero where
-// j <= i or j >= S.
-//
-// Roles (one persistent CTA per SM, 64 + 32 T3_EPI_WARPS threads):
-//   warp 0 : TMA producer (128-byte K chunks of the SNP rows and pair rows)
-//   warp 1 : TMEM allocation and the single-thread MMA issue
-//   warps 2.. : epilogue (TMEM -> registers -> 27-cell table -> MI -> list);
-//               T3_EPI_WARPS / 4 warps per TMEM lane quarter, each taking
-//               every (T3_EPI_WARPS / 4)-th 16-column chunk, so that several
-//               warps per scheduler hide the epilogue's latencies
-// Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
+// Roles (one persistent CTA per SM, 512 threads):
+//   warps 0-2  : producers (lane 0 issues the TMA copies of its stage)
+//   warp 3     : lane 0 issues the MMAs, lane 1 schedules tiles; the warp
+//                allocates and frees TMEM
+//   warps 4-15 : epilogue (TMEM -> registers -> 27-cell table -> MI ->
+//                list), three warps per TMEM lane quarter, each taking every
+//                third group of 4 pairs
 #include "fc_tc.cuh"
 #include "fc_ie.cuh"
 
@@ -46,43 +65,36 @@ namespace fc {
 
 namespace {
 
-// Pair rows of one slab.  Thread (i - i0, t): t runs over the pairs (i, j),
-// j in [j_lo, S32), times the 16-byte chunks of a row.
-__global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int64_t S32, int64_t i0,
-                            const int64_t *rowbase, uint8_t *P)
-{
-    const int64_t ii = blockIdx.y;
-    const int64_t i = i0 + ii;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t jlo = 32 * ((i + 1) / 32);
-    const int cw = 8 * Wt;                         // 16-byte chunks per row
-    if (t >= (S32 - jlo) * cw) return;
-    const int64_t jo = t / cw;
-    const int ch = (int)(t - jo * cw);
-    const int64_t j = jlo + jo;
-    const uint4 *ei0 = reinterpret_cast<const uint4 *>(E + (2 * i) * pitch) + ch;
-    const uint4 *ei1 = reinterpret_cast<const uint4 *>(E + (2 * i + 1) * pitch) + ch;
-    const uint4 a0 = *ei0, a1 = *ei1;
-    uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
-    if (j > i && j < S) {
-        b0 = *(reinterpret_cast<const uint4 *>(E + (2 * j) * pitch) + ch);
-        b1 = *(reinterpret_cast<const uint4 *>(E + (2 * j + 1) * pitch) + ch);
-    }
-    const int64_t row = rowbase[ii] + jo * 4;
-    auto put = [&](int ab, const uint4 &x, const uint4 &y) {
-        *(reinterpret_cast<uint4 *>(P + (row + ab) * pitch) + ch) =
-            make_uint4(x.x & y.x, x.y & y.y, x.z & y.z, x.w & y.w);
-    };
-    put(0, a0, b0);
-    put(1, a0, b1);
-    put(2, a1, b0);
-    put(3, a1, b1);
-}
-
-constexpr int T3_EPI_WARPS = 8;
-constexpr int T3_EPI_PER_Q = T3_EPI_WARPS / 4;     // epilogue warps per TMEM lane quarter
+constexpr int T3_LOADERS = 3;                      // = load stages
+constexpr int T3_EPI_WARP0 = 4;
+constexpr int T3_EPI_WARPS = 12;
+constexpr int T3_PARTS = T3_EPI_WARPS / 4;         // epilogue warps per TMEM lane quarter
 constexpr int T3_EPI_THREADS = 32 * T3_EPI_WARPS;
-constexpr int T3_THREADS = 64 + T3_EPI_THREADS;
+constexpr int T3_THREADS = 32 * T3_EPI_WARP0 + T3_EPI_THREADS;
+constexpr int T3_SJ_WORDS = 16;                    // per pair: T01[9], Tj[3], rank base (2 words), valid, pad
+static_assert(T3_EPI_WARP0 % 4 == 0, "epilogue warp w reads TMEM lane quarter w % 4");
+
+template <int ENC>
+struct T3Shape {
+    static constexpr int NP = ENC ? 64 : 32;              // SNPs j (pairs) per tile
+    static constexpr int RROWS = 2 * NP;                   // raw rows 2 j + b
+    static constexpr int NMMA = 2 * RROWS;                 // pair rows = MMA N
+    static constexpr uint32_t B_BYTES = (uint32_t)NMMA * TC_BK;
+    static constexpr uint32_t STAGE = TC_A_BYTES + B_BYTES;   // A | B
+    static constexpr int QUADS = NP / 4;                   // groups of 4 pairs per tile
+    static constexpr int ROUNDS = (QUADS + T3_PARTS - 1) / T3_PARTS;
+};
+
+__device__ __forceinline__ uint64_t c3(uint64_t n) { return n * (n - 1) * (n - 2) / 6; }   // 0 for n < 3
+__device__ __forceinline__ uint64_t c2(uint64_t n) { return n * (n - 1) / 2; }             // 0 for n < 2
+
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
 
 // Two exact FP32 accumulators (integers below 2^16) packed as lo | hi << 16:
 // x + 2^23 has the integer in its low mantissa bits, and the exponent
@@ -94,15 +106,42 @@ __device__ __forceinline__ uint32_t pack_exact(uint32_t lo_bits, uint32_t hi_bit
     return a + (b << 16) - 0x4B000000u;
 }
 
-__device__ __forceinline__ uint64_t c3(uint64_t n) { return n * (n - 1) * (n - 2) / 6; }   // 0 for n < 3
-__device__ __forceinline__ uint64_t c2(uint64_t n) { return n * (n - 1) / 2; }             // 0 for n < 2
-
-template <int MODE>
-__global__ void __launch_bounds__(T3_THREADS, 1)
-    k_triples_tc(const __grid_constant__ CUtensorMap tmapE, const __grid_constant__ CUtensorMap tmapP, TriplesArgs a)
+// One encoded accumulator x = n_case + 4096 n_ctrl (exact, x < 2^24) as
+// n_case | n_ctrl << 16: n_ctrl = floor(x / 4096) and n_case = x - 4096 n_ctrl
+// are exact in FP32 and below 2^12.
+__device__ __forceinline__ uint32_t unpack_enc(uint32_t bits)
 {
+    const float x = __uint_as_float(bits);
+    const float hi = floorf(x * (1.0f / 4096.0f));
+    const float lo = fmaf(hi, -4096.0f, x);
+    return pack_exact(__float_as_uint(lo), __float_as_uint(hi));
+}
+
+// One barrier of the NT epilogue threads that also tells every thread
+// whether any thread passed a true predicate.
+template <int NT>
+__device__ __forceinline__ bool epi_bar_or(bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, p;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(NT)
+        : "memory");
+    return r != 0;
+}
+
+template <int MODE, int ENC>
+__global__ void __launch_bounds__(T3_THREADS, 1)
+    k_triples_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapP, TriplesArgs a)
+{
+    using Sh = T3Shape<ENC>;
+    constexpr int NP = Sh::NP;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_full[TC_MAX_STAGES], bar_empty[TC_MAX_STAGES];
+    __shared__ uint64_t bar_full[T3_LOADERS], bar_empty[T3_LOADERS];
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_done;
     __shared__ uint32_t tmem_base_slot;
     __shared__ uint64_t bar_sfull[TC_SCHED], bar_sempty[TC_SCHED];
@@ -113,19 +152,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int stages = a.stages;
     volatile int *abort_flag = &abort_flag_s;
 
+    // Stages [A 16 KiB | B], 1024-byte aligned; then the
+    // x ln x table, the list and the tables of the tile's SNPs j.
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *stA = smem;
-    uint8_t *stB = smem + (size_t)stages * TC_A_BYTES;
-    float *xltab = reinterpret_cast<float *>(stB + (size_t)stages * TC_B_BYTES);   // x ln x
+    float *xltab = reinterpret_cast<float *>(smem + (size_t)T3_LOADERS * Sh::STAGE);
     const int lt_floats = (a.M + 1 + 3) & ~3;
     uint64_t *lrank = reinterpret_cast<uint64_t *>(xltab + lt_floats);
     float *lscore = reinterpret_cast<float *>(lrank + a.P2);
+    uint32_t *sJ = reinterpret_cast<uint32_t *>(lscore + a.P2);   // [2][NP][T3_SJ_WORDS]
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) {
+        for (int s = 0; s < T3_LOADERS; ++s) {
             mbar_init(&bar_full[s], 1);
             mbar_init(&bar_empty[s], 1);
         }
@@ -136,20 +175,21 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         mbar_init(&bar_done, 1);
         for (int s = 0; s < TC_SCHED; ++s) {
             mbar_init(&bar_sfull[s], 1);
-            mbar_init(&bar_sempty[s], 1 + T3_EPI_WARPS);   // the MMA thread and the epilogue warps
+            // The producer warps, the MMA thread and the epilogue warps.
+            mbar_init(&bar_sempty[s], T3_LOADERS + 1 + T3_EPI_WARPS);
         }
         abort_flag_s = 0;
         buf_count = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == 3) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_slot)),
                      "r"(TC_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = threadIdx.x; i <= a.M; i += blockDim.x) xltab[i] = a.xlogx[i];
+    for (int i = threadIdx.x; i < lt_floats; i += blockDim.x) xltab[i] = i <= a.M ? a.xlogx[i] : 0.f;
     if (MODE == MODE_TOPN) {
         for (int i = threadIdx.x; i < a.P2; i += blockDim.x) {
             lscore[i] = -FLT_MAX;
@@ -160,81 +200,83 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = tmem_base_slot;
+    const long long wt = a.wait_ticks;
 
-    const int kc0 = a.W0, kc1 = a.Wt - a.W0;   // 128-sample chunks per class
-
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
-        if (lane == 0) {
-            uint32_t fill = 0;
-            bool ok = true;
-            for (int it = 0; ok; ++it) {
-                const int slot = it % TC_SCHED;
-                const uint32_t sn = (uint32_t)(it / TC_SCHED);
-                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err)) break;
-                int t = atomicAdd(a.tile_counter, 1);
-                if (t >= a.ntiles) t = -1;
-                sched_tile[slot] = t;
-                mbar_arrive(&bar_sfull[slot]);
-                if (t < 0) break;
-                const uint4 tile = a.tiles[t];
-                const int rowP = (int)tile.x, Lb = (int)tile.w;
-                for (int c = 0; c < 2 && ok; ++c) {
-                    const int nk = c ? kc1 : kc0;
-                    const int xbase = c ? kc0 * TC_BK : 0;
-                    for (int kc = 0; kc < nk; ++kc, ++fill) {
-                        const int s = fill % stages;
-                        const uint32_t n = fill / stages;
-                        if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
-                        mbar_expect_tx(&bar_full[s], TC_A_BYTES + TC_B_BYTES);
-                        tma_load_2d(&tmapE, &bar_full[s], stA + (size_t)s * TC_A_BYTES, xbase + kc * TC_BK, Lb * TC_BM);
-                        tma_load_2d(&tmapP, &bar_full[s], stB + (size_t)s * TC_B_BYTES, xbase + kc * TC_BK, rowP);
-                    }
-                }
+    if (warp < T3_LOADERS) {
+        // ---------------- producers ----------------
+        // Warp w owns stage w and the fills f = w (mod 3); lane 0 issues.
+        const int w = warp;
+        uint8_t *st = smem + (size_t)w * Sh::STAGE;
+        uint32_t fill = 0;
+        uint32_t issued = 0, last_n = 0;
+        bool ok = true;
+        for (int it = 0; ok; ++it) {
+            const int slot = it % TC_SCHED;
+            const uint32_t sn = (uint32_t)(it / TC_SCHED);
+            if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt)) break;
+            const int t = sched_tile[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_sempty[slot]);
+            if (t < 0) break;
+            if (lane != 0) {
+                fill += (uint32_t)a.Wt;
+                continue;
             }
-            // Let every copy issued so far land before the CTA can exit.
-            const uint32_t issued = fill;
-            for (uint32_t f = (issued > (uint32_t)stages ? issued - stages : 0); f < issued; ++f) {
-                const int s = f % stages;
-                const uint32_t n = f / stages;
-                long long t0 = clock64();
-                while (!mbar_try(&bar_full[s], n & 1) && clock64() - t0 < WAIT_BUDGET) {}
+            const uint4 tile = a.tiles[t];
+            const int rowP = (int)tile.x, Lb = (int)tile.w;
+            for (int kc = 0; kc < a.Wt; ++kc, ++fill) {
+                if ((int)(fill % T3_LOADERS) != w) continue;
+                const uint32_t n = fill / T3_LOADERS;
+                if (!mbar_wait(&bar_empty[w], (n & 1) ^ 1, abort_flag, a.err, wt)) { ok = false; break; }
+                const int x = kc * TC_BK;
+                mbar_expect_tx(&bar_full[w], Sh::STAGE);
+                tma_load_2d(&tmapA, &bar_full[w], st, x, Lb * TC_BM);
+                tma_load_2d(&tmapP, &bar_full[w], st + TC_A_BYTES, x, rowP);
+                ++issued;
+                last_n = n;
             }
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issue ----------------
+        // Let the copies of this stage land before the CTA can exit (one
+        // stage: every earlier fill of it was consumed before this one).
+        if (lane == 0 && issued > 0) {
+            long long t0 = clock64();
+            while (!mbar_try(&bar_full[w], last_n & 1) && clock64() - t0 < WAIT_BUDGET) {}
+        }
+    } else if (warp == 3) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_e4m3_f32(TC_BM, TC_BN);
+            // ---------------- MMA issue ----------------
+            const uint32_t idesc = idesc_e4m3_f32(TC_BM, Sh::NMMA);
             uint32_t fill = 0;
             bool ok = true;
             for (int it = 0; ok; ++it) {
                 const int slot = it % TC_SCHED;
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
-                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt)) break;
                 const int t = sched_tile[slot];
                 mbar_arrive(&bar_sempty[slot]);
                 if (t < 0) break;
                 const int b = it & 1;
                 const uint32_t u = (uint32_t)(it >> 1);
-                if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err)) break;
+                if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err, wt)) break;
                 tc_fence_after();
-                for (int c = 0; c < 2 && ok; ++c) {
-                    const int nk = c ? kc1 : kc0;
-                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + c * 128);
-                    for (int kc = 0; kc < nk; ++kc, ++fill) {
-                        const int s = fill % stages;
-                        const uint32_t n = fill / stages;
-                        if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t aaddr = smem_u32(stA + (size_t)s * TC_A_BYTES);
-                        const uint32_t baddr = smem_u32(stB + (size_t)s * TC_B_BYTES);
-#pragma unroll
-                        for (int kk = 0; kk < TC_BK / 32; ++kk) {
-                            mma_e4m3(d, smem_desc_sw128(aaddr + kk * 32), smem_desc_sw128(baddr + kk * 32), idesc,
-                                     (kc > 0 || kk > 0) ? 1u : 0u);
-                        }
-                        mma_commit(&bar_empty[s]);
+                for (int kc = 0; kc < a.Wt; ++kc, ++fill) {
+                    const int s = (int)(fill % T3_LOADERS);
+                    const uint32_t n = fill / T3_LOADERS;
+                    if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err, wt)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const bool cls1 = !ENC && kc >= a.W0;
+                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + (cls1 ? 128 : 0));
+                    const bool first = ENC ? kc == 0 : (kc == 0 || kc == a.W0);
+                    const uint32_t aaddr = smem_u32(smem + (size_t)s * Sh::STAGE);
+                    const uint32_t baddr = aaddr + TC_A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 32; ++kk)
+                        mma_e4m3(d, smem_desc_sw128(aaddr + kk * 32), smem_desc_sw128(baddr + kk * 32), idesc,
+                                 (!first || kk > 0) ? 1u : 0u);
+                    mma_commit(&bar_empty[s]);
                 }
                 if (ok) mma_commit(&bar_tfull[b]);
             }
@@ -242,92 +284,167 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             mma_commit(&bar_done);
             long long t0 = clock64();
             while (!mbar_try(&bar_done, 0) && clock64() - t0 < WAIT_BUDGET) {}
+        } else if (lane == 1) {
+            // ---------------- tile scheduler ----------------
+            for (int it = 0;; ++it) {
+                const int slot = it % TC_SCHED;
+                const uint32_t sn = (uint32_t)(it / TC_SCHED);
+                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err, wt)) break;
+                int t = atomicAdd(a.tile_counter, 1);
+                if (t >= a.ntiles) t = -1;
+                sched_tile[slot] = t;
+                mbar_arrive(&bar_sfull[slot]);
+                if (t < 0) break;
+            }
         }
     } else {
         // ---------------- epilogue ----------------
-        // TMEM lane = tile row = SNP row 2 l_loc + g of the A block; column
-        // 4 q + (2a + b) = pair q of the B block, genotypes (a, b).  Warp w
-        // reads lane quarter w % 4 and the chunks of part (w - 2) / 4.
-        const int tid = threadIdx.x - 64;           // 0 .. T3_EPI_THREADS - 1
+        // TMEM lane = A row = 2 l_loc + g; column (within a class for ENC = 0)
+        // 2 NP a + 2 q + b = pair (i, NP J + q) with genotypes (a, b).  Warp w
+        // reads lane quarter w % 4 and the groups of 4 pairs part, part + 3, ..
+        const int tid = threadIdx.x - 32 * T3_EPI_WARP0;   // 0 .. T3_EPI_THREADS - 1
         const int quarter = warp & 3;
-        const int part = (warp - 2) >> 2;           // 0 .. T3_EPI_PER_Q - 1
+        const int part = (warp - T3_EPI_WARP0) >> 2;       // 0 .. T3_PARTS - 1
         const int row = quarter * 32 + lane;
         const int l_loc = row >> 1;
         const int g = row & 1;
         const int L = a.L;
-        const int Bcap = a.Bcap;
         const uint32_t lt = (uint32_t)a.M;
         const int64_t Sp = a.S_pad;
+        const bool whole = a.rank_begin == 0 && a.rank_end >= a.total;
+        // A round inserts at most 2 candidates per thread.  A merge is due
+        // when the buffer might not hold two more rounds: every thread reads
+        // the fill before the round's barrier, after its own insertions of
+        // the round before, so the fill at that barrier is at most the
+        // largest value read plus one round.
+        const int headroom = 2 * 2 * T3_EPI_THREADS;
         float thr_s = -FLT_MAX;
         uint64_t thr_r = NO_RANK;
         for (int it = 0;; ++it) {
             const int slot = it % TC_SCHED;
             const uint32_t sn = (uint32_t)(it / TC_SCHED);
-            const bool ok = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err);
-            const int t = ok ? sched_tile[slot] : -1;
-            if (ok) {
+            const bool okw = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt);
+            const int t = okw ? sched_tile[slot] : -1;
+            if (okw) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_sempty[slot]);
             }
             const int b = it & 1;
             const uint32_t u = (uint32_t)(it >> 1);
-            if (t >= 0) mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err);
+            // Tile data that does not depend on the accumulators, loaded while
+            // the tile's MMAs may still run.
+            int64_t l = 0;
+            int J = 0;
+            uint32_t Tl[3] = {0, 0, 0}, T02[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            bool lv = false;
+            uint32_t *sJb = sJ + (size_t)b * NP * T3_SJ_WORDS;
+            if (t >= 0) {
+                const uint4 tile = a.tiles[t];
+                const int64_t i = tile.y;
+                J = (int)tile.z;
+                l = (int64_t)tile.w * 64 + l_loc;
+                lv = l < a.S;
+                const int64_t lc = lv ? l : a.S - 1;
+                uint32_t Ti[3];
+                unpack_marg(a.marg4[i], Ti);
+                unpack_marg(a.marg4[lc], Tl);
+                const uint4 p4 = a.PR[(size_t)i * Sp + lc];
+                const uint32_t R[4] = {p4.x, p4.y, p4.z, p4.w};
+                full2(R, Ti, Tl, T02);
+                // The tables of the tile's SNPs j, one thread per j.
+                if (tid < NP) {
+                    const int64_t j = (int64_t)J * NP + tid;
+                    const int64_t jc = j < a.S ? j : a.S - 1;
+                    uint32_t Tj[3], T01[9];
+                    unpack_marg(a.marg4[jc], Tj);
+                    const uint4 q4 = a.PR[(size_t)i * Sp + jc];
+                    const uint32_t Rq[4] = {q4.x, q4.y, q4.z, q4.w};
+                    full2(Rq, Ti, Tj, T01);
+                    // rank of (i, j, l) = base_i - C(S - j, 2) + l - j - 1
+                    const uint64_t base_i = a.total - c3((uint64_t)(a.S - i)) + c2((uint64_t)(a.S - i - 1));
+                    const uint64_t rb = base_i - c2((uint64_t)(a.S - jc)) - (uint64_t)jc - 1;
+                    uint4 *rec = reinterpret_cast<uint4 *>(sJb + (size_t)tid * T3_SJ_WORDS);
+                    rec[0] = make_uint4(T01[0], T01[1], T01[2], T01[3]);
+                    rec[1] = make_uint4(T01[4], T01[5], T01[6], T01[7]);
+                    rec[2] = make_uint4(T01[8], Tj[0], Tj[1], Tj[2]);
+                    rec[3] = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), (j > i && j < a.S) ? 1u : 0u, 0u);
+                }
+                mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err, wt);
+            }
             // One stop decision for all epilogue warps (they meet at named
-            // barriers, which have no timeout); t is the same for all.
+            // barriers, which have no timeout); t is the same for all.  The
+            // barrier also publishes the tables of the SNPs j.
             epi_bar_n<T3_EPI_THREADS>();
             if (tid == 0) epi_stop = *abort_flag;
             epi_bar_n<T3_EPI_THREADS>();
             if (epi_stop || t < 0) break;
             tc_fence_after();
-            const uint4 tile = a.tiles[t];
-            const int64_t i = tile.y;
-            const int J = (int)tile.z, Lb = (int)tile.w;
-            const int64_t l = (int64_t)Lb * 64 + l_loc;
-            // Tables that depend on i and l only: per-SNP counts and the
-            // full pair table of (i, l).
-            uint32_t Ti[3], Tl[3] = {0, 0, 0}, T02[9];
-            unpack_marg(a.marg4[i], Ti);
-            if (l < a.S) unpack_marg(a.marg4[l], Tl);
-            {
-                uint4 p = make_uint4(0, 0, 0, 0);
-                if (i < l && l < a.S) p = a.PR[(size_t)i * Sp + l];
-                const uint32_t R[4] = {p.x, p.y, p.z, p.w};
-                full2(R, Ti, Tl, T02);
-            }
-            const uint64_t base_i = a.total - c3((uint64_t)(a.S - i)) + c2((uint64_t)(a.S - i - 1));
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            // Chunks part, part + T3_EPI_PER_Q, ... of the eight 16-column
-            // chunks; the buffer is released after this warp's last read.
-            // Every warp runs the same number of rounds (a round without a
-            // chunk scores nothing), because each round of the top-N step
-            // meets at block barriers.
-            constexpr int ROUNDS = (8 + T3_EPI_PER_Q - 1) / T3_EPI_PER_Q;
-            for (int rnd = 0; rnd < ROUNDS; ++rnd) {
-                const int ch = part + rnd * T3_EPI_PER_Q;
-                const bool has = ch < 8;               // warp-uniform
-                // The chunk's lower-order tables, loaded before the TMEM
-                // reads so that their latency overlaps; indices are clamped
-                // into the tables (entries of invalid combinations are loaded
-                // but not used).
-                const int64_t lc = l < a.S ? l : a.S - 1;
-                uint4 mj[2], pij[2], pjl[2];
-                uint32_t v0[16], v1[16];
+            const int64_t lc = lv ? l : a.S - 1;
+            // Pair-table entries PR[j][l] of the first group, then one group ahead.
+            uint4 pjl[2], pjl_next[2];
 #pragma unroll
-                for (int x = 0; x < 16; ++x) { v0[x] = 0; v1[x] = 0; }
-                if (has) {
+            for (int m = 0; m < 2; ++m) {
+                const int64_t jj = min((int64_t)J * NP + part * 4 + 2 * m + g, a.S - 1);
+                pjl_next[m] = a.PR[(size_t)jj * Sp + lc];
+            }
+            // Every warp runs the same number of rounds (a round without a
+            // group scores nothing), because each round meets at a barrier.
+            for (int rnd = 0; rnd < Sh::ROUNDS; ++rnd) {
+                const int qd = part + rnd * T3_PARTS;            // group of pairs 4 qd .. 4 qd + 3
+                const bool has = qd < Sh::QUADS;                 // warp-uniform
+                pjl[0] = pjl_next[0];
+                pjl[1] = pjl_next[1];
+                if (qd + T3_PARTS < Sh::QUADS) {
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
-                        const int64_t jj = min((int64_t)J * 32 + ch * 4 + 2 * m + g, a.S - 1);
-                        mj[m] = a.marg4[jj];
-                        pij[m] = a.PR[(size_t)i * Sp + jj];
-                        pjl[m] = a.PR[(size_t)jj * Sp + lc];
+                        const int64_t jj = min((int64_t)J * NP + (qd + T3_PARTS) * 4 + 2 * m + g, a.S - 1);
+                        pjl_next[m] = a.PR[(size_t)jj * Sp + lc];
                     }
-                    tmem_ld16(taddr + ch * 16, v0);
-                    tmem_ld16(taddr + 128 + ch * 16, v1);
-                    tmem_wait_ld();
-                    tmem_regs_after_wait(v0);
-                    tmem_regs_after_wait(v1);
-                    if (ch + T3_EPI_PER_Q >= 8) {
+                }
+                // This lane's cells (genotype g of SNP l) for the group's 4
+                // pairs q: cell[4 q + 2 a + b], packed cases | controls << 16.
+                uint32_t cell[16];
+#pragma unroll
+                for (int x = 0; x < 16; ++x) cell[x] = 0;
+                if (has) {
+                    const uint32_t c0 = (uint32_t)(8 * qd);            // a = 0: columns 2 q + b
+                    const uint32_t c1 = (uint32_t)(2 * NP + 8 * qd);   // a = 1
+                    if (ENC) {
+                        uint32_t v0[8], v1[8];
+                        tmem_ld8(taddr + c0, v0);
+                        tmem_ld8(taddr + c1, v1);
+                        tmem_wait_ld();
+                        tmem_regs_after_wait(v0);
+                        tmem_regs_after_wait(v1);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int bb = 0; bb < 2; ++bb) {
+                                cell[4 * q + bb] = unpack_enc(v0[2 * q + bb]);
+                                cell[4 * q + 2 + bb] = unpack_enc(v1[2 * q + bb]);
+                            }
+                    } else {
+                        uint32_t v0[8], v1[8], w0[8], w1[8];
+                        tmem_ld8(taddr + c0, v0);
+                        tmem_ld8(taddr + 128 + c0, w0);
+                        tmem_ld8(taddr + c1, v1);
+                        tmem_ld8(taddr + 128 + c1, w1);
+                        tmem_wait_ld();
+                        tmem_regs_after_wait(v0);
+                        tmem_regs_after_wait(v1);
+                        tmem_regs_after_wait(w0);
+                        tmem_regs_after_wait(w1);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int bb = 0; bb < 2; ++bb) {
+                                cell[4 * q + bb] = pack_exact(v0[2 * q + bb], w0[2 * q + bb]);
+                                cell[4 * q + 2 + bb] = pack_exact(v1[2 * q + bb], w1[2 * q + bb]);
+                            }
+                    }
+                    if (qd + T3_PARTS >= Sh::QUADS) {
+                        // This warp's last read of the buffer.
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&bar_tempty[b]);
@@ -338,39 +455,39 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 bool val[2];
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
-                    // This thread scores pair 2m + g of the chunk; the partner
-                    // lane (genotype 1 - g of the same SNP l) scores 2m + 1 - g
-                    // and sends the packed cells this thread lacks.
+                    // This lane scores pair 2m + g of the group; its partner
+                    // lane (genotype 1 - g of the same SNP l) scores 2m + 1 - g.
+                    // Each sends the cells of the other's pair.
                     uint32_t Rr[8];
 #pragma unroll
                     for (int ab = 0; ab < 4; ++ab) {
-                        const uint32_t pA = pack_exact(v0[8 * m + ab], v1[8 * m + ab]);           // pair 2m
-                        const uint32_t pB = pack_exact(v0[8 * m + 4 + ab], v1[8 * m + 4 + ab]);   // pair 2m+1
-                        const uint32_t own = g ? pB : pA;
-                        const uint32_t pt = __shfl_xor_sync(FULL, g ? pA : pB, 1);
-                        Rr[2 * ab] = g ? pt : own;
-                        Rr[2 * ab + 1] = g ? own : pt;
+                        const uint32_t own = g ? cell[4 * (2 * m + 1) + ab] : cell[4 * (2 * m) + ab];
+                        const uint32_t other = g ? cell[4 * (2 * m) + ab] : cell[4 * (2 * m + 1) + ab];
+                        const uint32_t recv = __shfl_xor_sync(FULL, other, 1);
+                        Rr[2 * ab] = g ? recv : own;   // Rr[4 a + 2 b + genotype of l]
+                        Rr[2 * ab + 1] = g ? own : recv;
                     }
-                    const int q = ch * 4 + 2 * m + g;
-                    const int64_t j = (int64_t)J * 32 + q;
-                    // Lexicographic rank of (i, j, l).
-                    const uint64_t rank0 = base_i - c2((uint64_t)(a.S - j)) + (uint64_t)(l - j - 1);
-                    const bool valid = has && i < j && j < l && l < a.S && rank0 >= a.rank_begin &&
-                                       rank0 < a.rank_end;
+                    const int q = 4 * qd + 2 * m + g;    // pair within the tile
+                    const uint4 *rec = reinterpret_cast<const uint4 *>(sJb + (size_t)(has ? q : 0) * T3_SJ_WORDS);
+                    const uint4 r3 = rec[3];
+                    const int64_t j = (int64_t)J * NP + q;
+                    const uint64_t rank0 = (((uint64_t)r3.y << 32) | r3.x) + (uint64_t)l;
+                    const bool valid = has && r3.z != 0 && lv && j < l &&
+                                       (whole || (rank0 >= a.rank_begin && rank0 < a.rank_end));
                     uint32_t T[27];
                     float hsum = 0.f;
                     if (valid) {
-                        uint32_t Tj[3], T01[9], T12[9];
-                        unpack_marg(mj[m], Tj);
-                        const uint32_t R01[4] = {pij[m].x, pij[m].y, pij[m].z, pij[m].w};
+                        const uint4 r0 = rec[0], r1 = rec[1], r2 = rec[2];
+                        const uint32_t T01[9] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w, r2.x};
+                        const uint32_t Tj[3] = {r2.y, r2.z, r2.w};
+                        uint32_t T12[9];
                         const uint32_t R12[4] = {pjl[m].x, pjl[m].y, pjl[m].z, pjl[m].w};
-                        full2(R01, Ti, Tj, T01);
                         full2(R12, Tj, Tl, T12);
                         full3(Rr, T01, T02, T12, T);
 #pragma unroll
                         for (int x = 0; x < 27; ++x) {
                             // Clamped so that no index can leave the table
-                            // (a, b <= n for exact counts, so nothing changes).
+                            // (a, b <= n <= M for exact counts).
                             const uint32_t ca = T[x] & 0xffffu, cb = T[x] >> 16;
                             const uint32_t n = min(ca + cb, lt);
                             hsum += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
@@ -391,15 +508,12 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                 }
                 if (MODE == MODE_TOPN) {
-                    // Merge the buffer into the list when a full chunk (2 per
-                    // thread) might not fit.
-                    // Every thread reads the buffer fill before any thread of
-                    // this round adds to it, so that all take the same branch.
-                    epi_bar_n<T3_EPI_THREADS>();
-                    const int fill_now = buf_count;
-                    epi_bar_n<T3_EPI_THREADS>();
-                    if (fill_now > Bcap - 2 * T3_EPI_THREADS) {
-                        const int nb = buf_count;
+                    // One barrier with an OR reduction gives every thread the
+                    // same merge decision.
+                    const bool need = epi_bar_or<T3_EPI_THREADS>(buf_count > a.Bcap - headroom);
+                    if (need) {
+                        epi_bar_n<T3_EPI_THREADS>();
+                        const int nb = min(buf_count, a.Bcap);
                         for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) {
                             lscore[x] = -FLT_MAX;
                             lrank[x] = NO_RANK;
@@ -422,7 +536,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         if (lane == 0 && mk) base = atomicAdd(&buf_count, __popc(mk));
                         base = __shfl_sync(FULL, base, 0);
                         if (cand) {
-                            const int s2 = L + base + __popc(mk & ((1u << lane) - 1u));
+                            // The headroom keeps the slot inside the buffer.
+                            const int s2 = min(L + base + __popc(mk & ((1u << lane) - 1u)), a.P2 - 1);
                             lscore[s2] = sc[m];
                             lrank[s2] = rk[m];
                         }
@@ -432,7 +547,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         }
         if (MODE == MODE_TOPN) {
             epi_bar_n<T3_EPI_THREADS>();
-            const int nb = buf_count;
+            const int nb = min(buf_count, a.Bcap);
             for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
             epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
             for (int x = tid; x < L; x += T3_EPI_THREADS) {
@@ -444,36 +559,90 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == 3) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
                      : "memory");
     }
 }
 
+template <int ENC>
+size_t smem_bytes_enc(int M, int P2)
+{
+    using Sh = T3Shape<ENC>;
+    return 1024 + (size_t)T3_LOADERS * Sh::STAGE + (size_t)((M + 1 + 3) & ~3) * 4 + (size_t)P2 * (8 + 4) +
+           (size_t)2 * Sh::NP * T3_SJ_WORDS * 4;
+}
+
+template <int MODE, int ENC>
+void *kernel_ptr()
+{
+    return reinterpret_cast<void *>(&k_triples_tc<MODE, ENC>);
+}
+
+// Pair rows of the first SNPs [i0, i1): thread (i - i0, t), t over the
+// pairs (i, j), j in [NP Jlo(i), S_NP), times the 16-byte chunks of a row;
+// the row of pair (a, j, b) is rowbase[i - i0] + (J - Jlo) 4 NP + 2 NP a + 2 q + b
+// (j = NP J + q).
+__global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int64_t S_np, int NP, int64_t i0,
+                            const int64_t *rowbase, uint8_t *P)
+{
+    const int64_t ii = blockIdx.y;
+    const int64_t i = i0 + ii;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t jlo = NP * ((i + 1) / NP);
+    const int cw = 8 * Wt;                         // 16-byte chunks per row
+    if (t >= (S_np - jlo) * cw) return;
+    const int64_t jo = t / cw;
+    const int ch = (int)(t - jo * cw);
+    const int64_t j = jlo + jo;
+    const uint4 a0 = *(reinterpret_cast<const uint4 *>(E + (2 * i) * pitch) + ch);
+    const uint4 a1 = *(reinterpret_cast<const uint4 *>(E + (2 * i + 1) * pitch) + ch);
+    uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
+    if (j > i && j < S) {
+        b0 = *(reinterpret_cast<const uint4 *>(E + (2 * j) * pitch) + ch);
+        b1 = *(reinterpret_cast<const uint4 *>(E + (2 * j + 1) * pitch) + ch);
+    }
+    const int64_t blk = jo / NP, q = jo % NP;
+    const int64_t row = rowbase[ii] + blk * 4 * NP + 2 * q;
+    auto put = [&](int a, int b, const uint4 &x, const uint4 &y) {
+        *(reinterpret_cast<uint4 *>(P + (row + 2 * NP * a + b) * pitch) + ch) =
+            make_uint4(x.x & y.x, x.y & y.y, x.z & y.z, x.w & y.w);
+    };
+    put(0, 0, a0, b0);
+    put(0, 1, a0, b1);
+    put(1, 0, a1, b0);
+    put(1, 1, a1, b1);
+}
+
 }  // namespace
 
-cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int64_t S32, int64_t i0, int64_t i1,
+int triples_pairs_per_tile(int enc) { return enc ? T3Shape<1>::NP : T3Shape<0>::NP; }
+
+size_t triples_smem_bytes(int enc, int M, int P2) { return enc ? smem_bytes_enc<1>(M, P2) : smem_bytes_enc<0>(M, P2); }
+
+cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int NP, int64_t i0, int64_t i1,
                              const int64_t *rowbase, uint8_t *P, cudaStream_t st)
 {
     if (i1 <= i0) return cudaSuccess;
-    const int64_t maxn = S32 * 8 * (int64_t)Wt;
+    const int64_t S_np = (S + NP - 1) / NP * NP;
+    const int64_t maxn = S_np * 8 * (int64_t)Wt;
     dim3 grid((unsigned)((maxn + 255) / 256), (unsigned)(i1 - i0));
-    k_pair_rows<<<grid, 256, 0, st>>>(E, pitch, Wt, S, S32, i0, rowbase, P);
+    k_pair_rows<<<grid, 256, 0, st>>>(E, pitch, Wt, S, S_np, NP, i0, rowbase, P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapE, const CUtensorMap &tmapP, const TriplesArgs &a,
+cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapA, const CUtensorMap &tmapP, const TriplesArgs &a,
                               int grid, cudaStream_t st)
 {
-    const size_t bytes = pairs_smem_bytes(a.stages, a.M, a.P2);
-    void *fn = mode == MODE_TOPN ? reinterpret_cast<void *>(&k_triples_tc<MODE_TOPN>)
-                                 : reinterpret_cast<void *>(&k_triples_tc<MODE_DUMP>);
+    const size_t bytes = triples_smem_bytes(a.enc, a.M, a.P2);
+    void *fn = mode == MODE_TOPN ? (a.enc ? kernel_ptr<MODE_TOPN, 1>() : kernel_ptr<MODE_TOPN, 0>())
+                                 : (a.enc ? kernel_ptr<MODE_DUMP, 1>() : kernel_ptr<MODE_DUMP, 0>());
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    CUtensorMap mE = tmapE, mP = tmapP;
+    CUtensorMap mA = tmapA, mP = tmapP;
     TriplesArgs args = a;
-    void *params[] = {&mE, &mP, &args};
+    void *params[] = {&mA, &mP, &args};
     return cudaLaunchKernel(fn, dim3(grid), dim3(T3_THREADS), params, bytes, st);
 }
 

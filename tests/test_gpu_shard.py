@@ -55,15 +55,17 @@ def test_range_list_is_exact_top_n_of_the_range(fc):
         fc.fc_search_range(h, 3, 30, 10, total + 1)
 
 
-@pytest.mark.parametrize("slab_mb", [None, "20"])
-def test_order3_tensor_core_ranges(fc, monkeypatch, slab_mb):
+@pytest.mark.parametrize("slab_mb,enc", [(None, None), ("20", None), (None, "0"), ("20", "0")])
+def test_order3_tensor_core_ranges(fc, monkeypatch, slab_mb, enc):
     """Rank ranges on the order-3 tensor-core path (one slab, and four slabs
-    of pair rows): each range list is the exact top-N of its combinations,
-    and the shards merge to the whole search."""
+    of pair rows; both forms of the kernel): each range list is the exact
+    top-N of its combinations, and the shards merge to the whole search."""
     from paper_2201_03331_gb300.shard import merge_shard_lists, search_shard
     monkeypatch.setenv("FC_TRIPLES_PATH", "tc")
     if slab_mb:
         monkeypatch.setenv("FC_TRIPLES_SLAB_MB", slab_mb)
+    if enc:
+        monkeypatch.setenv("FC_TRIPLES_ENC", enc)
     ds = make_dataset("rng3", seed=975, S=130, cases=600, controls=700, k=3, top_n=25, planted=(9, 64, 121))
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     full = fc.fc_search(h, 3, 25)

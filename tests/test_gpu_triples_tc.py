@@ -29,10 +29,20 @@ def fc():
     return fcm
 
 
+@pytest.fixture(params=["1", "0"], ids=["one-accumulator", "per-class"])
+def form(request, monkeypatch):
+    """Both forms of the kernel: one accumulator n_case + 4096 n_ctrl (the
+    default while both classes have at most 4095 samples) and one
+    accumulator per class (FC_TRIPLES_ENC=0, the form for larger classes)."""
+    if request.param == "0":
+        monkeypatch.setenv("FC_TRIPLES_ENC", "0")
+    else:
+        monkeypatch.delenv("FC_TRIPLES_ENC", raising=False)
+    return int(request.param)
+
+
 @pytest.fixture
 def path(monkeypatch):
-    monkeypatch.delenv("FC_TRIPLES_SLAB_MB", raising=False)
-
     def set_path(p):
         monkeypatch.setenv("FC_TRIPLES_PATH", p)
     return set_path
@@ -44,18 +54,19 @@ def all_triples(S):
 
 @pytest.mark.parametrize("S,cases,controls,seed", [(3, 40, 50, 1), (33, 700, 650, 2), (70, 129, 1000, 3),
                                                    (100, 1500, 2100, 4), (131, 1, 300, 5), (97, 300, 1, 6)])
-def test_dense_tables_exact(fc, S, cases, controls, seed):
+def test_dense_tables_exact(fc, form, S, cases, controls, seed):
     """Every combination's 27-cell table, for SNP counts that are not
     multiples of the 32-pair and 64-SNP blocks and ragged sample counts."""
     ds = make_dataset("t3", seed=700 + seed, S=S, cases=cases, controls=controls, k=3, top_n=5)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
+    assert fc.fc_triples_form(h) == form
     _, tab = fc.fc_triples_dense(h, scores=False, tables=True)
     ref = oracle.tables(ds.genotypes, ds.phenotype, 3, all_triples(S))
     bad = np.nonzero(np.any(tab != ref, axis=(1, 2)))[0]
     assert len(bad) == 0, (len(bad), all_triples(S)[bad[:5]], tab[bad[:1]], ref[bad[:1]])
 
 
-def test_dense_tables_several_slabs(fc, monkeypatch):
+def test_dense_tables_several_slabs(fc, form, monkeypatch):
     """A slab capacity of 1 MiB forces one slab per few first SNPs; the
     tables are the same."""
     monkeypatch.setenv("FC_TRIPLES_SLAB_MB", "1")
@@ -66,7 +77,34 @@ def test_dense_tables_several_slabs(fc, monkeypatch):
     assert np.array_equal(tab, ref)
 
 
-def test_dense_scores_within_fp32_bound(fc):
+def test_dense_tables_many_sample_chunks(fc, form):
+    """Classes of 4,100 and 3,001 samples (33 and 24 chunks of 128 samples,
+    both ragged): the pair rows formed on chip for every chunk give the
+    exact tables."""
+    ds = make_dataset("t3k", seed=721, S=70, cases=4100, controls=3001, k=3, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    _, tab = fc.fc_triples_dense(h, scores=False, tables=True)
+    ref = oracle.tables(ds.genotypes, ds.phenotype, 3, all_triples(70))
+    assert np.array_equal(tab, ref)
+
+
+def test_dense_tables_large_classes_one_accumulator(fc):
+    """4,000 cases and 1,800 controls: the one-accumulator form holds
+    n_case + 4096 n_ctrl up to about 7.4e6 exactly; a class of 4,096 samples
+    takes the per-class form."""
+    ds = make_dataset("t3e", seed=725, S=40, cases=4000, controls=1800, k=3, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    assert fc.fc_triples_form(h) == 1
+    _, tab = fc.fc_triples_dense(h, scores=False, tables=True)
+    assert np.array_equal(tab, oracle.tables(ds.genotypes, ds.phenotype, 3, all_triples(40)))
+    big = make_dataset("t3f", seed=726, S=40, cases=4096, controls=100, k=3, top_n=5)
+    hb = fc.fc_load(big.genotypes, big.phenotype)
+    assert fc.fc_triples_form(hb) == 0
+    _, tab = fc.fc_triples_dense(hb, scores=False, tables=True)
+    assert np.array_equal(tab, oracle.tables(big.genotypes, big.phenotype, 3, all_triples(40)))
+
+
+def test_dense_scores_within_fp32_bound(fc, form):
     ds = make_dataset("t3sc", seed=730, S=150, cases=1500, controls=1711, k=3, top_n=5, planted=(9, 70, 140))
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     sc, _ = fc.fc_triples_dense(h, scores=True, tables=False)
@@ -75,7 +113,7 @@ def test_dense_scores_within_fp32_bound(fc):
 
 
 @pytest.mark.parametrize("S,cases,controls,top_n", [(130, 900, 1100, 100), (300, 2000, 1000, 60)])
-def test_search_tc_matches_oracle(fc, path, S, cases, controls, top_n):
+def test_search_tc_matches_oracle(fc, form, path, S, cases, controls, top_n):
     path("tc")
     ds = make_dataset("t3search", seed=740 + S, S=S, cases=cases, controls=controls, k=3, top_n=top_n,
                       planted=(13, S // 2, S - 7))
@@ -90,8 +128,8 @@ def test_search_tc_matches_oracle(fc, path, S, cases, controls, top_n):
     assert tuple(g_idx[0]) == (13, S // 2, S - 7)
 
 
-def test_search_several_slabs_agree(fc, path, monkeypatch):
-    ds = make_dataset("t3slab", seed=750, S=260, cases=1000, controls=1300, k=3, top_n=80,
+def test_search_several_slabs_agree(fc, form, path, monkeypatch):
+    ds = make_dataset("t3slab", seed=751, S=260, cases=1000, controls=1300, k=3, top_n=80,
                       planted=(3, 100, 250))
     path("tc")
     h = fc.fc_load(ds.genotypes, ds.phenotype)
@@ -104,6 +142,22 @@ def test_search_several_slabs_agree(fc, path, monkeypatch):
     for x in (b, c):
         assert np.array_equal(a[0], x[0])
         np.testing.assert_allclose(a[1], x[1], rtol=1e-12)
+
+
+def test_search_repeated_and_reloaded_agree(fc, path):
+    ds = make_dataset("t3rep", seed=750, S=260, cases=1000, controls=1300, k=3, top_n=80,
+                      planted=(3, 100, 250))
+    path("tc")
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    a = fc.fc_search(h, 3, 80)
+    h2 = fc.fc_load(ds.genotypes, ds.phenotype)
+    b = fc.fc_search(h2, 3, 80)
+    assert fc.fc_last_search_kind(h2) == 6
+    c = fc.fc_search(h2, 3, 80)
+    for x in (b, c):
+        assert np.array_equal(a[0], x[0])
+        np.testing.assert_allclose(a[1], x[1], rtol=1e-12)
+    assert tuple(a[0][0]) == (3, 100, 250)
 
 
 def test_tc_and_popc_paths_agree_full_size(fc, path):

@@ -236,6 +236,7 @@ cudaError_t launch_final_sort_batch(const JobDesc *jobs, int n_jobs, double *res
 // ---- order-2 tensor-core path (fc_pairs_tc.cu) -----------------------------
 
 constexpr int TC_MAX_STAGES = 6;
+constexpr int TC_MAX_PRODUCERS = 4;   // TMA producer warps of the order-2 and orders 4-6 kernels
 enum { MODE_DUMP = 2 };
 // Time budget of one mbarrier wait in the tensor-core kernels, in clock64
 // ticks (about 2 s).  The pipeline waits of the order-2 kernel take theirs
@@ -255,6 +256,7 @@ struct PairsArgs {
     uint64_t pair_base;     // C(S, 2)
     uint64_t rank_begin, rank_end;   // only pairs with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2, stages;
+    int producers;          // TMA producer warps (a divisor of stages, at most 4)
     long long wait_ticks;   // budget of each pipeline wait (clock64 ticks)
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
@@ -337,6 +339,7 @@ struct QuadsArgs {
     float hy, invN;
     uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2, stages;
+    int producers;          // TMA producer warps (a divisor of stages, at most 4)
     float *list_score;      // [grid][L]
     uint64_t *list_rank;
     int *gthr;

@@ -30,9 +30,12 @@
 // on the left tuple only and one that depends on the right tuple only, both
 // computed on the host.
 //
-// Roles (one persistent CTA per SM, 192 threads), as in the order-2 kernel:
-//   warp 0 : TMA producer (128-byte K chunks of the left and right blocks)
-//   warp 1 : TMEM allocation and the single-thread MMA issue
+// Roles (one persistent CTA per SM, TC_THREADS_MP threads), as in the
+// order-2 kernel:
+//   warps 0, 6, 7, 8 : TMA producers (128-byte K chunks of the left and right
+//                      blocks), producer p owning the stages s = p (mod
+//                      producers)
+//   warp 1 : TMEM allocation; lane 0 issues the MMAs and schedules the tiles
 //   warps 2-5 : epilogue (TMEM -> registers -> partial MI over a row's cells
 //               -> sum over a left tuple's lanes -> CTA top list)
 // Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
@@ -90,7 +93,7 @@ __global__ void k_tuple_rows(const uint4 *X, int64_t S_pad, int Wt, const uint64
 }
 
 template <int LT, int RT, int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS_MP, 1)
     k_quads_tc(const __grid_constant__ CUtensorMap tmapL, const __grid_constant__ CUtensorMap tmapR, QuadsArgs a)
 {
     constexpr int RL = LT == 2 ? 9 : 27;            // rows (cells) per left tuple
@@ -133,7 +136,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_init(&bar_done, 1);
         for (int s = 0; s < TC_SCHED; ++s) {
             mbar_init(&bar_sfull[s], 1);
-            mbar_init(&bar_sempty[s], 5);   // the MMA thread and the four epilogue warps
+            // The producers, the MMA thread and the four epilogue warps.
+            mbar_init(&bar_sempty[s], a.producers + 5);
         }
         abort_flag_s = 0;
         buf_count = 0;
@@ -160,19 +164,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int kc0 = a.W0, kc1 = a.Wt - a.W0;   // 128-sample chunks per class
 
-    if (warp == 0) {
-        // ---------------- TMA producer ----------------
+    const int prod = tc_producer_of(warp, a.producers);
+    if (prod >= 0) {
+        // ---------------- TMA producers ----------------
         if (lane == 0) {
+            const int P = a.producers;
             uint32_t fill = 0;
+            // Last fill issued into each owned stage (at most two: stages prod
+            // and prod + P).
+            int last0 = -1, last1 = -1;
             bool ok = true;
             for (int it = 0; ok; ++it) {
                 const int slot = it % TC_SCHED;
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
-                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err)) break;
-                int t = atomicAdd(a.tile_counter, 1);
-                if (t >= a.ntiles) t = -1;
-                sched_tile[slot] = t;
-                mbar_arrive(&bar_sfull[slot]);
+                if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
+                const int t = sched_tile[slot];
+                mbar_arrive(&bar_sempty[slot]);
                 if (t < 0) break;
                 const uint2 tile = a.tiles[t];
                 const int rowL = (int)tile.x * 128, rowR = (int)tile.y * 128;
@@ -181,30 +188,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int xbase = c ? kc0 * TC_BK : 0;
                     for (int kc = 0; kc < nk; ++kc, ++fill) {
                         const int s = fill % stages;
+                        if (s % P != prod) continue;
                         const uint32_t n = fill / stages;
                         if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
                         mbar_expect_tx(&bar_full[s], TC_A_BYTES + TC_B_BYTES);
                         tma_load_2d(&tmapL, &bar_full[s], stA + (size_t)s * TC_A_BYTES, xbase + kc * TC_BK, rowL);
                         tma_load_2d(&tmapR, &bar_full[s], stB + (size_t)s * TC_B_BYTES, xbase + kc * TC_BK, rowR);
+                        if (s == prod) last0 = (int)fill; else last1 = (int)fill;
                     }
                 }
             }
-            // Let every copy issued so far land before the CTA can exit.
-            const uint32_t issued = fill;
-            for (uint32_t f = (issued > (uint32_t)stages ? issued - stages : 0); f < issued; ++f) {
-                const int s = f % stages;
-                const uint32_t n = f / stages;
+            // Let the last copies into the stages this producer owns land
+            // before the CTA can exit (earlier ones were consumed).
+            for (int q = 0; q < 2; ++q) {
+                const int s = prod + q * P;
+                const int f = q ? last1 : last0;
+                if (s >= stages || f < 0) continue;
+                const uint32_t n = (uint32_t)f / stages;
                 long long t0 = clock64();
                 while (!mbar_try(&bar_full[s], n & 1) && clock64() - t0 < WAIT_BUDGET) {}
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issue ----------------
         if (lane == 0) {
+            // ---------------- MMA issue ----------------
             const uint32_t idesc = idesc_e4m3_f32(TC_BM, TC_BN);
             uint32_t fill = 0;
             bool ok = true;
+            // This thread also schedules the tiles, TC_LOOKAHEAD ahead of the
+            // one it consumes (another lane of this warp spinning on the ring
+            // delayed the MMA issue).
+            int published = 0;
+            bool sched_done = false;
+            auto publish = [&](int k) -> bool {
+                const int pslot = k % TC_SCHED;
+                const uint32_t psn = (uint32_t)(k / TC_SCHED);
+                if (!mbar_wait(&bar_sempty[pslot], (psn & 1) ^ 1, abort_flag, a.err)) return false;
+                int t = -1;
+                if (!sched_done) {
+                    t = atomicAdd(a.tile_counter, 1);
+                    if (t >= a.ntiles) { t = -1; sched_done = true; }
+                }
+                sched_tile[pslot] = t;
+                mbar_arrive(&bar_sfull[pslot]);
+                return true;
+            };
+            for (; published < TC_LOOKAHEAD && ok; ++published) ok = publish(published);
             for (int it = 0; ok; ++it) {
+                if (!(ok = publish(published++))) break;
                 const int slot = it % TC_SCHED;
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
                 if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
@@ -240,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             long long t0 = clock64();
             while (!mbar_try(&bar_done, 0) && clock64() - t0 < WAIT_BUDGET) {}
         }
-    } else {
+    } else if (warp >= 2 && warp < 6) {
         // ---------------- epilogue ----------------
         // TMEM lane = left row 32 w + RL p + d_L; column 32 c + RR q + d_R =
         // right tuple RPC c + q of the tile, genotype digits d_R.
@@ -421,7 +452,7 @@ cudaError_t launch_quads_tc(int k, int mode, const CUtensorMap &tmapL, const CUt
     CUtensorMap mL = tmapL, mR = tmapR;
     QuadsArgs args = a;
     void *params[] = {&mL, &mR, &args};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(TC_THREADS), params, bytes, st);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(TC_THREADS_MP), params, bytes, st);
 }
 
 }  // namespace fc

@@ -557,6 +557,21 @@ int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t 
     return FC_OK;
 }
 
+// TMA producer warps of the order-2 and orders 4-6 kernels: every stage
+// count up to 4 gets one producer per stage; 5 stages drop to 4, and 6 take
+// three producers of two stages each.
+void tc_producer_split(int *stages, int *producers)
+{
+    if (*stages == 5) *stages = 4;
+    *producers = *stages <= 4 ? *stages : 3;
+    // FC_TC_PRODUCERS=p (a tuning knob) takes p producers where p divides
+    // the stage count.
+    if (const char *v = getenv("FC_TC_PRODUCERS")) {
+        const int p = atoi(v);
+        if (p >= 1 && p <= TC_MAX_PRODUCERS && *stages % p == 0) *producers = p;
+    }
+}
+
 int pow2_at_least(int v)
 {
     int p = 1;
@@ -603,6 +618,7 @@ PairsArgs Dataset::pairs_args(int L, float hy, float invN)
     for (int st = TC_MAX_STAGES; st >= 2; --st) {
         if (pairs_smem_bytes(st, (int)M, pa.P2) <= (size_t)max_smem_optin) { pa.stages = st; break; }
     }
+    tc_producer_split(&pa.stages, &pa.producers);
     // FC_TEST_WAIT_TICKS (tests only) shortens the pipeline waits so that
     // they run out and the kernel reports FC_ETIMEOUT.
     pa.wait_ticks = TC_WAIT_TICKS;
@@ -1103,6 +1119,7 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
     for (int st = TC_MAX_STAGES; st >= 2; --st) {
         if (pairs_smem_bytes(st, (int)M, qa.P2) <= (size_t)max_smem_optin) { qa.stages = st; break; }
     }
+    tc_producer_split(&qa.stages, &qa.producers);
     return qa;
 }
 

@@ -16,7 +16,20 @@ constexpr int TC_BN = 128;          // tile columns
 constexpr int TC_BK = 128;          // K bytes (samples) per pipeline stage
 constexpr int TC_SNPS = 64;         // SNPs per tile side
 constexpr int TC_THREADS = 192;
+// Kernels with several TMA producer warps: warp 0 and warps TC_PROD_WARP1 ..
+// issue the copies (TMA copies issued from one thread complete about one
+// stage at a time); producer p owns the stages s = p (mod producers).
+constexpr int TC_PROD_WARP1 = 6;                              // after warp 1 (MMA) and the four epilogue warps
+constexpr int TC_THREADS_MP = 32 * (TC_PROD_WARP1 + TC_MAX_PRODUCERS - 1);
+
+// Producer index of warp w, or -1 (warp 0 -> 0, warp TC_PROD_WARP1 + q -> q + 1).
+__device__ __forceinline__ int tc_producer_of(int w, int producers)
+{
+    const int p = w == 0 ? 0 : (w >= TC_PROD_WARP1 ? w - TC_PROD_WARP1 + 1 : -1);
+    return p < producers ? p : -1;
+}
 constexpr int TC_SCHED = 4;         // depth of the tile-scheduling ring
+constexpr int TC_LOOKAHEAD = 2;     // tiles the MMA thread publishes ahead of the one it consumes
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr uint32_t TC_A_BYTES = TC_BM * TC_BK;   // 16 KiB
 constexpr uint32_t TC_B_BYTES = TC_BN * TC_BK;   // 16 KiB

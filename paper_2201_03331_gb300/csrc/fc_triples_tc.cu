@@ -53,7 +53,7 @@
 //
 // Roles (one persistent CTA per SM, 512 threads):
 //   warps 0-2  : producers (lane 0 issues the TMA copies of its stage)
-//   warp 3     : lane 0 issues the MMAs, lane 1 schedules tiles; the warp
+//   warp 3     : lane 0 issues the MMAs and schedules the tiles; the warp
 //                allocates and frees TMEM
 //   warps 4-15 : epilogue (TMEM -> registers -> 27-cell table -> MI ->
 //                list), three warps per TMEM lane quarter, each taking every
@@ -248,7 +248,27 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             const uint32_t idesc = idesc_e4m3_f32(TC_BM, Sh::NMMA);
             uint32_t fill = 0;
             bool ok = true;
+            // This thread also schedules the tiles, TC_LOOKAHEAD ahead of the
+            // one it consumes (another lane of this warp spinning on the ring
+            // delayed the MMA issue).
+            int published = 0;
+            bool sched_done = false;
+            auto publish = [&](int k) -> bool {
+                const int pslot = k % TC_SCHED;
+                const uint32_t psn = (uint32_t)(k / TC_SCHED);
+                if (!mbar_wait(&bar_sempty[pslot], (psn & 1) ^ 1, abort_flag, a.err, wt)) return false;
+                int t = -1;
+                if (!sched_done) {
+                    t = atomicAdd(a.tile_counter, 1);
+                    if (t >= a.ntiles) { t = -1; sched_done = true; }
+                }
+                sched_tile[pslot] = t;
+                mbar_arrive(&bar_sfull[pslot]);
+                return true;
+            };
+            for (; published < TC_LOOKAHEAD && ok; ++published) ok = publish(published);
             for (int it = 0; ok; ++it) {
+                if (!(ok = publish(published++))) break;
                 const int slot = it % TC_SCHED;
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
                 if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt)) break;
@@ -284,18 +304,6 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             mma_commit(&bar_done);
             long long t0 = clock64();
             while (!mbar_try(&bar_done, 0) && clock64() - t0 < WAIT_BUDGET) {}
-        } else if (lane == 1) {
-            // ---------------- tile scheduler ----------------
-            for (int it = 0;; ++it) {
-                const int slot = it % TC_SCHED;
-                const uint32_t sn = (uint32_t)(it / TC_SCHED);
-                if (!mbar_wait(&bar_sempty[slot], (sn & 1) ^ 1, abort_flag, a.err, wt)) break;
-                int t = atomicAdd(a.tile_counter, 1);
-                if (t >= a.ntiles) t = -1;
-                sched_tile[slot] = t;
-                mbar_arrive(&bar_sfull[slot]);
-                if (t < 0) break;
-            }
         }
     } else {
         // ---------------- epilogue ----------------

@@ -295,6 +295,7 @@ struct TriplesArgs {
     uint64_t total;         // C(S, 3)
     uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count
     int L, Bcap, P2;        // list, candidate buffer (>= 2048), pow2 >= L + Bcap
+    int check_rounds;       // epilogue rounds between buffer checks (Bcap holds that many rounds)
     long long wait_ticks;   // budget of each pipeline wait (clock64 ticks)
     float *list_score;      // [grid][L]
     uint64_t *list_rank;

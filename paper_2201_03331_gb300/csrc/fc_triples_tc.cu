@@ -117,23 +117,6 @@ __device__ __forceinline__ uint32_t unpack_enc(uint32_t bits)
     return pack_exact(__float_as_uint(lo), __float_as_uint(hi));
 }
 
-// One barrier of the NT epilogue threads that also tells every thread
-// whether any thread passed a true predicate.
-template <int NT>
-__device__ __forceinline__ bool epi_bar_or(bool pred)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred q, p;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "n"(NT)
-        : "memory");
-    return r != 0;
-}
-
 template <int MODE, int ENC>
 __global__ void __launch_bounds__(T3_THREADS, 1)
     k_triples_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapP, TriplesArgs a)
@@ -320,14 +303,29 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         const uint32_t lt = (uint32_t)a.M;
         const int64_t Sp = a.S_pad;
         const bool whole = a.rank_begin == 0 && a.rank_end >= a.total;
-        // A round inserts at most 2 candidates per thread.  A merge is due
-        // when the buffer might not hold two more rounds: every thread reads
-        // the fill before the round's barrier, after its own insertions of
-        // the round before, so the fill at that barrier is at most the
-        // largest value read plus one round.
-        const int headroom = 2 * 2 * T3_EPI_THREADS;
+        // A round inserts at most 2 candidates per thread.  Every
+        // a.check_rounds rounds (and at the start of each tile) the threads
+        // read the buffer's fill between two barriers, where nobody inserts,
+        // and merge it into the list if the next check_rounds rounds might
+        // not fit.
+        const int headroom = a.check_rounds * 2 * T3_EPI_THREADS;
         float thr_s = -FLT_MAX;
         uint64_t thr_r = NO_RANK;
+        // Merge the buffer into the list (all epilogue threads, uniform).
+        auto merge = [&]() {
+            epi_bar_n<T3_EPI_THREADS>();
+            const int nb = min(buf_count, a.Bcap);
+            for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) {
+                lscore[x] = -FLT_MAX;
+                lrank[x] = NO_RANK;
+            }
+            epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
+            if (tid == 0) {
+                buf_count = 0;
+                if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr, ordered_int(lscore[L - 1]));
+            }
+            epi_bar_n<T3_EPI_THREADS>();
+        };
         for (int it = 0;; ++it) {
             const int slot = it % TC_SCHED;
             const uint32_t sn = (uint32_t)(it / TC_SCHED);
@@ -379,13 +377,23 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 }
                 mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err, wt);
             }
+            // The global threshold only rises; a value read once per tile
+            // admits at most a few more candidates than a fresh one would.
+            const float gthr = MODE == MODE_TOPN ? from_ordered(*(volatile int *)a.gthr) : -FLT_MAX;
             // One stop decision for all epilogue warps (they meet at named
             // barriers, which have no timeout); t is the same for all.  The
-            // barrier also publishes the tables of the SNPs j.
+            // barrier also publishes the tables of the SNPs j, and between
+            // the two barriers the buffer's fill is the same for all.
             epi_bar_n<T3_EPI_THREADS>();
             if (tid == 0) epi_stop = *abort_flag;
+            const int fill0 = buf_count;
             epi_bar_n<T3_EPI_THREADS>();
             if (epi_stop || t < 0) break;
+            if (MODE == MODE_TOPN) {
+                if (fill0 > a.Bcap - headroom) merge();
+                thr_s = lscore[L - 1];
+                thr_r = lrank[L - 1];
+            }
             tc_fence_after();
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
             const int64_t lc = lv ? l : a.S - 1;
@@ -401,6 +409,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             for (int rnd = 0; rnd < Sh::ROUNDS; ++rnd) {
                 const int qd = part + rnd * T3_PARTS;            // group of pairs 4 qd .. 4 qd + 3
                 const bool has = qd < Sh::QUADS;                 // warp-uniform
+                if (MODE == MODE_TOPN && rnd > 0 && rnd % a.check_rounds == 0) {
+                    epi_bar_n<T3_EPI_THREADS>();
+                    const int fill = buf_count;
+                    epi_bar_n<T3_EPI_THREADS>();
+                    if (fill > a.Bcap - headroom) merge();
+                    thr_s = lscore[L - 1];
+                    thr_r = lrank[L - 1];
+                }
                 pjl[0] = pjl_next[0];
                 pjl[1] = pjl_next[1];
                 if (qd + T3_PARTS < Sh::QUADS) {
@@ -492,14 +508,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         const uint32_t R12[4] = {pjl[m].x, pjl[m].y, pjl[m].z, pjl[m].w};
                         full2(R12, Tj, Tl, T12);
                         full3(Rr, T01, T02, T12, T);
+                        // Three partial sums (nine cells each) shorten the chain
+                        // of dependent additions; every partial sum is still at
+                        // most N ln 2, so the error bound above holds.
+                        float hs[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                         for (int x = 0; x < 27; ++x) {
                             // Clamped so that no index can leave the table
                             // (a, b <= n <= M for exact counts).
                             const uint32_t ca = T[x] & 0xffffu, cb = T[x] >> 16;
                             const uint32_t n = min(ca + cb, lt);
-                            hsum += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
+                            hs[x % 3] += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
                         }
+                        hsum = (hs[0] + hs[1]) + hs[2];
                     }
                     const float score = fmaf(-hsum, a.invN, a.hy);
                     const uint64_t rank = valid ? rank0 : NO_RANK;
@@ -516,26 +537,6 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     }
                 }
                 if (MODE == MODE_TOPN) {
-                    // One barrier with an OR reduction gives every thread the
-                    // same merge decision.
-                    const bool need = epi_bar_or<T3_EPI_THREADS>(buf_count > a.Bcap - headroom);
-                    if (need) {
-                        epi_bar_n<T3_EPI_THREADS>();
-                        const int nb = min(buf_count, a.Bcap);
-                        for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) {
-                            lscore[x] = -FLT_MAX;
-                            lrank[x] = NO_RANK;
-                        }
-                        epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
-                        if (tid == 0) {
-                            buf_count = 0;
-                            if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr, ordered_int(lscore[L - 1]));
-                        }
-                        epi_bar_n<T3_EPI_THREADS>();
-                    }
-                    thr_s = lscore[L - 1];
-                    thr_r = lrank[L - 1];
-                    const float gthr = from_ordered(*(volatile int *)a.gthr);
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
                         const bool cand = val[m] && sc[m] >= gthr && better(sc[m], rk[m], thr_s, thr_r);

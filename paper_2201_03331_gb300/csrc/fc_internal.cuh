@@ -278,11 +278,11 @@ cudaError_t launch_marginals(const uint4 *X, int64_t S, int64_t S_pad, int W0, i
 cudaError_t launch_pairs_tc(int mode, const CUtensorMap &tmap, const PairsArgs &a, int grid, cudaStream_t st);
 
 // Order-3 tensor-core search (fc_triples_tc.cu).  A tile pairs the 64 SNPs
-// l of block Lb (128 e4m3 rows 2 l + g) with the NP pairs (i, NP J + q),
-// q < NP, of slab rows [rowP, rowP + 4 NP) (pair row (a, q, b) at
+// l0 .. l0 + 63 (128 e4m3 rows 2 l + g) with the NP pairs (i, j0 + q), q < NP,
+// of slab rows [rowP, rowP + 4 NP) (pair row (a, q, b) at
 // rowP + 2 NP a + 2 q + b); NP = triples_pairs_per_tile(enc).
 struct TriplesArgs {
-    const uint4 *tiles;     // {rowP, i, J, Lb} per tile of this launch
+    const uint4 *tiles;     // {rowP, i, j0, l0} per tile of this launch
     int ntiles;
     int enc;                // 1: one accumulator n_case + 4096 n_ctrl (operand with controls = 64)
     int64_t S, S_pad;

@@ -798,11 +798,12 @@ struct TriplePlan {
 std::mutex g_plan3_mu;
 std::shared_ptr<const TriplePlan> g_plan3;
 
-// Tiles {rowP, i, J, Lb}: first SNP i, block J of NP second SNPs j (from the
-// block of i + 1; slab rows [rowP, rowP + 4 NP)), 64-SNP block Lb of the
-// third SNPs l, for every block that holds some l > j; in order of i, so that
-// a rank range is a contiguous run of tiles.  Slabs hold the rows of
-// consecutive first SNPs up to cap_rows rows (at least one SNP's).
+// Tiles {rowP, i, j0, l0}: first SNP i, the block of NP second SNPs from
+// j0 = i + 1 + NP J' (slab rows [rowP, rowP + 4 NP)), the 64 third SNPs from
+// l0 = j0 + 1 + 64 L', for every block with j0 <= S - 2 and l0 <= S - 1; in
+// order of i, so that a rank range is a contiguous run of tiles.  Slabs hold
+// the rows of consecutive first SNPs up to cap_rows rows (at least one
+// SNP's).
 std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_rows)
 {
     {
@@ -813,15 +814,13 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_ro
     pl->S = S;
     pl->NP = NP;
     pl->cap_rows = cap_rows;
-    const int64_t nJ = (S + NP - 1) / NP;
-    const int64_t nLb = (S + 63) / 64;
     std::vector<uint4> &tiles = pl->tiles;
     pl->rowbase.assign((size_t)S, 0);
     pl->first_tile.assign((size_t)S + 1, 0);
     Dataset::TripleSlab cur;
     for (int64_t i = 0; i + 2 < S; ++i) {
-        const int64_t Jlo = (i + 1) / NP;
-        const int64_t n = (nJ - Jlo) * 4 * NP;   // rows of the pairs of i
+        const int64_t nJ = (S - 1 - i + NP - 1) / NP;
+        const int64_t n = nJ * 4 * NP;   // rows of the pairs of i
         if (cur.rows + n > cap_rows && i > cur.i0) {
             cur.i1 = i;
             cur.t1 = (int64_t)tiles.size();
@@ -833,11 +832,11 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_ro
         }
         pl->rowbase[(size_t)i] = cur.rows;
         pl->first_tile[(size_t)i] = (int64_t)tiles.size();
-        for (int64_t J = Jlo; NP * J <= S - 2; ++J) {
-            const int64_t jmin = std::max<int64_t>(NP * J, i + 1);
-            for (int64_t Lb = (jmin + 1) / 64; Lb < nLb; ++Lb)
-                tiles.push_back(make_uint4((uint32_t)(cur.rows + (J - Jlo) * 4 * NP), (uint32_t)i, (uint32_t)J,
-                                           (uint32_t)Lb));
+        for (int64_t Jp = 0; Jp < nJ; ++Jp) {
+            const int64_t j0 = i + 1 + NP * Jp;
+            if (j0 > S - 2) break;
+            for (int64_t l0 = j0 + 1; l0 <= S - 1; l0 += 64)
+                tiles.push_back(make_uint4((uint32_t)(cur.rows + Jp * 4 * NP), (uint32_t)i, (uint32_t)j0, (uint32_t)l0));
         }
         cur.rows += n;
     }
@@ -903,7 +902,7 @@ int Dataset::prepare_triples()
     }
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, free_b / 4);
-    const int64_t nJ = (S + NP - 1) / NP;
+    const int64_t nJ = (S - 2 + NP) / NP;   // blocks of the pairs of i = 0
     const int64_t cap_rows = std::max<int64_t>((int64_t)(cap / pitch), nJ * 4 * NP);
     const std::shared_ptr<const TriplePlan> plan = plan_triples(S, NP, cap_rows);
     const std::vector<uint4> &tiles = plan->tiles;

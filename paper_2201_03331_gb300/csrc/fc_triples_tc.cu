@@ -29,9 +29,13 @@
 //
 // The pair rows live in a slab in device memory, the paper's `combine` of
 // two genotype tables done once per data set (k_pair_rows): for each first
-// SNP i, the rows of its pairs (i, j) with j in [NP floor((i + 1) / NP), S_NP)
-// in blocks of NP pairs, pair row (a, q, b) of a block at row
-// 2 NP a + 2 q + b, zero where j <= i or j >= S.  Forming them on chip
+// SNP i, the rows of its pairs (i, j), j = i + 1 + NP J' + q, in blocks of NP
+// pairs, pair row (a, q, b) of a block at row 2 NP a + 2 q + b, zero where
+// j >= S.  A tile is (i, the block of SNPs j from j0 = i + 1 + NP J', the 64
+// SNPs l from l0 = j0 + 1 + 64 L'): blocks start right after the SNPs before
+// them, so that only the triangle l <= j of a tile's first l block and the
+// ends beyond S are wasted (83 % of the tile area holds combinations at 1 000
+// SNPs, against 78 % with blocks aligned to multiples of 64).  Forming them on chip
 // instead (TMA of the rows of the SNPs j, AND with the rows of SNP i in
 // shared memory) was measured slower: the 48 KiB of shared-memory traffic
 // per 128-sample chunk of the builder cost more than the slab's one-time
@@ -85,6 +89,15 @@ struct T3Shape {
     static constexpr int ROUNDS = (QUADS + T3_PARTS - 1) / T3_PARTS;
 };
 
+// Entries of the shared-memory x ln x table: the power of two above M (the
+// entries beyond M are 0), so that a masked index never leaves it.
+__host__ __device__ inline int xl_table_size(int M)
+{
+    int n = 4;
+    while (n <= M) n <<= 1;
+    return n;
+}
+
 __device__ __forceinline__ uint64_t c3(uint64_t n) { return n * (n - 1) * (n - 2) / 6; }   // 0 for n < 3
 __device__ __forceinline__ uint64_t c2(uint64_t n) { return n * (n - 1) / 2; }             // 0 for n < 2
 
@@ -106,15 +119,13 @@ __device__ __forceinline__ uint32_t pack_exact(uint32_t lo_bits, uint32_t hi_bit
     return a + (b << 16) - 0x4B000000u;
 }
 
-// One encoded accumulator x = n_case + 4096 n_ctrl (exact, x < 2^24) as
-// n_case | n_ctrl << 16: n_ctrl = floor(x / 4096) and n_case = x - 4096 n_ctrl
-// are exact in FP32 and below 2^12.
+// One encoded accumulator x = n_case + 4096 n_ctrl (an exact integer below
+// 2^24, n_case < 4096) as n_case | n_ctrl << 16: v = x as an integer, and
+// v + (v >> 12) (65536 - 4096) moves n_ctrl from bit 12 to bit 16.
 __device__ __forceinline__ uint32_t unpack_enc(uint32_t bits)
 {
-    const float x = __uint_as_float(bits);
-    const float hi = floorf(x * (1.0f / 4096.0f));
-    const float lo = fmaf(hi, -4096.0f, x);
-    return pack_exact(__float_as_uint(lo), __float_as_uint(hi));
+    const uint32_t v = __float2uint_rz(__uint_as_float(bits));
+    return v + (v >> 12) * 61440u;
 }
 
 template <int MODE, int ENC>
@@ -141,7 +152,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     // x ln x table, the list and the tables of the tile's SNPs j.
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     float *xltab = reinterpret_cast<float *>(smem + (size_t)T3_LOADERS * Sh::STAGE);
-    const int lt_floats = (a.M + 1 + 3) & ~3;
+    const int lt_floats = xl_table_size(a.M);   // a power of two above M
     uint64_t *lrank = reinterpret_cast<uint64_t *>(xltab + lt_floats);
     float *lscore = reinterpret_cast<float *>(lrank + a.P2);
     uint32_t *sJ = reinterpret_cast<uint32_t *>(lscore + a.P2);   // [2][NP][T3_SJ_WORDS]
@@ -206,14 +217,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 continue;
             }
             const uint4 tile = a.tiles[t];
-            const int rowP = (int)tile.x, Lb = (int)tile.w;
+            const int rowP = (int)tile.x, l0 = (int)tile.w;
             for (int kc = 0; kc < a.Wt; ++kc, ++fill) {
                 if ((int)(fill % T3_LOADERS) != w) continue;
                 const uint32_t n = fill / T3_LOADERS;
                 if (!mbar_wait(&bar_empty[w], (n & 1) ^ 1, abort_flag, a.err, wt)) { ok = false; break; }
                 const int x = kc * TC_BK;
                 mbar_expect_tx(&bar_full[w], Sh::STAGE);
-                tma_load_2d(&tmapA, &bar_full[w], st, x, Lb * TC_BM);
+                tma_load_2d(&tmapA, &bar_full[w], st, x, 2 * l0);
                 tma_load_2d(&tmapP, &bar_full[w], st + TC_A_BYTES, x, rowP);
                 ++issued;
                 last_n = n;
@@ -291,7 +302,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     } else {
         // ---------------- epilogue ----------------
         // TMEM lane = A row = 2 l_loc + g; column (within a class for ENC = 0)
-        // 2 NP a + 2 q + b = pair (i, NP J + q) with genotypes (a, b).  Warp w
+        // 2 NP a + 2 q + b = pair (i, j0 + q) with genotypes (a, b).  Warp w
         // reads lane quarter w % 4 and the groups of 4 pairs part, part + 3, ..
         const int tid = threadIdx.x - 32 * T3_EPI_WARP0;   // 0 .. T3_EPI_THREADS - 1
         const int quarter = warp & 3;
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         const int l_loc = row >> 1;
         const int g = row & 1;
         const int L = a.L;
-        const uint32_t lt = (uint32_t)a.M;
+        const uint32_t tmask = (uint32_t)lt_floats - 1;
         const int64_t Sp = a.S_pad;
         const bool whole = a.rank_begin == 0 && a.rank_end >= a.total;
         // A round inserts at most 2 candidates per thread.  Every
@@ -339,16 +350,15 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             const uint32_t u = (uint32_t)(it >> 1);
             // Tile data that does not depend on the accumulators, loaded while
             // the tile's MMAs may still run.
-            int64_t l = 0;
-            int J = 0;
+            int64_t l = 0, j0 = 0;
             uint32_t Tl[3] = {0, 0, 0}, T02[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             bool lv = false;
             uint32_t *sJb = sJ + (size_t)b * NP * T3_SJ_WORDS;
             if (t >= 0) {
                 const uint4 tile = a.tiles[t];
                 const int64_t i = tile.y;
-                J = (int)tile.z;
-                l = (int64_t)tile.w * 64 + l_loc;
+                j0 = tile.z;
+                l = (int64_t)tile.w + l_loc;
                 lv = l < a.S;
                 const int64_t lc = lv ? l : a.S - 1;
                 uint32_t Ti[3];
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 full2(R, Ti, Tl, T02);
                 // The tables of the tile's SNPs j, one thread per j.
                 if (tid < NP) {
-                    const int64_t j = (int64_t)J * NP + tid;
+                    const int64_t j = j0 + tid;
                     const int64_t jc = j < a.S ? j : a.S - 1;
                     uint32_t Tj[3], T01[9];
                     unpack_marg(a.marg4[jc], Tj);
@@ -373,7 +383,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     rec[0] = make_uint4(T01[0], T01[1], T01[2], T01[3]);
                     rec[1] = make_uint4(T01[4], T01[5], T01[6], T01[7]);
                     rec[2] = make_uint4(T01[8], Tj[0], Tj[1], Tj[2]);
-                    rec[3] = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), (j > i && j < a.S) ? 1u : 0u, 0u);
+                    rec[3] = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), j < a.S ? 1u : 0u, 0u);
                 }
                 mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err, wt);
             }
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             uint4 pjl[2], pjl_next[2];
 #pragma unroll
             for (int m = 0; m < 2; ++m) {
-                const int64_t jj = min((int64_t)J * NP + part * 4 + 2 * m + g, a.S - 1);
+                const int64_t jj = min(j0 + part * 4 + 2 * m + g, a.S - 1);
                 pjl_next[m] = a.PR[(size_t)jj * Sp + lc];
             }
             // Every warp runs the same number of rounds (a round without a
@@ -422,7 +432,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 if (qd + T3_PARTS < Sh::QUADS) {
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
-                        const int64_t jj = min((int64_t)J * NP + (qd + T3_PARTS) * 4 + 2 * m + g, a.S - 1);
+                        const int64_t jj = min(j0 + (qd + T3_PARTS) * 4 + 2 * m + g, a.S - 1);
                         pjl_next[m] = a.PR[(size_t)jj * Sp + lc];
                     }
                 }
@@ -494,7 +504,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     const int q = 4 * qd + 2 * m + g;    // pair within the tile
                     const uint4 *rec = reinterpret_cast<const uint4 *>(sJb + (size_t)(has ? q : 0) * T3_SJ_WORDS);
                     const uint4 r3 = rec[3];
-                    const int64_t j = (int64_t)J * NP + q;
+                    const int64_t j = j0 + q;
                     const uint64_t rank0 = (((uint64_t)r3.y << 32) | r3.x) + (uint64_t)l;
                     const bool valid = has && r3.z != 0 && lv && j < l &&
                                        (whole || (rank0 >= a.rank_begin && rank0 < a.rank_end));
@@ -514,11 +524,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         float hs[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                         for (int x = 0; x < 27; ++x) {
-                            // Clamped so that no index can leave the table
-                            // (a, b <= n <= M for exact counts).
-                            const uint32_t ca = T[x] & 0xffffu, cb = T[x] >> 16;
-                            const uint32_t n = min(ca + cb, lt);
-                            hs[x % 3] += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
+                            // Masked so that no index can leave the table
+                            // (exact counts, a + b <= M, are below its size).
+                            const uint32_t ca = T[x] & tmask, cb = (T[x] >> 16) & tmask;
+                            const uint32_t n = (ca + cb) & tmask;
+                            hs[x % 3] += (xltab[n] - xltab[ca]) - xltab[cb];
                         }
                         hsum = (hs[0] + hs[1]) + hs[2];
                     }
@@ -579,7 +589,7 @@ template <int ENC>
 size_t smem_bytes_enc(int M, int P2)
 {
     using Sh = T3Shape<ENC>;
-    return 1024 + (size_t)T3_LOADERS * Sh::STAGE + (size_t)((M + 1 + 3) & ~3) * 4 + (size_t)P2 * (8 + 4) +
+    return 1024 + (size_t)T3_LOADERS * Sh::STAGE + (size_t)xl_table_size(M) * 4 + (size_t)P2 * (8 + 4) +
            (size_t)2 * Sh::NP * T3_SJ_WORDS * 4;
 }
 
@@ -590,25 +600,25 @@ void *kernel_ptr()
 }
 
 // Pair rows of the first SNPs [i0, i1): thread (i - i0, t), t over the
-// pairs (i, j), j in [NP Jlo(i), S_NP), times the 16-byte chunks of a row;
-// the row of pair (a, j, b) is rowbase[i - i0] + (J - Jlo) 4 NP + 2 NP a + 2 q + b
-// (j = NP J + q).
-__global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int64_t S_np, int NP, int64_t i0,
+// pairs (i, j), j = i + 1 + jo, jo < NP ceil((S - 1 - i) / NP), times the
+// 16-byte chunks of a row; the row of pair (a, j, b) is
+// rowbase[i - i0] + (jo / NP) 4 NP + 2 NP a + 2 (jo % NP) + b.
+__global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int NP, int64_t i0,
                             const int64_t *rowbase, uint8_t *P)
 {
     const int64_t ii = blockIdx.y;
     const int64_t i = i0 + ii;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t jlo = NP * ((i + 1) / NP);
+    const int64_t npairs = (S - 1 - i + NP - 1) / NP * NP;
     const int cw = 8 * Wt;                         // 16-byte chunks per row
-    if (t >= (S_np - jlo) * cw) return;
+    if (t >= npairs * cw) return;
     const int64_t jo = t / cw;
     const int ch = (int)(t - jo * cw);
-    const int64_t j = jlo + jo;
+    const int64_t j = i + 1 + jo;
     const uint4 a0 = *(reinterpret_cast<const uint4 *>(E + (2 * i) * pitch) + ch);
     const uint4 a1 = *(reinterpret_cast<const uint4 *>(E + (2 * i + 1) * pitch) + ch);
     uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0;
-    if (j > i && j < S) {
+    if (j < S) {
         b0 = *(reinterpret_cast<const uint4 *>(E + (2 * j) * pitch) + ch);
         b1 = *(reinterpret_cast<const uint4 *>(E + (2 * j + 1) * pitch) + ch);
     }
@@ -634,10 +644,9 @@ cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S,
                              const int64_t *rowbase, uint8_t *P, cudaStream_t st)
 {
     if (i1 <= i0) return cudaSuccess;
-    const int64_t S_np = (S + NP - 1) / NP * NP;
-    const int64_t maxn = S_np * 8 * (int64_t)Wt;
+    const int64_t maxn = (S - 1 - i0 + NP - 1) / NP * NP * 8 * (int64_t)Wt;   // the pairs of i0, the most
     dim3 grid((unsigned)((maxn + 255) / 256), (unsigned)(i1 - i0));
-    k_pair_rows<<<grid, 256, 0, st>>>(E, pitch, Wt, S, S_np, NP, i0, rowbase, P);
+    k_pair_rows<<<grid, 256, 0, st>>>(E, pitch, Wt, S, NP, i0, rowbase, P);
     return cudaGetLastError();
 }
 

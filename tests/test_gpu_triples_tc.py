@@ -88,15 +88,19 @@ def test_dense_tables_many_sample_chunks(fc, form):
     assert np.array_equal(tab, ref)
 
 
-def test_dense_tables_large_classes_one_accumulator(fc):
-    """4,000 cases and 1,800 controls: the one-accumulator form holds
-    n_case + 4096 n_ctrl up to about 7.4e6 exactly; a class of 4,096 samples
-    takes the per-class form."""
-    ds = make_dataset("t3e", seed=725, S=40, cases=4000, controls=1800, k=3, top_n=5)
+@pytest.mark.parametrize("cases,controls", [(4000, 90), (90, 4000)])
+def test_dense_tables_large_classes_one_accumulator(fc, cases, controls):
+    """The one-accumulator form near the ends of its range: n_case + 4096
+    n_ctrl reaches about 3.7e5 (4,000 cases) and 1.6e7, close to 2^24
+    (4,000 controls), and stays exact."""
+    ds = make_dataset("t3e", seed=725 + cases, S=40, cases=cases, controls=controls, k=3, top_n=5)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     assert fc.fc_triples_form(h) == 1
     _, tab = fc.fc_triples_dense(h, scores=False, tables=True)
     assert np.array_equal(tab, oracle.tables(ds.genotypes, ds.phenotype, 3, all_triples(40)))
+
+
+def test_dense_tables_class_of_4096_takes_the_per_class_form(fc):
     big = make_dataset("t3f", seed=726, S=40, cases=4096, controls=100, k=3, top_n=5)
     hb = fc.fc_load(big.genotypes, big.phenotype)
     assert fc.fc_triples_form(hb) == 0

@@ -307,6 +307,8 @@ struct TriplesArgs {
 };
 
 int triples_pairs_per_tile(int enc);
+// Candidates one round of the kernel's epilogue may add to its buffer.
+int triples_round_candidates();
 size_t triples_smem_bytes(int enc, int M, int P2);
 // Slab rows of the first SNPs [i0, i1) from the e4m3 rows E (pitch bytes per
 // row); rowbase[i - i0] is the first slab row of SNP i.

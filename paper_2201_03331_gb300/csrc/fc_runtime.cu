@@ -775,10 +775,10 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.L = std::max(L, 1);
     ta.P2 = triples_list_size(L);
     ta.Bcap = ta.P2 - ta.L;
-    // One round of the kernel's epilogue inserts at most 2 x 384 candidates.
+    // Rounds of the kernel's epilogue between checks of its candidate buffer.
     ta.check_rounds = 1;
     for (int r = 3; r >= 1; --r)
-        if (r * 768 <= ta.Bcap) { ta.check_rounds = r; break; }
+        if (r * triples_round_candidates() <= ta.Bcap) { ta.check_rounds = r; break; }
     ta.wait_ticks = TC_WAIT_TICKS;
     return ta;
 }

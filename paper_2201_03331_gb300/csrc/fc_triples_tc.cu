@@ -55,13 +55,14 @@
 // u (2 ln M + 60 ln 2) for every M < 2^29, so the same FP64 rescoring window
 // applies.
 //
-// Roles (one persistent CTA per SM, 512 threads):
+// Roles (one persistent CTA per SM, 640 threads):
 //   warps 0-2  : producers (lane 0 issues the TMA copies of its stage)
 //   warp 3     : lane 0 issues the MMAs and schedules the tiles; the warp
 //                allocates and frees TMEM
-//   warps 4-15 : epilogue (TMEM -> registers -> 27-cell table -> MI ->
-//                list), three warps per TMEM lane quarter, each taking every
-//                third group of 4 pairs
+//   warps 4-19 : epilogue (TMEM -> registers -> 27-cell table -> MI ->
+//                list), four warps per TMEM lane quarter, each taking every
+//                fourth group of 4 pairs (an equal share of a tile's 16 or 8
+//                groups)
 #include "fc_tc.cuh"
 #include "fc_ie.cuh"
 
@@ -71,7 +72,7 @@ namespace {
 
 constexpr int T3_LOADERS = 3;                      // = load stages
 constexpr int T3_EPI_WARP0 = 4;
-constexpr int T3_EPI_WARPS = 12;
+constexpr int T3_EPI_WARPS = 16;
 constexpr int T3_PARTS = T3_EPI_WARPS / 4;         // epilogue warps per TMEM lane quarter
 constexpr int T3_EPI_THREADS = 32 * T3_EPI_WARPS;
 constexpr int T3_THREADS = 32 * T3_EPI_WARP0 + T3_EPI_THREADS;
@@ -637,6 +638,8 @@ __global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, 
 }  // namespace
 
 int triples_pairs_per_tile(int enc) { return enc ? T3Shape<1>::NP : T3Shape<0>::NP; }
+
+int triples_round_candidates() { return 2 * T3_EPI_THREADS; }
 
 size_t triples_smem_bytes(int enc, int M, int P2) { return enc ? smem_bytes_enc<1>(M, P2) : smem_bytes_enc<0>(M, P2); }
 

@@ -535,7 +535,7 @@ def run_batch(args):
     sweep_s = sweep_ms / max(args.steps, 1) / 1e3
     kinds = [fc.fc_batch_job_kind(h, j) for j in range(n_jobs)]
     job_ds = [ds for ds, _ in batch for _ in range(args.c5_replicates)]
-    tc_jobs = [j for j in range(n_jobs) if kinds[j] == 6]
+    tc_jobs = [j for j in range(n_jobs) if kinds[j] in (6, 8)]
     if tc_jobs:
         # The tensor-core jobs dominate: their contraction (8 cells x M
         # samples x 2 FLOP per combination) over the whole kernel time of the

@@ -224,11 +224,14 @@ int fc_search_job(fc_handle *h, int job, int k, int64_t top_n, uint32_t *out_idx
 /*
  * fc_batch_job_kind - the path the last fc_search_batch on h took for job
  * `job` (values of fc_last_search_kind): the persistent batched sweep
- * (1, 3 or 4), or, for order-3 jobs large enough for the tensor cores, the
- * order-3 tensor-core search (6), run one job after another after the
- * persistent launch (FC_BATCH_TC=0 keeps every job in the persistent
- * launch).  0 before the first batched search.  FC_EINVAL for a bad handle
- * or job.
+ * (1, 3 or 4); for order-3 jobs large enough for the tensor cores, the
+ * batched tensor-core launches (8: the replicates of a data set share its
+ * pair-row slab, one persistent launch per group of data sets whose slabs
+ * fit the slab buffer together, all in the same CUDA graph as the sweep),
+ * or the per-job tensor-core search (6) for such jobs that the batched form
+ * does not take (FC_BATCH_TC3=0: none), run one after another.
+ * FC_BATCH_TC=0 keeps every job in the persistent sweep.  0 before the
+ * first batched search.  FC_EINVAL for a bad handle or job.
  */
 int fc_batch_job_kind(const fc_handle *h, int job);
 
@@ -328,7 +331,8 @@ int fc_triples_form(const fc_handle *h);
  * prefix's own table (k = 2..4), 5 (k-2)-prefix table extended by SNP pairs,
  * all 3^k cells counted (k = 4..6), 6 tensor-core order-3 contraction of
  * pair rows with SNP rows (8 cells counted, 19 derived), 7 tensor-core
- * contraction of tuple rows with tuple rows, orders 4-6 (all 3^k cells).
+ * contraction of tuple rows with tuple rows, orders 4-6 (all 3^k cells),
+ * 8 (batch jobs only) kind 6 in the batched tensor-core launches.
  * Every kind yields the same exact tables. */
 int fc_last_search_kind(const fc_handle *h);
 

@@ -281,10 +281,39 @@ cudaError_t launch_pairs_tc(int mode, const CUtensorMap &tmap, const PairsArgs &
 // l0 .. l0 + 63 (128 e4m3 rows 2 l + g) with the NP pairs (i, j0 + q), q < NP,
 // of slab rows [rowP, rowP + 4 NP) (pair row (a, q, b) at
 // rowP + 2 NP a + 2 q + b); NP = triples_pairs_per_tile(enc).
+// One job of the batched order-3 launch (a data set with one phenotype
+// replicate).  The replicates of a data set share its sample order (that of
+// its first replicate), its pair-row slab (genotypes only, e5m2 1.0) and its
+// tiles; the job's SNP rows carry its classes (e5m2 1.0 for a case, 4096 for
+// a control), so an accumulator holds n_case + 4096 n_ctrl.
+struct T3Job {
+    const CUtensorMap *tmapA;   // the job's SNP rows, 128 x 128-byte boxes
+    const CUtensorMap *tmapP;   // the data set's slab, 4 NP x 128-byte boxes
+    const uint4 *tiles;         // the data set's tiles {rowP, i, j0, l0}
+    const uint4 *marg4;         // the job's per-SNP genotype counts
+    const uint4 *PR;            // the job's restricted pair table [S_pad][S_pad]
+    int64_t S, S_pad;
+    uint64_t total;             // C(S, 3)
+    float hy, invN;
+    int Wt;                     // 128-sample chunks
+    int split;                  // enc 2: first chunk of the second accumulator
+    int item_first, ntiles;     // the job's items [item_first, item_first + ntiles) of its launch
+    int slot;                   // lists [slot][grid][L], threshold gthr[slot]
+    int pad;
+};
+
 struct TriplesArgs {
     const uint4 *tiles;     // {rowP, i, j0, l0} per tile of this launch
     int ntiles;
-    int enc;                // 1: one accumulator n_case + 4096 n_ctrl (operand with controls = 64)
+    // 1: one accumulator n_case + 4096 n_ctrl (operand with controls = 64);
+    // 0: one accumulator per class; 2 (batched launch only): two accumulators
+    // n_case + 4096 n_ctrl over the chunks [0, split) and [split, Wt).
+    int enc;
+    // Batched launch (jobs != null): items of all jobs, job-major; the fields
+    // above and below that describe one data set come from the job table,
+    // and list_score, list_rank and gthr are indexed by the job's slot.
+    const T3Job *jobs;
+    int n_jobs, n_items;
     int64_t S, S_pad;
     int W0, Wt;             // 128-sample chunks: cases [0, W0), controls [W0, Wt)
     const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
@@ -297,10 +326,10 @@ struct TriplesArgs {
     int L, Bcap, P2;        // list, candidate buffer (>= 2048), pow2 >= L + Bcap
     int check_rounds;       // epilogue rounds between buffer checks (Bcap holds that many rounds)
     long long wait_ticks;   // budget of each pipeline wait (clock64 ticks)
-    float *list_score;      // [grid][L]
+    float *list_score;      // [grid][L] (batched: [slots][grid][L])
     uint64_t *list_rank;
-    int *gthr;              // global score threshold (ordered int)
-    int *tile_counter;      // next tile of this launch, zeroed before launch
+    int *gthr;              // global score threshold (ordered int; batched: one per slot)
+    int *tile_counter;      // next tile (item) of this launch, zeroed before launch
     uint32_t *err;
     float *dump_scores;     // MODE_DUMP: [C(S,3)] by rank
     uint32_t *dump_tables;  // MODE_DUMP: [C(S,3)][27][2]
@@ -316,8 +345,17 @@ cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S,
                              const int64_t *rowbase, uint8_t *P, cudaStream_t st);
 // tmapA: the e4m3 rows in 128 x 128-byte boxes; tmapP: the slab in 4 NP x
 // 128-byte boxes (both with the 128-byte swizzle).
+// set_attr = false skips setting the kernel's shared-memory attribute (set
+// by an earlier call; a graph capture may not set it); grid = 0 only sets it.
 cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapA, const CUtensorMap &tmapP, const TriplesArgs &a,
-                              int grid, cudaStream_t st);
+                              int grid, cudaStream_t st, bool set_attr = true);
+// Operands of the batched form (e5m2; see T3Job): rows 2 s + g of the bit
+// table X, controls of the replicate marked by ctrl (one uint4 of sample
+// bits per chunk; null: no classes).
+cudaError_t launch_expand_e5m2(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch,
+                               const uint4 *ctrl, uint8_t *E, cudaStream_t st);
+// n list entries (-FLT_MAX, NO_RANK).
+cudaError_t launch_fill_lists(float *s, uint64_t *r, size_t n, cudaStream_t st);
 
 // Orders 4 to 6 on tensor cores (fc_quads_tc.cu): left tuples of LT SNPs
 // x right tuples of RT SNPs, k = LT + RT (2 + 2, 2 + 3, 3 + 3).  Each side is
@@ -329,8 +367,17 @@ constexpr int tc_left_size(int k) { return k == 6 ? 3 : 2; }
 constexpr int tc_tuples_per_block(int T) { return 4 * (27 / (T == 2 ? 9 : 27)); }
 constexpr uint64_t NO_TUPLE = ~0ull;
 struct QuadsArgs {
-    const uint2 *tiles;     // {left block, right block} per tile
-    int ntiles;
+    // Tiles (left block a, right block b) come in strips: item q of the
+    // launch is (group g, right block b = lo + q - item_first) of the group
+    // {g0, g1, lo, item_first} with the first item_first <= q, and its tiles
+    // are the left blocks a in [g0, min(g1, amax[b])) (those with include[a]
+    // set, if include is not null).  Within a group the right blocks stream
+    // while the group's left blocks stay in L2.
+    const int4 *groups;     // by item_first
+    int ngroups;
+    int n_items;
+    const int *amax;        // [right blocks]: left blocks whose smallest last SNP is below the block's largest first SNP
+    const uint8_t *include;
     int64_t S;
     int W0, Wt;
     const uint64_t *ltup;   // left tuples: SNP t in bits [16 t, 16 t + 16), NO_TUPLE for padding

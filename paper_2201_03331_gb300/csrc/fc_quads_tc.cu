@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
     __shared__ uint64_t bar_tfull[2], bar_tempty[2], bar_done;
     __shared__ uint32_t tmem_base_slot;
     __shared__ uint64_t bar_sfull[TC_SCHED], bar_sempty[TC_SCHED];
-    __shared__ int sched_tile[TC_SCHED];
+    __shared__ int sched_tile[TC_SCHED];   // left block (-1: no more tiles)
+    __shared__ int sched_rb[TC_SCHED];     // right block
     __shared__ int abort_flag_s;
     __shared__ int buf_count;
     __shared__ int epi_stop;
@@ -179,10 +180,10 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
                 if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err)) break;
                 const int t = sched_tile[slot];
+                const int rb = sched_rb[slot];
                 mbar_arrive(&bar_sempty[slot]);
                 if (t < 0) break;
-                const uint2 tile = a.tiles[t];
-                const int rowL = (int)tile.x * 128, rowR = (int)tile.y * 128;
+                const int rowL = t * 128, rowR = rb * 128;
                 for (int c = 0; c < 2 && ok; ++c) {
                     const int nk = c ? kc1 : kc0;
                     const int xbase = c ? kc0 * TC_BK : 0;
@@ -220,16 +221,52 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
             // delayed the MMA issue).
             int published = 0;
             bool sched_done = false;
+            // The strip being handed out: right block s_b, left blocks
+            // [s_a, s_aend); the group of the last item taken.
+            int s_b = 0, s_a = 0, s_aend = 0;
+            int s_first = 0, s_end = 0, s_lo = 0, s_g0 = 0, s_g1 = 0;
+            auto next_tile = [&](int &ta, int &tb) -> bool {
+                for (;;) {
+                    while (s_a < s_aend) {
+                        const int x = s_a++;
+                        if (!a.include || a.include[x]) {
+                            ta = x;
+                            tb = s_b;
+                            return true;
+                        }
+                    }
+                    const int q = atomicAdd(a.tile_counter, 1);
+                    if (q >= a.n_items) return false;
+                    if (q >= s_end) {
+                        // Items only grow: the group is this one or a later one.
+                        int lo = 0, hi = a.ngroups - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (a.groups[mid].w <= q) lo = mid; else hi = mid - 1;
+                        }
+                        const int4 gr = a.groups[lo];
+                        s_g0 = gr.x;
+                        s_g1 = gr.y;
+                        s_lo = gr.z;
+                        s_first = gr.w;
+                        s_end = lo + 1 < a.ngroups ? a.groups[lo + 1].w : a.n_items;
+                    }
+                    s_b = s_lo + (q - s_first);
+                    s_a = s_g0;
+                    s_aend = min(s_g1, a.amax[s_b]);
+                }
+            };
             auto publish = [&](int k) -> bool {
                 const int pslot = k % TC_SCHED;
                 const uint32_t psn = (uint32_t)(k / TC_SCHED);
                 if (!mbar_wait(&bar_sempty[pslot], (psn & 1) ^ 1, abort_flag, a.err)) return false;
-                int t = -1;
-                if (!sched_done) {
-                    t = atomicAdd(a.tile_counter, 1);
-                    if (t >= a.ntiles) { t = -1; sched_done = true; }
+                int ta = -1, tb = 0;
+                if (!sched_done && !next_tile(ta, tb)) {
+                    ta = -1;
+                    sched_done = true;
                 }
-                sched_tile[pslot] = t;
+                sched_tile[pslot] = ta;
+                sched_rb[pslot] = tb;
                 mbar_arrive(&bar_sfull[pslot]);
                 return true;
             };
@@ -290,6 +327,7 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
             const uint32_t sn = (uint32_t)(it / TC_SCHED);
             const bool ok = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err);
             const int t = ok ? sched_tile[slot] : -1;
+            const int rb = ok ? sched_rb[slot] : 0;
             if (ok) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_sempty[slot]);
@@ -304,7 +342,7 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
             epi_bar();
             if (epi_stop || t < 0) break;
             tc_fence_after();
-            const uint2 tile = a.tiles[t];
+            const uint2 tile = make_uint2((uint32_t)t, (uint32_t)rb);   // left block, right block
             // This lane's left tuple: its last SNP and its part of the rank.
             uint64_t ltp = NO_TUPLE, lrk = 0;
             if (p < LPQ) {

@@ -522,8 +522,6 @@ int Dataset::time_sweep(int k, const TuneConfig &cfg, int L, uint64_t n, float *
 
 // ---- order-2 tensor-core path --------------------------------------------------
 
-namespace {
-
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                    CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -578,8 +576,6 @@ int pow2_at_least(int v)
     while (p < v) p <<= 1;
     return p;
 }
-
-}  // namespace
 
 bool Dataset::pairs_tc_eligible(int L)
 {
@@ -787,16 +783,9 @@ namespace {
 // The last order-3 slab and tile plan; it depends on S, the pairs per tile
 // and the slab capacity only, so the phenotype replicates of one data set
 // (and data sets of equal S) share it.
-struct TriplePlan {
-    int64_t S = -1, cap_rows = -1, max_rows = 0;
-    int NP = 0;
-    std::vector<uint4> tiles;
-    std::vector<int64_t> first_tile;   // [S + 1]: tiles of first SNP i are [first_tile[i], first_tile[i + 1])
-    std::vector<int64_t> rowbase;      // [S]: first slab row of SNP i within its slab
-    std::vector<Dataset::TripleSlab> slabs;
-};
 std::mutex g_plan3_mu;
 std::shared_ptr<const TriplePlan> g_plan3;
+}  // namespace
 
 // Tiles {rowP, i, j0, l0}: first SNP i, the block of NP second SNPs from
 // j0 = i + 1 + NP J' (slab rows [rowP, rowP + 4 NP)), the 64 third SNPs from
@@ -851,7 +840,6 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_ro
     g_plan3 = pl;
     return pl;
 }
-}  // namespace
 
 // The e4m3 rows (those of the order-2 path, or a copy with controls = 64 for
 // the one-accumulator form), the inclusion-exclusion tables, the x ln x
@@ -1029,7 +1017,6 @@ int Dataset::triples_dense(float *scores, uint32_t *tables)
 // ---- orders 4-6 on tensor cores: tuple operands ---------------------------------
 
 namespace {
-constexpr int64_t TUP_MAX_TILES = (int64_t)1 << 25;
 
 // Left tuples (SNPs c_0 < .. < c_{LT-1} with c_{LT-1} <= S - 1 - RT) in order of
 // their last SNP, right tuples (c_0 >= LT) in lexicographic order; SNP t of a
@@ -1082,14 +1069,19 @@ bool Dataset::tuples_tc_eligible(int k, int L)
     const int64_t nl = tuple_count(S, LT, RT), nr = tuple_count(S, RT, LT);
     const int64_t bl = (nl + tc_tuples_per_block(LT) - 1) / tc_tuples_per_block(LT);
     const int64_t br = (nr + tc_tuples_per_block(RT) - 1) / tc_tuples_per_block(RT);
-    // Tiles: combinations over the combinations of a tile, plus the block
-    // diagonal; the list stays below 2^25 entries.
-    const double tiles = (double)binom(S, k) / (tc_tuples_per_block(LT) * tc_tuples_per_block(RT)) + (double)bl;
-    if (tiles > (double)TUP_MAX_TILES) return false;
+    // Block indices and strips (group, right block) are ints; the groups hold
+    // at least 16 left blocks.
+    if (bl >= ((int64_t)1 << 31) / 128 || br >= ((int64_t)1 << 31) / 128) return false;
+    if ((double)(bl / 16 + 1) * (double)br >= 2147483647.0) return false;
+    // Both slabs stay resident: at most 60 % of the free memory (FC_TUPLES_SLAB_MB caps it).
     const double slab = (double)(bl + br) * 128.0 * ((double)Wt * 128 + 128);
     size_t free_b = 0, total_b = 0;
-    double cap = 64.0 * 1024 * 1024 * 1024;
-    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, (double)free_b / 4);
+    double cap = 192.0 * 1024 * 1024 * 1024;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, 0.6 * (double)free_b);
+    if (const char *mb = getenv("FC_TUPLES_SLAB_MB")) {
+        const long v = atol(mb);
+        if (v > 0) cap = std::min(cap, (double)v * 1024 * 1024);
+    }
     if (!tup[k - 4].ready && slab > cap) return false;
     const int Bcap = std::max(L, 1024);
     const int P2 = pow2_at_least(L + Bcap);
@@ -1100,8 +1092,11 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
 {
     const TupleTC &u = tup[k - 4];
     QuadsArgs qa{};
-    qa.tiles = u.tiles;
-    qa.ntiles = (int)u.ntiles;
+    qa.groups = u.groups;
+    qa.ngroups = u.ngroups;
+    qa.n_items = (int)u.n_items;
+    qa.amax = u.amax;
+    qa.include = nullptr;
     qa.S = S;
     qa.W0 = W0;
     qa.Wt = Wt;
@@ -1129,7 +1124,7 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
 void Dataset::release_tuples(int k)
 {
     TupleTC &u = tup[k - 4];
-    if (!u.QL && !u.QR && !u.lt && !u.tiles) return;
+    if (!u.QL && !u.QR && !u.lt && !u.groups) return;
     if (stream) cudaStreamSynchronize(stream);
     dev_free_pooled(u.QL, u.ql_bytes, device);
     dev_free_pooled(u.QR, u.qr_bytes, device);
@@ -1137,39 +1132,46 @@ void Dataset::release_tuples(int k)
     cudaFree(u.lr);
     cudaFree(u.rt);
     cudaFree(u.rr);
-    cudaFree(u.tiles);
+    cudaFree(u.groups);
+    cudaFree(u.amax);
     u = TupleTC{};
 }
 
-// Tuples with their parts of the rank, the tile plan, slabs and descriptors.
+// Tuples with their parts of the rank, the strip plan, slabs and descriptors.
 // The lexicographic rank of (left, right) is the sum over positions t of
 // C(S - c_{t-1} - 1, k - t) - C(S - c_t, k - t) (c_{-1} = -1): the terms of
 // the left SNPs plus C(S - c_{LT-1} - 1, k - LT) go with the left tuple, the
-// rest with the right tuple (modulo 2^64).  Tiles come in groups of left
-// blocks that fit in about 48 MB of L2: for each right block with a usable
-// tuple (largest first SNP above the group's smallest last SNP) the group's
-// left blocks follow one another while the right blocks stream.
+// rest with the right tuple (modulo 2^64).  A tile (left block a, right
+// block b) holds combinations where some right tuple starts after some left
+// tuple ends: rmax[b] > lmin[a], i.e. a < amax[b] (left blocks come in order
+// of their smallest last SNP).  Tiles come in groups of left blocks that fit
+// in about 48 MB of L2: for each right block with a usable tuple the group's
+// left blocks follow one another while the right blocks stream, one strip
+// (group, right block) per scheduler item, so no tile list is stored.
 namespace {
-// Tiles (left block, right block) of the orders 4-6 tensor-core kernel:
-// left blocks in groups of `group` (a group's operands stay in L2 while the
-// right blocks stream), pairs where some right tuple starts after some left
-// tuple ends.  include: the left blocks to take (all if null).
-void tuple_tiles(int64_t group, const std::vector<int64_t> &lmin, const std::vector<int64_t> &rmax,
-                 const std::vector<char> *include, std::vector<uint2> &tiles)
+// Groups {g0, g1, lo, item_first} of `group` left blocks (those with some
+// include[a] set, if include is not null): lo is the first right block with
+// a tile in the group; the group's items are its right blocks lo .. br - 1.
+int64_t tuple_groups(int64_t group, int64_t bl, const std::vector<int> &amax, const std::vector<char> *include,
+                     std::vector<int4> &groups)
 {
-    const int64_t bl = (int64_t)lmin.size(), br = (int64_t)rmax.size();
+    groups.clear();
+    const int64_t br = (int64_t)amax.size();
+    int64_t items = 0;
     for (int64_t g0 = 0; g0 < bl; g0 += group) {
         const int64_t g1 = std::min(bl, g0 + group);
-        int64_t lo = 0, hi = br;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) / 2;
-            if (rmax[(size_t)mid] > lmin[(size_t)g0]) hi = mid; else lo = mid + 1;
+        if (include) {
+            bool any = false;
+            for (int64_t a = g0; a < g1 && !any; ++a) any = (*include)[(size_t)a] != 0;
+            if (!any) continue;
         }
-        for (int64_t b = lo; b < br; ++b)
-            for (int64_t a = g0; a < g1; ++a)
-                if ((!include || (*include)[(size_t)a]) && rmax[(size_t)b] > lmin[(size_t)a])
-                    tiles.push_back(make_uint2((uint32_t)a, (uint32_t)b));
+        // First right block b with amax[b] > g0 (amax is nondecreasing).
+        const int64_t lo = std::upper_bound(amax.begin(), amax.end(), (int)g0) - amax.begin();
+        if (lo >= br) continue;
+        groups.push_back(make_int4((int)g0, (int)g1, (int)lo, (int)items));
+        items += br - lo;
     }
+    return items;
 }
 }  // namespace
 
@@ -1230,10 +1232,14 @@ int Dataset::prepare_tuples(int k)
     // ~48 MB of left blocks per group: about a third of L2 (two dies share
     // the 129 MB), so the group stays resident while the right blocks stream.
     u.group = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((48ull << 20) / (128 * pitch))));
-    std::vector<uint2> tiles;
-    tuple_tiles(u.group, u.lmin_host, u.rmax_host, nullptr, tiles);
-    if ((int64_t)tiles.size() > TUP_MAX_TILES) return set_error(FC_ERANGE, "tensor-core tile plan too large");
-    u.ntiles = (int64_t)tiles.size();
+    std::vector<int> &amax = u.amax_host;
+    amax.resize((size_t)br);
+    for (int64_t b = 0; b < br; ++b)
+        amax[(size_t)b] = (int)(std::lower_bound(u.lmin_host.begin(), u.lmin_host.end(), u.rmax_host[(size_t)b]) -
+                                u.lmin_host.begin());
+    u.n_items = tuple_groups(u.group, bl, amax, nullptr, u.groups_host);
+    if (u.n_items >= ((int64_t)1 << 31)) return set_error(FC_ERANGE, "tensor-core strip plan too large");
+    u.ngroups = (int)u.groups_host.size();
     u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
     u.qr_bytes = std::max<size_t>((size_t)br * 128 * pitch, 1);
     if ((e = dev_alloc_pooled((void **)&u.QL, u.ql_bytes, device)) != cudaSuccess ||
@@ -1243,13 +1249,15 @@ int Dataset::prepare_tuples(int k)
         (e = dev_alloc((void **)&u.lr, sizeof(uint64_t) * std::max<size_t>(lr.size(), 1))) != cudaSuccess ||
         (e = dev_alloc((void **)&u.rt, sizeof(uint64_t) * std::max<size_t>(rt.size(), 1))) != cudaSuccess ||
         (e = dev_alloc((void **)&u.rr, sizeof(uint64_t) * std::max<size_t>(rr.size(), 1))) != cudaSuccess ||
-        (e = dev_alloc((void **)&u.tiles, sizeof(uint2) * std::max<size_t>(tiles.size(), 1))) != cudaSuccess)
+        (e = dev_alloc((void **)&u.groups, sizeof(int4) * std::max<size_t>(u.groups_host.size(), 1))) != cudaSuccess ||
+        (e = dev_alloc((void **)&u.amax, sizeof(int) * std::max<size_t>(amax.size(), 1))) != cudaSuccess)
         return cuda_status(e, "tuple lists");
     cudaMemcpyAsync(u.lt, lt.data(), sizeof(uint64_t) * lt.size(), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(u.lr, lr.data(), sizeof(uint64_t) * lr.size(), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(u.rt, rt.data(), sizeof(uint64_t) * rt.size(), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(u.rr, rr.data(), sizeof(uint64_t) * rr.size(), cudaMemcpyHostToDevice, stream);
-    cudaMemcpyAsync(u.tiles, tiles.data(), sizeof(uint2) * tiles.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(u.groups, u.groups_host.data(), sizeof(int4) * u.groups_host.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(u.amax, amax.data(), sizeof(int) * amax.size(), cudaMemcpyHostToDevice, stream);
     if ((e = launch_gate()) != cudaSuccess ||
         (e = launch_tuple_rows(LT, X, S_pad, Wt, u.lt, bl, (int64_t)pitch, u.QL, stream)) != cudaSuccess ||
         (e = launch_tuple_rows(RT, X, S_pad, Wt, u.rt, br, (int64_t)pitch, u.QR, stream)) != cudaSuccess)
@@ -1293,8 +1301,8 @@ int Dataset::tuples_dense(int k, float *scores, uint32_t *tables)
     if (ns) cudaMemsetAsync(qa.dump_scores, 0, ns, stream);
     if (nt) cudaMemsetAsync(qa.dump_tables, 0, nt, stream);
     const TupleTC &u = tup[k - 4];
-    if (u.ntiles > 0) {
-        const int grid = (int)std::min<int64_t>(sms, u.ntiles);
+    if (u.n_items > 0) {
+        const int grid = (int)std::min<int64_t>(sms, u.n_items);
         if ((e = launch_gate()) != cudaSuccess ||
             (e = launch_quads_tc(k, MODE_DUMP, u.tmapL, u.tmapR, qa, grid, stream)) != cudaSuccess)
             return cuda_status(e, "tensor-core tuple kernel");
@@ -1354,7 +1362,10 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         TriplesArgs ta{};
         QuadsArgs qa{};
         std::vector<uint32_t> range_tiles;   // order 2, rank range: the tiles of its row blocks
-        std::vector<uint2> range_tiles4;     // orders 4-6, rank range: the tiles of its left blocks
+        // Orders 4-6, rank range: the groups with a left block of the range
+        // and the left blocks to take.
+        std::vector<int4> range_groups4;
+        std::vector<char> include4;
         struct SlabLaunch { int si; int64_t t0, t1; };
         std::vector<SlabLaunch> launches3;
         int grid = 0;
@@ -1393,11 +1404,12 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             int rc = prepare_tuples(k);
             if (rc) return rc;
             qa = tuples_args(k, L, (float)hy, (float)(1.0 / Nd));
-            int64_t nt = tup[k - 4].ntiles;
+            int64_t nt = tup[k - 4].n_items;
             if (!whole) {
                 const TupleTC &u = tup[k - 4];
                 const int LT = tc_left_size(k), LPB = tc_tuples_per_block(LT);
-                std::vector<char> include(u.lmin_host.size(), 0);
+                std::vector<char> &include = include4;
+                include.assign(u.lmin_host.size(), 0);
                 for (size_t x = 0; x < u.lt_host.size(); ++x) {
                     const uint64_t t = u.lt_host[x];
                     if (t == NO_TUPLE) continue;
@@ -1412,9 +1424,9 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                     const uint64_t first = rank_of(S, k, c);
                     if (first < r1 && first + count > r0) include[x / (size_t)LPB] = 1;
                 }
-                tuple_tiles(u.group, u.lmin_host, u.rmax_host, &include, range_tiles4);
-                nt = (int64_t)range_tiles4.size();
-                qa.ntiles = (int)nt;
+                nt = tuple_groups(u.group, (int64_t)u.lmin_host.size(), u.amax_host, &include, range_groups4);
+                qa.n_items = (int)nt;
+                qa.ngroups = (int)range_groups4.size();
                 qa.rank_begin = r0;
                 qa.rank_end = r1;
             }
@@ -1445,7 +1457,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             p[9] = A.take(sizeof(uint32_t) * (size_t)N * k);
             p[10] = A.take(sizeof(double) * (size_t)N);
             p[11] = A.take(sizeof(int) * 4);
-            p[12] = A.take(sizeof(uint32_t) * range_tiles.size() + sizeof(uint2) * range_tiles4.size());
+            p[12] = A.take(sizeof(uint32_t) * range_tiles.size() + sizeof(int4) * range_groups4.size() +
+                           include4.size() + 16);
         };
         void *p[13];
         plan(ar, p);
@@ -1502,10 +1515,15 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             qa.gthr = (int *)p[11];
             qa.tile_counter = (int *)p[11] + 1;
             qa.err = err;
-            if (!range_tiles4.empty()) {
-                cudaMemcpyAsync(p[12], range_tiles4.data(), sizeof(uint2) * range_tiles4.size(),
-                                cudaMemcpyHostToDevice, stream);
-                qa.tiles = (const uint2 *)p[12];
+            if (!whole) {
+                int4 *dg = (int4 *)p[12];
+                uint8_t *di = (uint8_t *)(dg + range_groups4.size());
+                if (!range_groups4.empty())
+                    cudaMemcpyAsync(dg, range_groups4.data(), sizeof(int4) * range_groups4.size(),
+                                    cudaMemcpyHostToDevice, stream);
+                cudaMemcpyAsync(di, include4.data(), include4.size(), cudaMemcpyHostToDevice, stream);
+                qa.groups = dg;
+                qa.include = di;
             }
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
             cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);

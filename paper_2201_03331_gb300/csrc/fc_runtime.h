@@ -29,6 +29,11 @@ void fault_counters_reset();
 int check_device(int *dev, int *sms);
 int list_capacity(int64_t N);
 float score_error_bound(int k, int64_t M);
+int pow2_at_least(int v);
+// 2-D TMA descriptor over bytes: rows of inner_bytes (pitch apart), boxes of
+// 128 bytes x box_rows.
+int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t pitch, uint64_t rows,
+                   uint32_t box_rows, bool swizzle128);
 
 struct DeviceGuard {
     int prev = 0;
@@ -115,14 +120,19 @@ struct Dataset {
 
     // Tensor-core operands of orders 4-6, built on first use; one order's are
     // kept at a time: left and right tuple-row slabs (all 3^T genotype rows,
-    // 128-row blocks), the tuples with their parts of the rank, the tile list
-    // (left block, right block) and the slabs' TMA descriptors.
+    // 128-row blocks), the tuples with their parts of the rank, the strip
+    // plan of the tiles (left block, right block) and the slabs' TMA
+    // descriptors.
     struct TupleTC {
         uint8_t *QL = nullptr, *QR = nullptr;
         size_t ql_bytes = 0, qr_bytes = 0;
         uint64_t *lt = nullptr, *lr = nullptr, *rt = nullptr, *rr = nullptr;
-        uint2 *tiles = nullptr;
-        int64_t ntiles = 0;
+        int4 *groups = nullptr;    // {g0, g1, lo, item_first} per group of left blocks
+        int *amax = nullptr;       // [right blocks]
+        int ngroups = 0;
+        int64_t n_items = 0;       // strips (group, right block)
+        std::vector<int4> groups_host;
+        std::vector<int> amax_host;
         CUtensorMap tmapL{}, tmapR{};
         bool ready = false;
         // Host copies for rank-range searches: the left tuples, each left
@@ -208,6 +218,67 @@ TuneConfig tuned_config(Dataset &d, int k, int L, const TuneConfig &fallback, bo
 int sweep_candidates(const Dataset &d, int k, int L, int mode, int var, TuneConfig *out, int max_out);
 
 // Many data sets (x phenotype replicates) searched by one persistent launch.
+// Order-3 tile plan of one SNP count: tiles {rowP, i, j0, l0} (first SNP i,
+// the NP second SNPs from j0, the 64 third SNPs from l0), in order of i, and
+// the slabs of pair rows that hold at most cap_rows rows each.
+struct TriplePlan {
+    int64_t S = -1, cap_rows = -1, max_rows = 0;
+    int NP = 0;
+    std::vector<uint4> tiles;
+    std::vector<int64_t> first_tile;   // [S + 1]: tiles of first SNP i are [first_tile[i], first_tile[i + 1])
+    std::vector<int64_t> rowbase;      // [S]: first slab row of SNP i within its slab
+    std::vector<Dataset::TripleSlab> slabs;
+};
+std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_rows);
+
+// The batched order-3 tensor-core form: one persistent launch per group of
+// data sets whose pair-row slabs fit the slab buffer together, every
+// replicate of a data set a job of the launch (T3Job).
+struct Tc3Batch {
+    struct Launch {
+        int j0 = 0, j1 = 0;          // jobs (slots) [j0, j1)
+        int enc = 1, n_items = 0;
+        int M = 0;                   // largest sample count (x ln x table size)
+        std::vector<int> sets;       // data sets whose slabs this launch reads
+    };
+    struct Set {
+        int first_job = 0;           // job index of its first replicate
+        int enc = 1, split = 0, NP = 64;
+        int64_t M = 0;
+        int64_t rows = 0, pitch = 0, slab_rows = 0;
+        size_t slab_off = 0;         // within the slab buffer
+        int64_t tile_off = 0, ntiles = 0, rowbase_off = 0;
+    };
+    std::vector<Set> sets;
+    std::vector<Launch> launches;
+    std::vector<int> slot_job;       // job index of every slot
+    int n = 0, L = 0, grid = 0;
+    int level1 = 0, F = 0;           // two-level merge: groups of F lists per job
+    bool rebuild = false;            // slabs rebuilt before every launch (several groups)
+    std::vector<void *> allocs;      // device allocations of the plan
+    uint8_t *slab = nullptr;
+    uint8_t *E = nullptr;            // per data set: genotype rows (e5m2 1.0)
+    int64_t *rowbase = nullptr;
+    std::vector<size_t> e_off;       // per data set, within E
+    T3Job *d_jobs = nullptr;
+    CUtensorMap *d_maps = nullptr;
+    JobDesc *d_desc = nullptr, *d_desc1 = nullptr;
+    int *d_gthr = nullptr, *d_counter = nullptr;
+    float *list_s = nullptr, *mid_s = nullptr, *job_s = nullptr;
+    uint64_t *list_r = nullptr, *mid_r = nullptr, *job_r = nullptr;
+    float *xlogx = nullptr;
+    int M = 0;
+    double *res_s = nullptr, *out_score = nullptr;
+    uint64_t *res_r = nullptr;
+    uint32_t *res_tab = nullptr, *job_err = nullptr, *out_idx = nullptr;
+    std::vector<JobDesc> desc;
+    void *host = nullptr;
+    uint32_t *h_idx = nullptr, *h_err = nullptr;
+    double *h_score = nullptr;
+    void release();
+    ~Tc3Batch() { release(); }
+};
+
 struct BatchState {
     int n_data = 0, R = 0;
     int64_t max_M = 0;
@@ -242,6 +313,12 @@ struct BatchState {
     std::vector<int> sel;
     std::vector<char> tc;
     std::vector<int> job_kind;
+    // The phenotypes of every data set as loaded (R x M bytes each): the
+    // batched tensor-core form lays the replicates of a data set out in the
+    // sample order of its first one.
+    std::vector<std::vector<uint8_t>> ph;
+    std::unique_ptr<Tc3Batch> tc3;   // order 3: the batched tensor-core jobs (null if none)
+    std::vector<int> tc3_slot;       // slot of each job in tc3, or -1
     ~BatchState();
     void release_plan();
 };

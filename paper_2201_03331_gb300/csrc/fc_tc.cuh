@@ -122,6 +122,13 @@ __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with both operands e4m3 or both e5m2 (A and B type fields,
+// bits 7-9 and 10-12: 0 = E4M3, 1 = E5M2).
+__host__ __device__ constexpr uint32_t idesc_f8_f32(int M, int N, bool e5m2)
+{
+    return idesc_e4m3_f32(M, N) | (e5m2 ? (1u << 7) | (1u << 10) : 0u);
+}
+
 __device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate)
 {

@@ -63,6 +63,8 @@
 //                list), four warps per TMEM lane quarter, each taking every
 //                fourth group of 4 pairs (an equal share of a tile's 16 or 8
 //                groups)
+#include <algorithm>
+
 #include "fc_tc.cuh"
 #include "fc_ie.cuh"
 
@@ -81,7 +83,7 @@ static_assert(T3_EPI_WARP0 % 4 == 0, "epilogue warp w reads TMEM lane quarter w 
 
 template <int ENC>
 struct T3Shape {
-    static constexpr int NP = ENC ? 64 : 32;              // SNPs j (pairs) per tile
+    static constexpr int NP = ENC == 1 ? 64 : 32;         // SNPs j (pairs) per tile
     static constexpr int RROWS = 2 * NP;                   // raw rows 2 j + b
     static constexpr int NMMA = 2 * RROWS;                 // pair rows = MMA N
     static constexpr uint32_t B_BYTES = (uint32_t)NMMA * TC_BK;
@@ -129,10 +131,13 @@ __device__ __forceinline__ uint32_t unpack_enc(uint32_t bits)
     return v + (v >> 12) * 61440u;
 }
 
-template <int MODE, int ENC>
+// BATCH: the items of several jobs (T3Job), job-major, in one launch; the
+// operands are e5m2 with the class weight on the SNP rows only.
+template <int MODE, int ENC, bool BATCH>
 __global__ void __launch_bounds__(T3_THREADS, 1)
     k_triples_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapP, TriplesArgs a)
 {
+    static_assert(BATCH ? (ENC == 1 || ENC == 2) && MODE == MODE_TOPN : ENC <= 1, "forms of the two launch kinds");
     using Sh = T3Shape<ENC>;
     constexpr int NP = Sh::NP;
     extern __shared__ uint8_t smem_raw[];
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     __shared__ uint32_t tmem_base_slot;
     __shared__ uint64_t bar_sfull[TC_SCHED], bar_sempty[TC_SCHED];
     __shared__ int sched_tile[TC_SCHED];
+    __shared__ int sched_job[TC_SCHED];
     __shared__ int abort_flag_s;
     __shared__ int buf_count;
     __shared__ int epi_stop;
@@ -205,28 +211,40 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         uint32_t fill = 0;
         uint32_t issued = 0, last_n = 0;
         bool ok = true;
+        const CUtensorMap *mapA = &tmapA, *mapP = &tmapP;
+        const uint4 *tiles = a.tiles;
+        int Wt = a.Wt, cur_job = -1;
         for (int it = 0; ok; ++it) {
             const int slot = it % TC_SCHED;
             const uint32_t sn = (uint32_t)(it / TC_SCHED);
             if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt)) break;
             const int t = sched_tile[slot];
+            const int job = sched_job[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_sempty[slot]);
             if (t < 0) break;
+            if (BATCH && job != cur_job) {
+                cur_job = job;
+                const T3Job *jb = a.jobs + job;
+                mapA = jb->tmapA;
+                mapP = jb->tmapP;
+                tiles = jb->tiles;
+                Wt = jb->Wt;
+            }
             if (lane != 0) {
-                fill += (uint32_t)a.Wt;
+                fill += (uint32_t)Wt;
                 continue;
             }
-            const uint4 tile = a.tiles[t];
+            const uint4 tile = tiles[t];
             const int rowP = (int)tile.x, l0 = (int)tile.w;
-            for (int kc = 0; kc < a.Wt; ++kc, ++fill) {
+            for (int kc = 0; kc < Wt; ++kc, ++fill) {
                 if ((int)(fill % T3_LOADERS) != w) continue;
                 const uint32_t n = fill / T3_LOADERS;
                 if (!mbar_wait(&bar_empty[w], (n & 1) ^ 1, abort_flag, a.err, wt)) { ok = false; break; }
                 const int x = kc * TC_BK;
                 mbar_expect_tx(&bar_full[w], Sh::STAGE);
-                tma_load_2d(&tmapA, &bar_full[w], st, x, 2 * l0);
-                tma_load_2d(&tmapP, &bar_full[w], st + TC_A_BYTES, x, rowP);
+                tma_load_2d(mapA, &bar_full[w], st, x, 2 * l0);
+                tma_load_2d(mapP, &bar_full[w], st + TC_A_BYTES, x, rowP);
                 ++issued;
                 last_n = n;
             }
@@ -240,9 +258,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     } else if (warp == 3) {
         if (lane == 0) {
             // ---------------- MMA issue ----------------
-            const uint32_t idesc = idesc_e4m3_f32(TC_BM, Sh::NMMA);
+            const uint32_t idesc = idesc_f8_f32(TC_BM, Sh::NMMA, BATCH);
             uint32_t fill = 0;
             bool ok = true;
+            int Wt = a.Wt, split = a.W0, cur_job = -1;
+            // Scheduler state of a batched launch: the job of the last item
+            // taken and its items [s_first, s_end); items only grow.
+            int s_job = -1, s_first = 0, s_end = 0;
+            const int n_items = BATCH ? a.n_items : a.ntiles;
             // This thread also schedules the tiles, TC_LOOKAHEAD ahead of the
             // one it consumes (another lane of this warp spinning on the ring
             // delayed the MMA issue).
@@ -255,9 +278,26 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 int t = -1;
                 if (!sched_done) {
                     t = atomicAdd(a.tile_counter, 1);
-                    if (t >= a.ntiles) { t = -1; sched_done = true; }
+                    if (t >= n_items) {
+                        t = -1;
+                        sched_done = true;
+                    } else if (BATCH) {
+                        if (t >= s_end) {
+                            // The last job whose first item is at most t.
+                            int lo = s_job < 0 ? 0 : s_job, hi = a.n_jobs - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (a.jobs[mid].item_first <= t) lo = mid; else hi = mid - 1;
+                            }
+                            s_job = lo;
+                            s_first = a.jobs[lo].item_first;
+                            s_end = s_first + a.jobs[lo].ntiles;
+                        }
+                        t -= s_first;
+                    }
                 }
                 sched_tile[pslot] = t;
+                sched_job[pslot] = s_job;
                 mbar_arrive(&bar_sfull[pslot]);
                 return true;
             };
@@ -268,13 +308,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 const uint32_t sn = (uint32_t)(it / TC_SCHED);
                 if (!mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt)) break;
                 const int t = sched_tile[slot];
+                const int job = sched_job[slot];
                 mbar_arrive(&bar_sempty[slot]);
                 if (t < 0) break;
+                if (BATCH && job != cur_job) {
+                    cur_job = job;
+                    Wt = a.jobs[job].Wt;
+                    split = a.jobs[job].split;
+                }
                 const int b = it & 1;
                 const uint32_t u = (uint32_t)(it >> 1);
                 if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err, wt)) break;
                 tc_fence_after();
-                for (int kc = 0; kc < a.Wt; ++kc, ++fill) {
+                for (int kc = 0; kc < Wt; ++kc, ++fill) {
                     const int s = (int)(fill % T3_LOADERS);
                     const uint32_t n = fill / T3_LOADERS;
                     if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err, wt)) {
@@ -282,9 +328,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const bool cls1 = !ENC && kc >= a.W0;
-                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + (cls1 ? 128 : 0));
-                    const bool first = ENC ? kc == 0 : (kc == 0 || kc == a.W0);
+                    // ENC 0: controls, ENC 2: the chunks from split, into
+                    // the second accumulator.
+                    const bool acc1 = ENC != 1 && kc >= split;
+                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + (acc1 ? 128 : 0));
+                    const bool first = ENC == 1 ? kc == 0 : (kc == 0 || kc == split);
                     const uint32_t aaddr = smem_u32(smem + (size_t)s * Sh::STAGE);
                     const uint32_t baddr = aaddr + TC_A_BYTES;
 #pragma unroll
@@ -313,8 +361,16 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         const int g = row & 1;
         const int L = a.L;
         const uint32_t tmask = (uint32_t)lt_floats - 1;
-        const int64_t Sp = a.S_pad;
-        const bool whole = a.rank_begin == 0 && a.rank_end >= a.total;
+        // The data set and job of the tile (a batched launch reloads them
+        // when the job changes).
+        int64_t S = a.S, Sp = a.S_pad;
+        uint64_t total = a.total;
+        float hy = a.hy, invN = a.invN;
+        const uint4 *marg4 = a.marg4, *PR = a.PR;
+        int pjob = -1, pslot = 0;
+        // The job whose candidates the list holds.
+        int ljob = -1, lslot = 0;
+        const bool whole = BATCH || (a.rank_begin == 0 && a.rank_end >= a.total);
         // A round inserts at most 2 candidates per thread.  Every
         // a.check_rounds rounds (and at the start of each tile) the threads
         // read the buffer's fill between two barriers, where nobody inserts,
@@ -334,15 +390,28 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
             if (tid == 0) {
                 buf_count = 0;
-                if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr, ordered_int(lscore[L - 1]));
+                if (lrank[L - 1] != NO_RANK) atomicMax(a.gthr + lslot, ordered_int(lscore[L - 1]));
             }
             epi_bar_n<T3_EPI_THREADS>();
+        };
+        // The list's final order, written out as list lslot of this CTA.
+        auto flush = [&]() {
+            epi_bar_n<T3_EPI_THREADS>();
+            const int nb = min(buf_count, a.Bcap);
+            for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
+            epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
+            const size_t o = ((size_t)lslot * gridDim.x + blockIdx.x) * L;
+            for (int x = tid; x < L; x += T3_EPI_THREADS) {
+                a.list_score[o + x] = lscore[x];
+                a.list_rank[o + x] = lrank[x];
+            }
         };
         for (int it = 0;; ++it) {
             const int slot = it % TC_SCHED;
             const uint32_t sn = (uint32_t)(it / TC_SCHED);
             const bool okw = mbar_wait(&bar_sfull[slot], sn & 1, abort_flag, a.err, wt);
             const int t = okw ? sched_tile[slot] : -1;
+            const int job = okw ? sched_job[slot] : -1;
             if (okw) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_sempty[slot]);
@@ -355,51 +424,84 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             uint32_t Tl[3] = {0, 0, 0}, T02[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             bool lv = false;
             uint32_t *sJb = sJ + (size_t)b * NP * T3_SJ_WORDS;
+            const uint4 *tiles = a.tiles;
+            if (BATCH && t >= 0) {
+                const T3Job *jb = a.jobs + job;
+                tiles = jb->tiles;
+                if (job != pjob) {
+                    pjob = job;
+                    S = jb->S;
+                    Sp = jb->S_pad;
+                    total = jb->total;
+                    hy = jb->hy;
+                    invN = jb->invN;
+                    marg4 = jb->marg4;
+                    PR = jb->PR;
+                    pslot = jb->slot;
+                }
+            }
             if (t >= 0) {
-                const uint4 tile = a.tiles[t];
+                const uint4 tile = tiles[t];
                 const int64_t i = tile.y;
                 j0 = tile.z;
                 l = (int64_t)tile.w + l_loc;
-                lv = l < a.S;
-                const int64_t lc = lv ? l : a.S - 1;
+                lv = l < S;
+                const int64_t lc = lv ? l : S - 1;
                 uint32_t Ti[3];
-                unpack_marg(a.marg4[i], Ti);
-                unpack_marg(a.marg4[lc], Tl);
-                const uint4 p4 = a.PR[(size_t)i * Sp + lc];
+                unpack_marg(marg4[i], Ti);
+                unpack_marg(marg4[lc], Tl);
+                const uint4 p4 = PR[(size_t)i * Sp + lc];
                 const uint32_t R[4] = {p4.x, p4.y, p4.z, p4.w};
                 full2(R, Ti, Tl, T02);
                 // The tables of the tile's SNPs j, one thread per j.
                 if (tid < NP) {
                     const int64_t j = j0 + tid;
-                    const int64_t jc = j < a.S ? j : a.S - 1;
+                    const int64_t jc = j < S ? j : S - 1;
                     uint32_t Tj[3], T01[9];
-                    unpack_marg(a.marg4[jc], Tj);
-                    const uint4 q4 = a.PR[(size_t)i * Sp + jc];
+                    unpack_marg(marg4[jc], Tj);
+                    const uint4 q4 = PR[(size_t)i * Sp + jc];
                     const uint32_t Rq[4] = {q4.x, q4.y, q4.z, q4.w};
                     full2(Rq, Ti, Tj, T01);
                     // rank of (i, j, l) = base_i - C(S - j, 2) + l - j - 1
-                    const uint64_t base_i = a.total - c3((uint64_t)(a.S - i)) + c2((uint64_t)(a.S - i - 1));
-                    const uint64_t rb = base_i - c2((uint64_t)(a.S - jc)) - (uint64_t)jc - 1;
+                    const uint64_t base_i = total - c3((uint64_t)(S - i)) + c2((uint64_t)(S - i - 1));
+                    const uint64_t rb = base_i - c2((uint64_t)(S - jc)) - (uint64_t)jc - 1;
                     uint4 *rec = reinterpret_cast<uint4 *>(sJb + (size_t)tid * T3_SJ_WORDS);
                     rec[0] = make_uint4(T01[0], T01[1], T01[2], T01[3]);
                     rec[1] = make_uint4(T01[4], T01[5], T01[6], T01[7]);
                     rec[2] = make_uint4(T01[8], Tj[0], Tj[1], Tj[2]);
-                    rec[3] = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), j < a.S ? 1u : 0u, 0u);
+                    rec[3] = make_uint4((uint32_t)rb, (uint32_t)(rb >> 32), j < S ? 1u : 0u, 0u);
                 }
                 mbar_wait(&bar_tfull[b], u & 1, abort_flag, a.err, wt);
             }
             // The global threshold only rises; a value read once per tile
             // admits at most a few more candidates than a fresh one would.
-            const float gthr = MODE == MODE_TOPN ? from_ordered(*(volatile int *)a.gthr) : -FLT_MAX;
+            const float gthr = MODE == MODE_TOPN ? from_ordered(*(volatile int *)(a.gthr + (BATCH ? pslot : 0))) : -FLT_MAX;
             // One stop decision for all epilogue warps (they meet at named
             // barriers, which have no timeout); t is the same for all.  The
             // barrier also publishes the tables of the SNPs j, and between
             // the two barriers the buffer's fill is the same for all.
             epi_bar_n<T3_EPI_THREADS>();
             if (tid == 0) epi_stop = *abort_flag;
-            const int fill0 = buf_count;
+            int fill0 = buf_count;
             epi_bar_n<T3_EPI_THREADS>();
             if (epi_stop || t < 0) break;
+            if (BATCH && job != ljob) {
+                // A new job: the list of the last one goes out, and the list
+                // starts empty (uniform: every epilogue warp sees the same
+                // items).
+                if (ljob >= 0) {
+                    flush();
+                    for (int x = tid; x < a.P2; x += T3_EPI_THREADS) {
+                        lscore[x] = -FLT_MAX;
+                        lrank[x] = NO_RANK;
+                    }
+                    if (tid == 0) buf_count = 0;
+                    epi_bar_n<T3_EPI_THREADS>();
+                    fill0 = 0;
+                }
+                ljob = job;
+                lslot = pslot;
+            }
             if (MODE == MODE_TOPN) {
                 if (fill0 > a.Bcap - headroom) merge();
                 thr_s = lscore[L - 1];
@@ -407,13 +509,13 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            const int64_t lc = lv ? l : a.S - 1;
+            const int64_t lc = lv ? l : S - 1;
             // Pair-table entries PR[j][l] of the first group, then one group ahead.
             uint4 pjl[2], pjl_next[2];
 #pragma unroll
             for (int m = 0; m < 2; ++m) {
-                const int64_t jj = min(j0 + part * 4 + 2 * m + g, a.S - 1);
-                pjl_next[m] = a.PR[(size_t)jj * Sp + lc];
+                const int64_t jj = min(j0 + part * 4 + 2 * m + g, S - 1);
+                pjl_next[m] = PR[(size_t)jj * Sp + lc];
             }
             // Every warp runs the same number of rounds (a round without a
             // group scores nothing), because each round meets at a barrier.
@@ -433,8 +535,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 if (qd + T3_PARTS < Sh::QUADS) {
 #pragma unroll
                     for (int m = 0; m < 2; ++m) {
-                        const int64_t jj = min(j0 + (qd + T3_PARTS) * 4 + 2 * m + g, a.S - 1);
-                        pjl_next[m] = a.PR[(size_t)jj * Sp + lc];
+                        const int64_t jj = min(j0 + (qd + T3_PARTS) * 4 + 2 * m + g, S - 1);
+                        pjl_next[m] = PR[(size_t)jj * Sp + lc];
                     }
                 }
                 // This lane's cells (genotype g of SNP l) for the group's 4
@@ -445,7 +547,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 if (has) {
                     const uint32_t c0 = (uint32_t)(8 * qd);            // a = 0: columns 2 q + b
                     const uint32_t c1 = (uint32_t)(2 * NP + 8 * qd);   // a = 1
-                    if (ENC) {
+                    if (ENC == 1) {
                         uint32_t v0[8], v1[8];
                         tmem_ld8(taddr + c0, v0);
                         tmem_ld8(taddr + c1, v1);
@@ -474,8 +576,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         for (int q = 0; q < 4; ++q)
 #pragma unroll
                             for (int bb = 0; bb < 2; ++bb) {
-                                cell[4 * q + bb] = pack_exact(v0[2 * q + bb], w0[2 * q + bb]);
-                                cell[4 * q + 2 + bb] = pack_exact(v1[2 * q + bb], w1[2 * q + bb]);
+                                if (ENC == 0) {
+                                    cell[4 * q + bb] = pack_exact(v0[2 * q + bb], w0[2 * q + bb]);
+                                    cell[4 * q + 2 + bb] = pack_exact(v1[2 * q + bb], w1[2 * q + bb]);
+                                } else {
+                                    // Two encoded parts; each class sum stays below 2^16.
+                                    cell[4 * q + bb] = unpack_enc(v0[2 * q + bb]) + unpack_enc(w0[2 * q + bb]);
+                                    cell[4 * q + 2 + bb] = unpack_enc(v1[2 * q + bb]) + unpack_enc(w1[2 * q + bb]);
+                                }
                             }
                     }
                     if (qd + T3_PARTS >= Sh::QUADS) {
@@ -533,7 +641,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                         }
                         hsum = (hs[0] + hs[1]) + hs[2];
                     }
-                    const float score = fmaf(-hsum, a.invN, a.hy);
+                    const float score = fmaf(-hsum, invN, hy);
                     const uint64_t rank = valid ? rank0 : NO_RANK;
                     sc[m] = score;
                     rk[m] = rank;
@@ -565,16 +673,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                 }
             }
         }
-        if (MODE == MODE_TOPN) {
-            epi_bar_n<T3_EPI_THREADS>();
-            const int nb = min(buf_count, a.Bcap);
-            for (int x = L + nb + tid; x < a.P2; x += T3_EPI_THREADS) { lscore[x] = -FLT_MAX; lrank[x] = NO_RANK; }
-            epi_bitonic_desc_n<T3_EPI_THREADS>(lscore, lrank, a.P2, tid);
-            for (int x = tid; x < L; x += T3_EPI_THREADS) {
-                a.list_score[(size_t)blockIdx.x * L + x] = lscore[x];
-                a.list_rank[(size_t)blockIdx.x * L + x] = lrank[x];
-            }
-        }
+        // The last list (a batched launch: of the last job this CTA took;
+        // its lists of jobs it never took stay as filled before the launch).
+        if (MODE == MODE_TOPN && (!BATCH || ljob >= 0)) flush();
     }
 
     tc_fence_before();
@@ -587,17 +688,17 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 }
 
 template <int ENC>
-size_t smem_bytes_enc(int M, int P2)
+size_t smem_bytes_enc(int M, int P2)   // ENC 2 has the shape of ENC 0
 {
     using Sh = T3Shape<ENC>;
     return 1024 + (size_t)T3_LOADERS * Sh::STAGE + (size_t)xl_table_size(M) * 4 + (size_t)P2 * (8 + 4) +
            (size_t)2 * Sh::NP * T3_SJ_WORDS * 4;
 }
 
-template <int MODE, int ENC>
+template <int MODE, int ENC, bool BATCH>
 void *kernel_ptr()
 {
-    return reinterpret_cast<void *>(&k_triples_tc<MODE, ENC>);
+    return reinterpret_cast<void *>(&k_triples_tc<MODE, ENC, BATCH>);
 }
 
 // Pair rows of the first SNPs [i0, i1): thread (i - i0, t), t over the
@@ -635,13 +736,80 @@ __global__ void k_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, 
     put(1, 1, a1, b1);
 }
 
+// Rows of the batched form from a bit table X in the sample order of a data
+// set's first replicate: row 2 s + g, byte b of chunk w is e5m2 1.0 (0x3C)
+// where sample 128 w + b carries genotype g of SNP s, or 4096.0 (0x6C) where
+// it is also a control of the job's replicate (bit b of ctrl[w]; ctrl null:
+// the genotype rows without classes), else 0; rows of padding SNPs are zero.
+__global__ void k_expand_e5m2(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch,
+                              const uint4 *ctrl, uint8_t *E)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * Wt) return;
+    const int64_t row = t / Wt;
+    const int w = (int)(t % Wt);
+    const int64_t s = row >> 1;
+    const int g = (int)(row & 1);
+    uint4 bits = make_uint4(0, 0, 0, 0);
+    if (s < S) bits = X[((size_t)w * 3 + g) * S_pad + s];
+    const uint4 cm = ctrl ? ctrl[w] : make_uint4(0, 0, 0, 0);
+    const uint32_t b32[4] = {bits.x, bits.y, bits.z, bits.w};
+    const uint32_t c32[4] = {cm.x, cm.y, cm.z, cm.w};
+    uint4 *dst = reinterpret_cast<uint4 *>(E + row * pitch + (int64_t)w * 128);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        uint32_t o[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int bit0 = q * 16 + u * 4;
+            const uint32_t word = b32[bit0 >> 5], cw = c32[bit0 >> 5];
+            const int sh = bit0 & 31;
+            uint32_t v = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t byte = ((cw >> (sh + e)) & 1u) ? 0x6Cu : 0x3Cu;
+                v |= (((word >> (sh + e)) & 1u) ? byte : 0u) << (8 * e);
+            }
+            o[u] = v;
+        }
+        dst[q] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+__global__ void k_fill_lists(float *s, uint64_t *r, size_t n)
+{
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+        s[x] = -FLT_MAX;
+        r[x] = NO_RANK;
+    }
+}
+
 }  // namespace
 
-int triples_pairs_per_tile(int enc) { return enc ? T3Shape<1>::NP : T3Shape<0>::NP; }
+cudaError_t launch_expand_e5m2(const uint4 *X, int64_t S, int64_t S_pad, int Wt, int64_t rows, int64_t pitch,
+                               const uint4 *ctrl, uint8_t *E, cudaStream_t st)
+{
+    const int64_t n = rows * Wt;
+    k_expand_e5m2<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, S, S_pad, Wt, rows, pitch, ctrl, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_lists(float *s, uint64_t *r, size_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
+    k_fill_lists<<<(unsigned)blocks, 256, 0, st>>>(s, r, n);
+    return cudaGetLastError();
+}
+
+int triples_pairs_per_tile(int enc) { return enc == 1 ? T3Shape<1>::NP : T3Shape<0>::NP; }
 
 int triples_round_candidates() { return 2 * T3_EPI_THREADS; }
 
-size_t triples_smem_bytes(int enc, int M, int P2) { return enc ? smem_bytes_enc<1>(M, P2) : smem_bytes_enc<0>(M, P2); }
+size_t triples_smem_bytes(int enc, int M, int P2)
+{
+    return enc == 1 ? smem_bytes_enc<1>(M, P2) : smem_bytes_enc<0>(M, P2);
+}
 
 cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S, int NP, int64_t i0, int64_t i1,
                              const int64_t *rowbase, uint8_t *P, cudaStream_t st)
@@ -654,13 +822,23 @@ cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S,
 }
 
 cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapA, const CUtensorMap &tmapP, const TriplesArgs &a,
-                              int grid, cudaStream_t st)
+                              int grid, cudaStream_t st, bool set_attr)
 {
     const size_t bytes = triples_smem_bytes(a.enc, a.M, a.P2);
-    void *fn = mode == MODE_TOPN ? (a.enc ? kernel_ptr<MODE_TOPN, 1>() : kernel_ptr<MODE_TOPN, 0>())
-                                 : (a.enc ? kernel_ptr<MODE_DUMP, 1>() : kernel_ptr<MODE_DUMP, 0>());
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
+    void *fn = nullptr;
+    if (a.jobs) {
+        if (mode != MODE_TOPN || (a.enc != 1 && a.enc != 2)) return cudaErrorInvalidValue;
+        fn = a.enc == 1 ? kernel_ptr<MODE_TOPN, 1, true>() : kernel_ptr<MODE_TOPN, 2, true>();
+    } else {
+        if (a.enc != 0 && a.enc != 1) return cudaErrorInvalidValue;
+        fn = mode == MODE_TOPN ? (a.enc ? kernel_ptr<MODE_TOPN, 1, false>() : kernel_ptr<MODE_TOPN, 0, false>())
+                               : (a.enc ? kernel_ptr<MODE_DUMP, 1, false>() : kernel_ptr<MODE_DUMP, 0, false>());
+    }
+    if (set_attr) {
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+    }
+    if (grid <= 0) return cudaSuccess;   // attributes only
     CUtensorMap mA = tmapA, mP = tmapP;
     TriplesArgs args = a;
     void *params[] = {&mA, &mP, &args};

@@ -217,6 +217,11 @@ CONFIGS = {
                planted=(3, 40, 77, 110, 150), maf_range=(0.05, 0.5)),
     "P6": dict(seed=7, S=76, cases=1024, controls=1024, k=6, top_n=100,
                planted=(1, 14, 30, 45, 60, 75), maf_range=(0.05, 0.5)),
+    # A parity case for the order-4 tensor-core plan beyond a few hundred
+    # SNPs (a mid-size version of the paper's order-4 runs, Table 4), small
+    # enough in samples for an exhaustive oracle run.
+    "Q4": dict(seed=8, S=600, cases=256, controls=256, k=4, top_n=100,
+               planted=(9, 201, 402, 587), maf_range=(0.05, 0.5)),
 }
 
 CONFIG_TITLES = {
@@ -227,6 +232,7 @@ CONFIG_TITLES = {
     "C5": "order-3 batched, 64 data sets x 20 permutation replicates, top 10 each",
     "P5": "order-5 exhaustive, 152 SNPs x 2,048 samples (1,024/1,024), top 100",
     "P6": "order-6 exhaustive, 76 SNPs x 2,048 samples (1,024/1,024), top 100",
+    "Q4": "order-4 exhaustive, 600 SNPs x 512 samples (256/256), top 100",
 }
 
 

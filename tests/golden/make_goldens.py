@@ -13,7 +13,8 @@ ascending) on the synthetic workloads, never a value from the CUDA path.
 
 Workloads: C1 (order 2, 100 x 1,600), C2 (order 3, 1,000 x 4,000), C3
 (order 2 all-pairs, 40,000 x 8,192), C4 (order 4, 300 x 6,000), P5 / P6
-(orders 5 and 6 at 152 / 76 SNPs x 2,048 samples), and C5S, a fixed subset
+(orders 5 and 6 at 152 / 76 SNPs x 2,048 samples), Q4 (order 4, 600 x 512,
+a parity case for the order-4 tensor-core plan), and C5S, a fixed subset
 of the batched workload (64 data sets x 20 phenotype replicates, order 3,
 top 10 per job) -- the whole batch is about 1.5e11 combinations, hours of
 oracle time, so the subset below is stored and labelled as a subset.
@@ -33,7 +34,7 @@ sys.path.insert(0, ROOT)
 import oracle  # noqa: E402
 from synth import CONFIGS, make_batch, make_config  # noqa: E402
 
-SINGLE = ["C1", "C2", "C4", "P6", "P5", "C3"]
+SINGLE = ["C1", "C2", "C4", "P6", "P5", "Q4", "C3"]
 
 # The batched-workload subset: one replicate (number j mod 20) of every data
 # set j whose search costs at most C5S_MAX_WORK sample-combinations, the two

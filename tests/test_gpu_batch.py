@@ -106,8 +106,8 @@ def test_batch_hybrid_tensor_core_jobs(fc, monkeypatch):
     h = fc.fc_load_batch(gens, phs)
     a = fc.fc_search_batch(h, 3, 10)
     kinds = [fc.fc_batch_job_kind(h, j) for j in range(6)]
-    assert kinds[0] == kinds[1] == kinds[4] == kinds[5] == 6
-    assert kinds[2] == kinds[3] != 6
+    assert kinds[0] == kinds[1] == kinds[4] == kinds[5] == 8
+    assert kinds[2] == kinds[3] not in (6, 8)
     b = fc.fc_search_batch(h, 3, 10)   # replay: same lists
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
@@ -118,7 +118,7 @@ def test_batch_hybrid_tensor_core_jobs(fc, monkeypatch):
     monkeypatch.setenv("FC_BATCH_TC", "0")
     h2 = fc.fc_load_batch(gens, phs)
     c = fc.fc_search_batch(h2, 3, 10)
-    assert all(fc.fc_batch_job_kind(h2, j) != 6 for j in range(6))
+    assert all(fc.fc_batch_job_kind(h2, j) not in (6, 8) for j in range(6))
     assert np.array_equal(a[0], c[0]) and np.array_equal(a[2], c[2])
     np.testing.assert_allclose(a[1], c[1], rtol=1e-12)
     assert tuple(a[0][0, 0]) == (7, 200, 411)
@@ -127,3 +127,91 @@ def test_batch_hybrid_tensor_core_jobs(fc, monkeypatch):
     def score_of(cmb):
         return float(oracle.mi(oracle.tables(gens[2], phs[2][1], 3, [cmb]), 3)[0])
     assert_topn_equal(a[0][5], a[1][5], o_idx, o_s, score_of)
+
+
+def _tc3_sets(R=3):
+    """Data sets for the batched tensor-core form: S >= 384 takes the tensor
+    cores; t0 has both classes below 4096 (one accumulator), t1 4200 cases
+    (two accumulators over the samples), t2 is small (persistent sweep).
+    Replicate 0 of each is a shuffled phenotype, so that the first
+    replicate's sample order is not the input order, and the last replicate
+    of t0 has another case count than the others."""
+    sets = [make_dataset("t0", seed=121, S=400, cases=700, controls=650, k=3, top_n=10, planted=(5, 180, 390)),
+            make_dataset("t1", seed=122, S=386, cases=4200, controls=300, k=3, top_n=10, planted=(11, 90, 301)),
+            make_dataset("t2", seed=123, S=60, cases=300, controls=320, k=3, top_n=10)]
+    rng = np.random.default_rng(140)
+    phs = []
+    for i, ds in enumerate(sets):
+        base = ds.phenotype[rng.permutation(ds.M)]
+        ph = permuted_phenotypes(base, R, seed=130 + i)
+        if i == 0:
+            ph[R - 1] = (rng.random(ds.M) < 0.6).astype(np.uint8)
+        phs.append(ph)
+    return sets, phs
+
+
+def test_batch_tc3_forms_match_sweep_and_per_job(fc, monkeypatch):
+    """Both batched tensor-core forms give the lists of the all-sweep batch
+    (every count exact, the same FP64 rescoring) and of per-job searches."""
+    sets, phs = _tc3_sets()
+    gens = [ds.genotypes for ds in sets]
+    h = fc.fc_load_batch(gens, phs)
+    a = fc.fc_search_batch(h, 3, 10)
+    kinds = [fc.fc_batch_job_kind(h, j) for j in range(9)]
+    assert kinds[:6] == [8] * 6, kinds
+    assert all(x not in (6, 8) for x in kinds[6:]), kinds
+    b = fc.fc_search_batch(h, 3, 10)   # replay
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    for j in (0, 2, 3, 5):
+        idx, s = fc.fc_search_job(h, j, 3, 10)
+        assert np.array_equal(idx, a[0][j, :len(s)])
+        np.testing.assert_allclose(s, a[1][j, :len(s)], rtol=1e-12)
+    monkeypatch.setenv("FC_BATCH_TC", "0")
+    h2 = fc.fc_load_batch(gens, phs)
+    c = fc.fc_search_batch(h2, 3, 10)
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[2], c[2])
+    np.testing.assert_allclose(a[1], c[1], rtol=1e-12)
+    fc.fc_free(h)
+    fc.fc_free(h2)
+
+
+def test_batch_tc3_small_slab_buffer_and_long_lists(fc, monkeypatch):
+    """A slab buffer that holds one data set's slab at a time (one launch per
+    data set, slabs rebuilt in the graph) and lists long enough for the
+    two-level merge give the lists of the per-job tensor-core searches."""
+    sets, phs = _tc3_sets(R=2)
+    gens = [ds.genotypes for ds in sets]
+    monkeypatch.setenv("FC_BATCH_SLAB_MB", "1")
+    h = fc.fc_load_batch(gens, phs)
+    a = fc.fc_search_batch(h, 3, 200)
+    assert [fc.fc_batch_job_kind(h, j) for j in range(4)] == [8] * 4
+    b = fc.fc_search_batch(h, 3, 200)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    monkeypatch.setenv("FC_BATCH_TC3", "0")
+    h2 = fc.fc_load_batch(gens, phs)
+    c = fc.fc_search_batch(h2, 3, 200)
+    assert [fc.fc_batch_job_kind(h2, j) for j in range(4)] == [6] * 4
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[2], c[2])
+    np.testing.assert_allclose(a[1], c[1], rtol=1e-12)
+    fc.fc_free(h)
+    fc.fc_free(h2)
+
+
+def test_batch_tc3_one_job_against_oracle(fc):
+    """One batched tensor-core job (a shuffled replicate) against the oracle."""
+    ds = make_dataset("t3", seed=124, S=384, cases=300, controls=340, k=3, top_n=10, planted=(3, 150, 383))
+    small = make_dataset("t4", seed=125, S=40, cases=200, controls=220, k=3, top_n=10)
+    ph = permuted_phenotypes(ds.phenotype, 2, seed=150)
+    ph_small = permuted_phenotypes(small.phenotype, 2, seed=151)
+    h = fc.fc_load_batch([ds.genotypes, small.genotypes], [ph, ph_small])
+    idx, score, cnt = fc.fc_search_batch(h, 3, 10)
+    assert fc.fc_batch_job_kind(h, 1) == 8
+    assert tuple(idx[0, 0]) == (3, 150, 383)
+    o_idx, o_s, _ = oracle.search(ds.genotypes, ph[1], 3, 10)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ph[1], 3, [c]), 3)[0])
+    assert_topn_equal(idx[1, :cnt[1]], score[1, :cnt[1]], o_idx, o_s, score_of)
+    fc.fc_free(h)

@@ -84,6 +84,6 @@ def test_batched_subset_equals_oracle(fc):
         assert_topn_equal(idx[jj][:n], s[jj][:n], np.array(job["idx"], dtype=np.uint32),
                           np.array(job["score"]), _score_fn(ds.genotypes, ph[r], 3))
     # The subset holds jobs of both batched paths (persistent sweep and
-    # tensor cores).
-    assert 6 in kinds and len(kinds) >= 2, kinds
+    # batched tensor-core launches).
+    assert 8 in kinds and len(kinds) >= 2, kinds
     fc.fc_free(h)

@@ -39,7 +39,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5", "P5", "P6"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5", "P5", "P6", "T4"])
     p.add_argument("--c5-datasets", type=int, default=64)
     p.add_argument("--c5-replicates", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -51,6 +51,9 @@ def parse_args():
                         "one data set per rank (weak scaling)")
     p.add_argument("--snps", type=int, default=None,
                    help="keep only the workload's first N SNPs (smaller cases for profiler captures)")
+    p.add_argument("--range", default=None, metavar="S/P",
+                   help="search only rank range S of P equal ranges (the share of one of P GPUs); "
+                        "default for T4: 63/64")
     return p.parse_args()
 
 
@@ -312,13 +315,18 @@ def run_ours(args):
     ds = make_dataset(args.workload, S=S, **cfg) if world > 1 else make_config(args.workload, args.snps)
     k, top_n = ds.k, ds.top_n
     total = math.comb(ds.S, k)
+    from paper_2201_03331_gb300.shard import shard_ranges
+    part = args.range or ("63/64" if args.workload == "T4" else None)
     if shard:
         # This rank's share of the one search: a contiguous rank range.
-        from paper_2201_03331_gb300.shard import shard_ranges
         r0, r1 = shard_ranges(total, world)[rank]
+    elif part:
+        # One range of a search split P ways (what one of P GPUs would run).
+        ps, pp = (int(x) for x in part.split("/"))
+        r0, r1 = shard_ranges(total, pp)[ps]
 
     def one_search(handle):
-        if shard:
+        if shard or part:
             return fc.fc_search_range(handle, k, top_n, r0, r1)
         return fc.fc_search(handle, k, top_n)
 
@@ -358,6 +366,8 @@ def run_ours(args):
         if rank == 0:
             idx, score = merged
         value, ms_per_step = aggregate(dist, 1, total, args.steps, sum(step_ms))
+    elif part:
+        value, ms_per_step = aggregate(dist, world, r1 - r0, args.steps, sum(step_ms))
     else:
         value, ms_per_step = aggregate(dist, world, total, args.steps, sum(step_ms))
 
@@ -377,7 +387,7 @@ def run_ours(args):
         if i > 0:
             e2e_times.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(dist, sum(e2e_times) / len(e2e_times))
-    e2e = {"value": world * total / e2e_s, "unit": UNIT,
+    e2e = {"value": world * (r1 - r0 if part and not shard else total) / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(ds.genotypes.nbytes + ds.phenotype.nbytes),
            "d2h_bytes_per_step": int(idx2.nbytes + score2.nbytes + 8 + 4),
            "ms_per_step": 1e3 * e2e_s}
@@ -391,7 +401,7 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", DEFAULT_SM_MAX_MHZ))
     sweep_avg_s = (sweep_ms / max(sweeps, 1)) / 1e3
     kind = fc.fc_last_search_kind(h)
-    share = (r1 - r0) / total if shard and total else 1.0   # this rank's part of the work
+    share = (r1 - r0) / total if (shard or part) and total else 1.0   # this rank's part of the work
     if kind in (2, 6, 7):
         # Tensor-core contraction: contracted cells x M samples x 2 FLOP per
         # combination (orders 2, 3: the 2^k cells with genotypes in {0,1};
@@ -448,7 +458,9 @@ def run_ours(args):
                                "inclusion-exclusion tables; orders 4-6: tuple-row slabs), built by fc_load "
                                "and the first search; e2e rebuilds all of them every step",
                    "parallelism": ("one search sharded by rank range over the GPUs" if shard else
-                                   "one independent data set per GPU" if world > 1 else "single GPU")},
+                                   "one independent data set per GPU" if world > 1 else "single GPU"),
+                   **({"rank_range": f"range {part} of the C(S,k) lexicographic ranks: [{r0}, {r1})",
+                       "combinations_per_step": r1 - r0} if part and not shard else {})},
         "sample_combinations_per_s": value * ds.M,
         "roofline": roofline,
         "e2e": e2e,

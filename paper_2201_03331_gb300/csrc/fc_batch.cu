@@ -158,13 +158,13 @@ int plan_tc3(fc_handle *h, int L, int64_t top_n, std::unique_ptr<Tc3Batch> &out)
     if (env && strcmp(env, "0") == 0) return FC_OK;
     const int R = B.R;
     const int grid = lead.sms;
-    const int P2 = Dataset::triples_list_size(L);
     // The per-job merge of grid lists in one or two levels of k_merge_jobs.
     const int merge_cap = 16384;   // entries one merge block sorts (12 bytes each in shared memory)
     if (L > 1024 || (int64_t)L * grid > (int64_t)merge_cap * 16) return FC_OK;
     std::unique_ptr<Tc3Batch> T(new Tc3Batch());
     T->L = L;
     T->grid = grid;
+    T->smem_cap = lead.max_smem_optin;
     int64_t maxM = 0;
     for (int d = 0; d < B.n_data; ++d) {
         bool all = true, one_acc = true;
@@ -181,7 +181,7 @@ int plan_tc3(fc_handle *h, int L, int64_t top_n, std::unique_ptr<Tc3Batch> &out)
         // launch's largest sample count: one accumulator where both classes
         // of every replicate have at most 4095 samples and shared memory
         // fits, else two.
-        if (one_acc && triples_smem_bytes(1, (int)d0.M, P2) <= (size_t)lead.max_smem_optin) {
+        if (one_acc && triples_list_fit(1, d0.M, L, lead.max_smem_optin) > 0) {
             st.enc = 1;
         } else {
             // Two accumulators over the chunks [0, split) and [split, Wt) of
@@ -197,7 +197,7 @@ int plan_tc3(fc_handle *h, int L, int64_t top_n, std::unique_ptr<Tc3Batch> &out)
                 split = c + 1;
             }
             if (split <= 0 || split >= d0.Wt || d0.M - pre > 4095) continue;
-            if (triples_smem_bytes(2, (int)d0.M, P2) > (size_t)lead.max_smem_optin) continue;
+            if (triples_list_fit(2, d0.M, L, lead.max_smem_optin) < 0) continue;
             st.enc = 2;
             st.split = split;
         }
@@ -556,7 +556,7 @@ TriplesArgs tc3_args(const Tc3Batch &T, const Tc3Batch::Launch &ln, int g)
     a.xlogx = T.xlogx;
     a.M = ln.M;
     a.L = T.L;
-    a.P2 = Dataset::triples_list_size(T.L);
+    a.P2 = triples_list_fit(ln.enc, ln.M, T.L, T.smem_cap);
     a.Bcap = a.P2 - a.L;
     a.check_rounds = 1;
     for (int r = 3; r >= 1; --r)
@@ -777,12 +777,15 @@ int plan_batch(fc_handle *h, int k, int64_t top_n)
     if (T) {
         n2_all = std::max(n2_all, pow2_ge((T->level1 ? T->F : T->grid) * L));
         if (T->level1) n2_all = std::max(n2_all, pow2_ge(((T->grid + T->F - 1) / T->F) * L));
-        const CUtensorMap none{};
+        // Each form's kernel takes the shared memory of its largest launch.
+        size_t bytes[3] = {0, 0, 0};
         for (const Tc3Batch::Launch &ln : T->launches) {
             const TriplesArgs a = tc3_args(*T, ln, 0);
-            if ((e = launch_triples_tc(MODE_TOPN, none, none, a, 0, st)) != cudaSuccess)
-                return cuda_status(e, "batched order-3 attributes");
+            bytes[ln.enc] = std::max(bytes[ln.enc], triples_smem_bytes(ln.enc, a.M, a.P2));
         }
+        for (int enc = 1; enc <= 2; ++enc)
+            if (bytes[enc] && (e = prepare_triples_tc_batch(enc, bytes[enc])) != cudaSuccess)
+                return cuda_status(e, "batched order-3 attributes");
     }
     if ((e = prepare_merge_jobs(n2_all)) != cudaSuccess) return cuda_status(e, "merge attributes");
     if ((e = prepare_final_sort_batch(L)) != cudaSuccess) return cuda_status(e, "sort attributes");

@@ -349,6 +349,9 @@ cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S,
 // by an earlier call; a graph capture may not set it); grid = 0 only sets it.
 cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapA, const CUtensorMap &tmapP, const TriplesArgs &a,
                               int grid, cudaStream_t st, bool set_attr = true);
+// Shared-memory attribute of the batched kernel of form enc (1 or 2): the
+// largest launch's bytes, set before a graph capture.
+cudaError_t prepare_triples_tc_batch(int enc, size_t smem_bytes);
 // Operands of the batched form (e5m2; see T3Job): rows 2 s + g of the bit
 // table X, controls of the replicate marked by ctrl (one uint4 of sample
 // bits per chunk; null: no classes).
@@ -373,8 +376,9 @@ struct QuadsArgs {
     // are the left blocks a in [g0, min(g1, amax[b])) (those with include[a]
     // set, if include is not null).  Within a group the right blocks stream
     // while the group's left blocks stay in L2.
-    const int4 *groups;     // by item_first
+    const int4 *groups;     // by item_first (enc 1: right block pairs in place of right blocks)
     int ngroups;
+    int enc;                // 1: one accumulator n_case + 4096 n_ctrl, two right blocks per tile
     int n_items;
     const int *amax;        // [right blocks]: left blocks whose smallest last SNP is below the block's largest first SNP
     const uint8_t *include;
@@ -399,8 +403,13 @@ struct QuadsArgs {
     uint32_t *dump_tables;  // MODE_DUMP: [C(S,k)][3^k][2]
 };
 
-cudaError_t launch_tuple_rows(int T, const uint4 *X, int64_t S_pad, int Wt, const uint64_t *tuples, int64_t nblocks,
-                              int64_t pitch, uint8_t *Q, cudaStream_t st);
+// Tuple rows of T-SNP tuples (nblocks blocks of 128 rows); control words
+// (w >= W0) carry ctrl_byte (e4m3 1.0 = 0x38, or 64 = 0x68 for the encoded
+// form).
+cudaError_t launch_tuple_rows(int T, const uint4 *X, int64_t S_pad, int W0, int Wt, const uint64_t *tuples,
+                              int64_t nblocks, int64_t pitch, uint8_t ctrl_byte, uint8_t *Q, cudaStream_t st);
+// Shared memory of the orders 4-6 kernel (enc 1: two right blocks per stage).
+size_t quads_smem_bytes(int enc, int stages, int M, int P2);
 cudaError_t launch_quads_tc(int k, int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
                             int grid, cudaStream_t st);
 

@@ -30,6 +30,16 @@
 // on the left tuple only and one that depends on the right tuple only, both
 // computed on the host.
 //
+// Two forms (template ENC):
+//   ENC = 0: both classes carry 1; the case and control chunks accumulate
+//            into two accumulators; a tile is (left block, right block),
+//            N = 128 per class;
+//   ENC = 1: control samples carry the e4m3 value 64 in both slabs, so one
+//            accumulator holds n_case + 4096 n_ctrl (exact while both
+//            classes have at most 4095 samples); a tile is (left block, two
+//            consecutive right blocks), N = 256, which halves the left
+//            operand's bytes per multiply-add.
+//
 // Roles (one persistent CTA per SM, TC_THREADS_MP threads), as in the
 // order-2 kernel:
 //   warps 0, 6, 7, 8 : TMA producers (128-byte K chunks of the left and right
@@ -38,7 +48,8 @@
 //   warp 1 : TMEM allocation; lane 0 issues the MMAs and schedules the tiles
 //   warps 2-5 : epilogue (TMEM -> registers -> partial MI over a row's cells
 //               -> sum over a left tuple's lanes -> CTA top list)
-// Accumulators: two TMEM buffers x two classes x 128 FP32 columns.
+// Accumulators: two TMEM buffers x 256 FP32 columns (two classes x 128, or
+// two right blocks x 128).
 #include "fc_tc.cuh"
 
 namespace fc {
@@ -49,8 +60,8 @@ namespace {
 // SNP of the tuple at its genotype digit, first SNP most significant) over
 // 16 samples of one class word, expanded to bytes.
 template <int T>
-__global__ void k_tuple_rows(const uint4 *X, int64_t S_pad, int Wt, const uint64_t *tuples, int64_t nblocks,
-                             int64_t pitch, uint8_t *Q)
+__global__ void k_tuple_rows(const uint4 *X, int64_t S_pad, int W0, int Wt, const uint64_t *tuples, int64_t nblocks,
+                             int64_t pitch, uint32_t ctrl_byte, uint8_t *Q)
 {
     constexpr int R = T == 2 ? 9 : 27;              // rows per tuple
     constexpr int PQ = 27 / R;                      // tuples per quarter
@@ -81,21 +92,32 @@ __global__ void k_tuple_rows(const uint4 *X, int64_t S_pad, int Wt, const uint64
             bits = (acc >> ((sub & 1) * 16)) & 0xffffu;
         }
     }
+    const uint32_t one = (ch >> 3) < W0 ? 0x38u : ctrl_byte;   // e4m3 1.0, or the control value
     uint32_t o[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         uint32_t v = 0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v |= ((bits >> (4 * q + e)) & 1u ? 0x38u : 0u) << (8 * e);
+        for (int e = 0; e < 4; ++e) v |= ((bits >> (4 * q + e)) & 1u ? one : 0u) << (8 * e);
         o[q] = v;
     }
     *(reinterpret_cast<uint4 *>(Q + row * pitch) + ch) = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
-template <int LT, int RT, int MODE>
+// One encoded accumulator x = n_case + 4096 n_ctrl (an exact integer below
+// 2^24, n_case < 4096) as n_case | n_ctrl << 16.
+__device__ __forceinline__ uint32_t unpack_enc4(uint32_t bits)
+{
+    const uint32_t v = __float2uint_rz(__uint_as_float(bits));
+    return v + (v >> 12) * 61440u;
+}
+
+template <int LT, int RT, int MODE, int ENC>
 __global__ void __launch_bounds__(TC_THREADS_MP, 1)
     k_quads_tc(const __grid_constant__ CUtensorMap tmapL, const __grid_constant__ CUtensorMap tmapR, QuadsArgs a)
 {
+    constexpr uint32_t B_BYTES = ENC ? 2 * TC_B_BYTES : TC_B_BYTES;   // one or two right blocks per stage
+    constexpr int NB = ENC ? 256 : 128;                                 // MMA N
     constexpr int RL = LT == 2 ? 9 : 27;            // rows (cells) per left tuple
     constexpr int RR = RT == 2 ? 9 : 27;            // columns (cells) per right tuple
     constexpr int LPQ = 27 / RL;                    // left tuples per lane quarter
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *stA = smem;
     uint8_t *stB = smem + (size_t)stages * TC_A_BYTES;
-    float *xltab = reinterpret_cast<float *>(stB + (size_t)stages * TC_B_BYTES);   // x ln x
+    float *xltab = reinterpret_cast<float *>(stB + (size_t)stages * B_BYTES);   // x ln x
     const int lt_floats = (a.M + 1 + 3) & ~3;
     uint64_t *lrank = reinterpret_cast<uint64_t *>(xltab + lt_floats);
     float *lscore = reinterpret_cast<float *>(lrank + a.P2);
@@ -183,20 +205,20 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                 const int rb = sched_rb[slot];
                 mbar_arrive(&bar_sempty[slot]);
                 if (t < 0) break;
-                const int rowL = t * 128, rowR = rb * 128;
-                for (int c = 0; c < 2 && ok; ++c) {
-                    const int nk = c ? kc1 : kc0;
-                    const int xbase = c ? kc0 * TC_BK : 0;
-                    for (int kc = 0; kc < nk; ++kc, ++fill) {
-                        const int s = fill % stages;
-                        if (s % P != prod) continue;
-                        const uint32_t n = fill / stages;
-                        if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
-                        mbar_expect_tx(&bar_full[s], TC_A_BYTES + TC_B_BYTES);
-                        tma_load_2d(&tmapL, &bar_full[s], stA + (size_t)s * TC_A_BYTES, xbase + kc * TC_BK, rowL);
-                        tma_load_2d(&tmapR, &bar_full[s], stB + (size_t)s * TC_B_BYTES, xbase + kc * TC_BK, rowR);
-                        if (s == prod) last0 = (int)fill; else last1 = (int)fill;
-                    }
+                // ENC 1: rb is a pair of right blocks (rows 256 rb ..).
+                const int rowL = t * 128, rowR = rb * NB;
+                // The chunks in the order the MMA thread takes them (the
+                // case chunks, then the control chunks: all of them).
+                const int nk = kc0 + kc1;
+                for (int kc = 0; kc < nk; ++kc, ++fill) {
+                    const int s = fill % stages;
+                    if (s % P != prod) continue;
+                    const uint32_t n = fill / stages;
+                    if (!mbar_wait(&bar_empty[s], (n & 1) ^ 1, abort_flag, a.err)) { ok = false; break; }
+                    mbar_expect_tx(&bar_full[s], TC_A_BYTES + B_BYTES);
+                    tma_load_2d(&tmapL, &bar_full[s], stA + (size_t)s * TC_A_BYTES, kc * TC_BK, rowL);
+                    tma_load_2d(&tmapR, &bar_full[s], stB + (size_t)s * B_BYTES, kc * TC_BK, rowR);
+                    if (s == prod) last0 = (int)fill; else last1 = (int)fill;
                 }
             }
             // Let the last copies into the stages this producer owns land
@@ -213,7 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issue ----------------
-            const uint32_t idesc = idesc_e4m3_f32(TC_BM, TC_BN);
+            const uint32_t idesc = idesc_e4m3_f32(TC_BM, NB);
             uint32_t fill = 0;
             bool ok = true;
             // This thread also schedules the tiles, TC_LOOKAHEAD ahead of the
@@ -283,23 +305,25 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                 const uint32_t u = (uint32_t)(it >> 1);
                 if (!mbar_wait(&bar_tempty[b], (u & 1) ^ 1, abort_flag, a.err)) break;
                 tc_fence_after();
-                for (int c = 0; c < 2 && ok; ++c) {
-                    const int nk = c ? kc1 : kc0;
-                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + c * 128);
-                    for (int kc = 0; kc < nk; ++kc, ++fill) {
-                        const int s = fill % stages;
-                        const uint32_t n = fill / stages;
-                        if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t aaddr = smem_u32(stA + (size_t)s * TC_A_BYTES);
-                        const uint32_t baddr = smem_u32(stB + (size_t)s * TC_B_BYTES);
+                // ENC 0: case chunks into columns [0, 128), control chunks
+                // into [128, 256); ENC 1: every chunk into [0, 256).
+                const int nk = kc0 + kc1;
+                for (int kc = 0; kc < nk && ok; ++kc, ++fill) {
+                    const bool ctrl = !ENC && kc >= kc0;
+                    const int k0 = ctrl ? kc - kc0 : kc;   // chunk within its accumulator
+                    const uint32_t d = tmem_base + (uint32_t)(b * 256 + (ctrl ? 128 : 0));
+                    const int s = fill % stages;
+                    const uint32_t n = fill / stages;
+                    if (!mbar_wait(&bar_full[s], n & 1, abort_flag, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t aaddr = smem_u32(stA + (size_t)s * TC_A_BYTES);
+                    const uint32_t baddr = smem_u32(stB + (size_t)s * B_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < TC_BK / 32; ++kk) {
-                            mma_e4m3(d, smem_desc_sw128(aaddr + kk * 32), smem_desc_sw128(baddr + kk * 32), idesc,
-                                     (kc > 0 || kk > 0) ? 1u : 0u);
-                        }
-                        mma_commit(&bar_empty[s]);
+                    for (int kk = 0; kk < TC_BK / 32; ++kk) {
+                        mma_e4m3(d, smem_desc_sw128(aaddr + kk * 32), smem_desc_sw128(baddr + kk * 32), idesc,
+                                 (k0 > 0 || kk > 0) ? 1u : 0u);
                     }
+                    mma_commit(&bar_empty[s]);
                 }
                 if (ok) mma_commit(&bar_tfull[b]);
             }
@@ -352,14 +376,33 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
             }
             const uint32_t llast = (uint32_t)(ltp >> (16 * (LT - 1))) & 0xffffu;
             const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256);
-            for (int ch = 0; ch < 4; ++ch) {
+            constexpr int NCH = ENC ? 8 : 4;   // 32-column chunks of the tile
+            for (int ch = 0; ch < NCH; ++ch) {
+                // Counts of this chunk: cases in v0, controls in v1.
                 uint32_t v0[32], v1[32];
-                tmem_ld32(taddr + ch * 32, v0);
-                tmem_ld32(taddr + 128 + ch * 32, v1);
-                tmem_wait_ld();
-                tmem_regs_after_wait(v0);
-                tmem_regs_after_wait(v1);
-                if (ch == 3) {
+                if (ENC) {
+                    tmem_ld32(taddr + ch * 32, v0);
+                    tmem_wait_ld();
+                    tmem_regs_after_wait(v0);
+#pragma unroll
+                    for (int x = 0; x < 32; ++x) {
+                        const uint32_t pk = unpack_enc4(v0[x]);
+                        v0[x] = pk & 0xffffu;
+                        v1[x] = pk >> 16;
+                    }
+                } else {
+                    tmem_ld32(taddr + ch * 32, v0);
+                    tmem_ld32(taddr + 128 + ch * 32, v1);
+                    tmem_wait_ld();
+                    tmem_regs_after_wait(v0);
+                    tmem_regs_after_wait(v1);
+#pragma unroll
+                    for (int x = 0; x < 32; ++x) {
+                        v0[x] = f2u_exact(v0[x]);
+                        v1[x] = f2u_exact(v1[x]);
+                    }
+                }
+                if (ch == NCH - 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar_tempty[b]);
@@ -369,16 +412,17 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                 bool val[RPC];
 #pragma unroll
                 for (int q = 0; q < RPC; ++q) {
-                    // Right tuple RPC ch + q: the RR cells of this row.
-                    const size_t ri = (size_t)tile.y * (4 * RPC) + ch * RPC + q;
+                    // Right tuple RPC ch + q of the tile's right block(s): the
+                    // RR cells of this row.
+                    const size_t ri = (size_t)tile.y * (ENC ? 8 * RPC : 4 * RPC) + ch * RPC + q;
                     const uint64_t rtp = a.rtup[ri];
                     const uint32_t rfirst = (uint32_t)rtp & 0xffffu;
                     float part = 0.f;
 #pragma unroll
                     for (int c = 0; c < RR; ++c) {
                         // Clamped so that no index can leave the table.
-                        const uint32_t ca = min(f2u_exact(v0[RR * q + c]), lt);
-                        const uint32_t cb = min(f2u_exact(v1[RR * q + c]), lt);
+                        const uint32_t ca = min(v0[RR * q + c], lt);
+                        const uint32_t cb = min(v1[RR * q + c], lt);
                         const uint32_t n = min(ca + cb, lt);
                         part += (xltab[n] - xltab[min(ca, n)]) - xltab[min(cb, n)];
                     }
@@ -400,8 +444,8 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                             uint32_t *o = a.dump_tables + (size_t)rank * (2 * CK) + (size_t)cell_l * (2 * RR);
 #pragma unroll
                             for (int c = 0; c < RR; ++c) {
-                                o[2 * c] = min(f2u_exact(v0[RR * q + c]), lt);
-                                o[2 * c + 1] = min(f2u_exact(v1[RR * q + c]), lt);
+                                o[2 * c] = min(v0[RR * q + c], lt);
+                                o[2 * c + 1] = min(v1[RR * q + c], lt);
                             }
                         }
                     }
@@ -464,26 +508,41 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
 
 }  // namespace
 
-cudaError_t launch_tuple_rows(int T, const uint4 *X, int64_t S_pad, int Wt, const uint64_t *tuples, int64_t nblocks,
-                              int64_t pitch, uint8_t *Q, cudaStream_t st)
+cudaError_t launch_tuple_rows(int T, const uint4 *X, int64_t S_pad, int W0, int Wt, const uint64_t *tuples,
+                              int64_t nblocks, int64_t pitch, uint8_t ctrl_byte, uint8_t *Q, cudaStream_t st)
 {
     const int64_t n = nblocks * 128 * 8 * (int64_t)Wt;
     if (n == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((n + 255) / 256);
-    if (T == 2) k_tuple_rows<2><<<grid, 256, 0, st>>>(X, S_pad, Wt, tuples, nblocks, pitch, Q);
-    else k_tuple_rows<3><<<grid, 256, 0, st>>>(X, S_pad, Wt, tuples, nblocks, pitch, Q);
+    if (T == 2) k_tuple_rows<2><<<grid, 256, 0, st>>>(X, S_pad, W0, Wt, tuples, nblocks, pitch, ctrl_byte, Q);
+    else k_tuple_rows<3><<<grid, 256, 0, st>>>(X, S_pad, W0, Wt, tuples, nblocks, pitch, ctrl_byte, Q);
     return cudaGetLastError();
+}
+
+size_t quads_smem_bytes(int enc, int stages, int M, int P2)
+{
+    return 1024 + (size_t)stages * (TC_A_BYTES + (enc ? 2 : 1) * TC_B_BYTES) + (size_t)((M + 1 + 3) & ~3) * 4 +
+           (size_t)P2 * (8 + 4);
+}
+
+template <int LT, int RT>
+void *quads_kernel(int mode, int enc)
+{
+    if (mode == MODE_TOPN)
+        return enc ? reinterpret_cast<void *>(&k_quads_tc<LT, RT, MODE_TOPN, 1>)
+                   : reinterpret_cast<void *>(&k_quads_tc<LT, RT, MODE_TOPN, 0>);
+    return enc ? reinterpret_cast<void *>(&k_quads_tc<LT, RT, MODE_DUMP, 1>)
+               : reinterpret_cast<void *>(&k_quads_tc<LT, RT, MODE_DUMP, 0>);
 }
 
 cudaError_t launch_quads_tc(int k, int mode, const CUtensorMap &tmapL, const CUtensorMap &tmapR, const QuadsArgs &a,
                             int grid, cudaStream_t st)
 {
-    const size_t bytes = pairs_smem_bytes(a.stages, a.M, a.P2);
+    const size_t bytes = quads_smem_bytes(a.enc, a.stages, a.M, a.P2);
     void *fn = nullptr;
-    const bool top = mode == MODE_TOPN;
-    if (k == 4) fn = top ? reinterpret_cast<void *>(&k_quads_tc<2, 2, MODE_TOPN>) : reinterpret_cast<void *>(&k_quads_tc<2, 2, MODE_DUMP>);
-    if (k == 5) fn = top ? reinterpret_cast<void *>(&k_quads_tc<2, 3, MODE_TOPN>) : reinterpret_cast<void *>(&k_quads_tc<2, 3, MODE_DUMP>);
-    if (k == 6) fn = top ? reinterpret_cast<void *>(&k_quads_tc<3, 3, MODE_TOPN>) : reinterpret_cast<void *>(&k_quads_tc<3, 3, MODE_DUMP>);
+    if (k == 4) fn = quads_kernel<2, 2>(mode, a.enc);
+    if (k == 5) fn = quads_kernel<2, 3>(mode, a.enc);
+    if (k == 6) fn = quads_kernel<3, 3>(mode, a.enc);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;

@@ -713,26 +713,40 @@ int Dataset::pairs_dense(float *scores, uint32_t *tables)
 
 // ---- order-3 tensor-core operands --------------------------------------------
 
-// The order-3 tensor-core form for this data set: 1 (one accumulator
-// n_case + 4096 n_ctrl) while both classes have at most 4095 samples and
-// its shared memory fits, else 0 (one accumulator per class), else -1 (no
-// tensor-core search).  FC_TRIPLES_ENC=0 forces the per-class form.
+// The order-3 tensor-core form for searches with lists of L: 1 (one
+// accumulator n_case + 4096 n_ctrl) while both classes have at most 4095
+// samples and its shared memory fits, else 0 (one accumulator per class),
+// else -1 (no tensor-core search).  The same for every L up to 1024.
+// FC_TRIPLES_ENC=0 forces the per-class form.
 int Dataset::triples_form(int L) const
 {
-    const int P2 = triples_list_size(L);
     const char *f = getenv("FC_TRIPLES_ENC");
     const bool enc_ok = !(f && strcmp(f, "0") == 0) && M1 <= 4095 && M0 <= 4095;
-    if (enc_ok && triples_smem_bytes(1, (int)M, P2) <= (size_t)max_smem_optin) return 1;
-    if (triples_smem_bytes(0, (int)M, P2) <= (size_t)max_smem_optin) return 0;
+    if (enc_ok && triples_list_fit(1, L) > 0) return 1;
+    if (triples_list_fit(0, L) > 0) return 0;
     return -1;
 }
 
-// Candidate list of the order-3 kernel: L entries and a buffer of at least
-// 2048 (two rounds of its epilogue insert at most 1536).
+// Candidate list of the order-3 kernel (preferred size): L entries and a
+// buffer of at least 2048, three rounds of its epilogue's inserts (at most
+// 1024 each) between buffer checks.
 int Dataset::triples_list_size(int L)
 {
     return pow2_at_least(std::max(L, 1) + 2048);
 }
+
+int triples_list_fit(int enc, int64_t M, int L, int smem_cap)
+{
+    const int big = Dataset::triples_list_size(L);
+    if (triples_smem_bytes(enc, (int)M, big) <= (size_t)smem_cap) return big;
+    // A buffer of at least 1024 (one round between checks), for the larger
+    // x ln x tables of more than 4095 samples.
+    const int small = pow2_at_least(std::max(L, 1) + 1024);
+    if (small < big && triples_smem_bytes(enc, (int)M, small) <= (size_t)smem_cap) return small;
+    return -1;
+}
+
+int Dataset::triples_list_fit(int enc, int L) const { return fc::triples_list_fit(enc, M, L, max_smem_optin); }
 
 bool Dataset::triples_tc_eligible(int L)
 {
@@ -769,7 +783,7 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.rank_begin = 0;
     ta.rank_end = ~0ull;
     ta.L = std::max(L, 1);
-    ta.P2 = triples_list_size(L);
+    ta.P2 = triples_list_fit(enc3, L);
     ta.Bcap = ta.P2 - ta.L;
     // Rounds of the kernel's epilogue between checks of its candidate buffer.
     ta.check_rounds = 1;
@@ -844,14 +858,17 @@ std::shared_ptr<const TriplePlan> plan_triples(int64_t S, int NP, int64_t cap_ro
 // The e4m3 rows (those of the order-2 path, or a copy with controls = 64 for
 // the one-accumulator form), the inclusion-exclusion tables, the x ln x
 // table, the slab and tile plan, the slab buffer with its first slab and the
-// kernel's two TMA descriptors.  A slab holds at most min(16 GiB, a quarter
-// of the free device memory) of pair rows (FC_TRIPLES_SLAB_MB overrides the
-// 16 GiB), and at least the rows of one first SNP.  A single slab is kept for
-// later searches; with several, the buffer is released after each search.
-int Dataset::prepare_triples()
+// kernel's two TMA descriptors, in the form that lists of L take.  A slab
+// holds at most min(16 GiB, a quarter of the free device memory) of pair
+// rows (FC_TRIPLES_SLAB_MB overrides the 16 GiB), and at least the rows of
+// one first SNP.  A single slab is kept for later searches; with several,
+// the buffer is released after each search.  Operands of the other form are
+// rebuilt only when their form cannot take lists of L.
+int Dataset::prepare_triples(int L)
 {
-    if (triples_ready) return FC_OK;
-    const int form = triples_form(2048);
+    if (triples_ready && triples_list_fit(enc3, L) > 0) return FC_OK;
+    if (triples_ready) release_triples();
+    const int form = triples_form(L);
     if (form < 0) return set_error(FC_ERANGE, "order-3 tensor-core kernel does not fit in shared memory");
     int rc = prepare_pairs();
     if (rc) return rc;
@@ -968,7 +985,7 @@ void Dataset::release_triples()
 
 int Dataset::triples_dense(float *scores, uint32_t *tables)
 {
-    int rc = prepare_triples();
+    int rc = prepare_triples(0);
     if (rc) return rc;
     const uint64_t total = binom(S, 3);
     TriplesArgs ta = triples_args(0, (float)hy64(), (float)(1.0 / (double)M));
@@ -1047,6 +1064,14 @@ void enum_tuples(int64_t S, int T, bool left, int other, std::vector<uint64_t> &
     }
 }
 
+// Left blocks per group: ~48 MB of them, about a third of L2 (two dies share
+// the 129 MB), so that a group stays resident while the right blocks stream.
+int64_t tuple_group_size(int Wt)
+{
+    const uint64_t pitch = (uint64_t)Wt * 128 + 128;
+    return std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((48ull << 20) / (128 * pitch))));
+}
+
 int64_t tuple_count(int64_t S, int T, int other)
 {
     // Left and right counts are equal: C(S - other, T).
@@ -1069,10 +1094,11 @@ bool Dataset::tuples_tc_eligible(int k, int L)
     const int64_t nl = tuple_count(S, LT, RT), nr = tuple_count(S, RT, LT);
     const int64_t bl = (nl + tc_tuples_per_block(LT) - 1) / tc_tuples_per_block(LT);
     const int64_t br = (nr + tc_tuples_per_block(RT) - 1) / tc_tuples_per_block(RT);
-    // Block indices and strips (group, right block) are ints; the groups hold
-    // at least 16 left blocks.
+    // Block indices and strips (group, right block) are ints (the group size
+    // as in prepare_tuples).
     if (bl >= ((int64_t)1 << 31) / 128 || br >= ((int64_t)1 << 31) / 128) return false;
-    if ((double)(bl / 16 + 1) * (double)br >= 2147483647.0) return false;
+    const int64_t group = tuple_group_size(Wt);
+    if ((double)(bl / group + 1) * (double)br >= 2147483647.0) return false;
     // Both slabs stay resident: at most 60 % of the free memory (FC_TUPLES_SLAB_MB caps it).
     const double slab = (double)(bl + br) * 128.0 * ((double)Wt * 128 + 128);
     size_t free_b = 0, total_b = 0;
@@ -1085,7 +1111,24 @@ bool Dataset::tuples_tc_eligible(int k, int L)
     if (!tup[k - 4].ready && slab > cap) return false;
     const int Bcap = std::max(L, 1024);
     const int P2 = pow2_at_least(L + Bcap);
-    return pairs_smem_bytes(2, (int)M, P2) <= (size_t)max_smem_optin;
+    return quads_smem_bytes(tuples_form(), 2, (int)M, P2) <= (size_t)max_smem_optin;
+}
+
+// The orders 4-6 tensor-core form: 1 (one accumulator n_case + 4096 n_ctrl,
+// two right blocks per tile) while both classes have at most 4095 samples
+// and four of its 48 KB stages fit beside the x ln x table and a list of
+// 2048 entries, else 0 (one accumulator per class, 32 KB stages).  The
+// copies in flight set the operand stream (measured: at 2048 samples form 1
+// with four stages is 1.3x form 0 with six; at 6000 samples form 1 with
+// three stages is 4 % slower than form 0 with six).  FC_QUADS_ENC=0 forces
+// form 0, FC_QUADS_ENC=1 form 1 where the classes allow it.
+int Dataset::tuples_form() const
+{
+    const char *f = getenv("FC_QUADS_ENC");
+    if (f && strcmp(f, "0") == 0) return 0;
+    if (M1 > 4095 || M0 > 4095) return 0;
+    if (f && strcmp(f, "1") == 0) return 1;
+    return quads_smem_bytes(1, 4, (int)M, 2048) <= (size_t)max_smem_optin ? 1 : 0;
 }
 
 QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
@@ -1094,6 +1137,7 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
     QuadsArgs qa{};
     qa.groups = u.groups;
     qa.ngroups = u.ngroups;
+    qa.enc = u.enc;
     qa.n_items = (int)u.n_items;
     qa.amax = u.amax;
     qa.include = nullptr;
@@ -1115,7 +1159,7 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
     qa.P2 = L > 0 ? pow2_at_least(L + qa.Bcap) : 0;
     qa.stages = 2;
     for (int st = TC_MAX_STAGES; st >= 2; --st) {
-        if (pairs_smem_bytes(st, (int)M, qa.P2) <= (size_t)max_smem_optin) { qa.stages = st; break; }
+        if (quads_smem_bytes(u.enc, st, (int)M, qa.P2) <= (size_t)max_smem_optin) { qa.stages = st; break; }
     }
     tc_producer_split(&qa.stages, &qa.producers);
     return qa;
@@ -1196,6 +1240,9 @@ int Dataset::prepare_tuples(int k)
     enum_tuples(S, RT, false, LT, rt);
     const int64_t nl = (int64_t)lt.size(), nr = (int64_t)rt.size();
     const int64_t bl = (nl + LPB - 1) / LPB, br = (nr + RPB - 1) / RPB;
+    // Form 1 takes right blocks in pairs: the right slab gets an even count.
+    u.enc = tuples_form();
+    const int64_t br2 = u.enc ? (br + 1) / 2 * 2 : br;
     auto snp = [](uint64_t t, int i) { return (int64_t)((t >> (16 * i)) & 0xffffu); };
     std::vector<uint64_t> lr(lt.size()), rr(rt.size());
     for (size_t x = 0; x < lt.size(); ++x) {
@@ -1220,8 +1267,8 @@ int Dataset::prepare_tuples(int k)
     }
     lt.resize((size_t)bl * LPB, NO_TUPLE);
     lr.resize((size_t)bl * LPB, 0);
-    rt.resize((size_t)br * RPB, NO_TUPLE);
-    rr.resize((size_t)br * RPB, 0);
+    rt.resize((size_t)br2 * RPB, NO_TUPLE);
+    rr.resize((size_t)br2 * RPB, 0);
     u.lmin_host.resize((size_t)bl);
     u.rmax_host.resize((size_t)br);
     for (int64_t blk = 0; blk < bl; ++blk) u.lmin_host[(size_t)blk] = snp(lt[(size_t)blk * LPB], LT - 1);
@@ -1229,19 +1276,22 @@ int Dataset::prepare_tuples(int k)
         u.rmax_host[(size_t)blk] = snp(rt[(size_t)(std::min<int64_t>((blk + 1) * RPB, nr) - 1)], 0);
     const uint64_t kbytes = (uint64_t)Wt * 128;
     const uint64_t pitch = kbytes + 128;
-    // ~48 MB of left blocks per group: about a third of L2 (two dies share
-    // the 129 MB), so the group stays resident while the right blocks stream.
-    u.group = std::max<int64_t>(16, std::min<int64_t>(512, (int64_t)((48ull << 20) / (128 * pitch))));
+    u.group = tuple_group_size(Wt);
+    // amax per right block, or per pair of right blocks (form 1: the
+    // second block's, the larger; a padding block takes its partner's).
     std::vector<int> &amax = u.amax_host;
-    amax.resize((size_t)br);
-    for (int64_t b = 0; b < br; ++b)
-        amax[(size_t)b] = (int)(std::lower_bound(u.lmin_host.begin(), u.lmin_host.end(), u.rmax_host[(size_t)b]) -
+    const int64_t nb = u.enc ? br2 / 2 : br;
+    amax.resize((size_t)nb);
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t rb = u.enc ? std::min<int64_t>(2 * b + 1, br - 1) : b;
+        amax[(size_t)b] = (int)(std::lower_bound(u.lmin_host.begin(), u.lmin_host.end(), u.rmax_host[(size_t)rb]) -
                                 u.lmin_host.begin());
+    }
     u.n_items = tuple_groups(u.group, bl, amax, nullptr, u.groups_host);
     if (u.n_items >= ((int64_t)1 << 31)) return set_error(FC_ERANGE, "tensor-core strip plan too large");
     u.ngroups = (int)u.groups_host.size();
     u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
-    u.qr_bytes = std::max<size_t>((size_t)br * 128 * pitch, 1);
+    u.qr_bytes = std::max<size_t>((size_t)br2 * 128 * pitch, 1);
     if ((e = dev_alloc_pooled((void **)&u.QL, u.ql_bytes, device)) != cudaSuccess ||
         (e = dev_alloc_pooled((void **)&u.QR, u.qr_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tuple-row slab allocation");
@@ -1259,13 +1309,16 @@ int Dataset::prepare_tuples(int k)
     cudaMemcpyAsync(u.groups, u.groups_host.data(), sizeof(int4) * u.groups_host.size(), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(u.amax, amax.data(), sizeof(int) * amax.size(), cudaMemcpyHostToDevice, stream);
     if ((e = launch_gate()) != cudaSuccess ||
-        (e = launch_tuple_rows(LT, X, S_pad, Wt, u.lt, bl, (int64_t)pitch, u.QL, stream)) != cudaSuccess ||
-        (e = launch_tuple_rows(RT, X, S_pad, Wt, u.rt, br, (int64_t)pitch, u.QR, stream)) != cudaSuccess)
+        (e = launch_tuple_rows(LT, X, S_pad, W0, Wt, u.lt, bl, (int64_t)pitch, u.enc ? 0x68 : 0x38, u.QL, stream)) !=
+            cudaSuccess ||
+        (e = launch_tuple_rows(RT, X, S_pad, W0, Wt, u.rt, br2, (int64_t)pitch, u.enc ? 0x68 : 0x38, u.QR, stream)) !=
+            cudaSuccess)
         return cuda_status(e, "tuple-row kernel");
     note_launches(2);
     int rc;
     if ((rc = encode_tmap_u8(&u.tmapL, u.QL, kbytes, pitch, (uint64_t)bl * 128, 128, true)) != FC_OK) return rc;
-    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br * 128, 128, true)) != FC_OK) return rc;
+    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br2 * 128, u.enc ? 256 : 128, true)) != FC_OK)
+        return rc;
     // Host vectors go out of scope: the copies must have landed.
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tuple operands");
     u.lt_host = std::move(lt);
@@ -1351,7 +1404,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         // with SNP rows, one launch per slab of pair rows.
         // A rank range takes the tiles of its first SNPs, and the kernel
         // drops the combinations outside the range.
-        const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || triples_ready);
+        const bool tc3 = k == 3 && triples_tc_eligible(L) && (!no_alloc || (triples_ready && triples_list_fit(enc3, L) > 0));
         // Orders 4-6: tensor-core contraction of tuple rows with tuple rows.
         // A rank range takes the tiles of the left blocks holding a left
         // tuple whose combinations meet the range, and the kernel drops the
@@ -1386,7 +1439,7 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             }
             grid = std::min(sms, pa.ntiles);
         } else if (tc3) {
-            int rc = prepare_triples();
+            int rc = prepare_triples(L);
             if (rc) return rc;
             ta = triples_args(L, (float)hy, (float)(1.0 / Nd));
             ta.rank_begin = r0;
@@ -2010,7 +2063,7 @@ int fc_triples_form(const fc_handle *h)
     return guarded([&]() -> int {
         if (!h) return set_error(FC_EINVAL, "NULL handle");
         DeviceGuard g(h->ds.device);
-        return h->ds.triples_form(2048);
+        return h->ds.triples_form(0);
     });
 }
 

@@ -30,6 +30,9 @@ int check_device(int *dev, int *sms);
 int list_capacity(int64_t N);
 float score_error_bound(int k, int64_t M);
 int pow2_at_least(int v);
+// Candidate-list entries (a power of two) of the order-3 kernel in form enc
+// for lists of L with M samples within smem_cap bytes of shared memory, or -1.
+int triples_list_fit(int enc, int64_t M, int L, int smem_cap);
 // 2-D TMA descriptor over bytes: rows of inner_bytes (pitch apart), boxes of
 // 128 bytes x box_rows.
 int encode_tmap_u8(CUtensorMap *map, void *base, uint64_t inner_bytes, uint64_t pitch, uint64_t rows,
@@ -127,6 +130,7 @@ struct Dataset {
         uint8_t *QL = nullptr, *QR = nullptr;
         size_t ql_bytes = 0, qr_bytes = 0;
         uint64_t *lt = nullptr, *lr = nullptr, *rt = nullptr, *rr = nullptr;
+        int enc = 0;               // form (tuples_form)
         int4 *groups = nullptr;    // {g0, g1, lo, item_first} per group of left blocks
         int *amax = nullptr;       // [right blocks]
         int ngroups = 0;
@@ -187,13 +191,15 @@ struct Dataset {
     bool triples_tc_eligible(int L);
     int triples_form(int L) const;
     static int triples_list_size(int L);
-    int prepare_triples();
+    int triples_list_fit(int enc, int L) const;
+    int prepare_triples(int L);
     int build_slab3(int s);
     void release_triples();
     void release_pairs();
     TriplesArgs triples_args(int L, float hy, float invN);
     int triples_dense(float *scores, uint32_t *tables);
     bool tuples_tc_eligible(int k, int L);
+    int tuples_form() const;
     int prepare_tuples(int k);
     void release_tuples(int k);
     QuadsArgs tuples_args(int k, int L, float hy, float invN);
@@ -252,7 +258,7 @@ struct Tc3Batch {
     std::vector<Set> sets;
     std::vector<Launch> launches;
     std::vector<int> slot_job;       // job index of every slot
-    int n = 0, L = 0, grid = 0;
+    int n = 0, L = 0, grid = 0, smem_cap = 0;
     int level1 = 0, F = 0;           // two-level merge: groups of F lists per job
     bool rebuild = false;            // slabs rebuilt before every launch (several groups)
     std::vector<void *> allocs;      // device allocations of the plan

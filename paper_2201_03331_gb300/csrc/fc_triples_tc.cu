@@ -821,6 +821,13 @@ cudaError_t launch_pair_rows(const uint8_t *E, int64_t pitch, int Wt, int64_t S,
     return cudaGetLastError();
 }
 
+cudaError_t prepare_triples_tc_batch(int enc, size_t smem_bytes)
+{
+    if (enc != 1 && enc != 2) return cudaErrorInvalidValue;
+    void *fn = enc == 1 ? kernel_ptr<MODE_TOPN, 1, true>() : kernel_ptr<MODE_TOPN, 2, true>();
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+}
+
 cudaError_t launch_triples_tc(int mode, const CUtensorMap &tmapA, const CUtensorMap &tmapP, const TriplesArgs &a,
                               int grid, cudaStream_t st, bool set_attr)
 {

@@ -222,6 +222,10 @@ CONFIGS = {
     # enough in samples for an exhaustive oracle run.
     "Q4": dict(seed=8, S=600, cases=256, controls=256, k=4, top_n=100,
                planted=(9, 201, 402, 587), maf_range=(0.05, 0.5)),
+    # Order 4 at the size of the paper's single-node order-4 run (Table 4:
+    # 2,409 variants, 2,048 samples).
+    "T4": dict(seed=9, S=2409, cases=1024, controls=1024, k=4, top_n=100,
+               planted=(100, 900, 1700, 2300), maf_range=(0.05, 0.5)),
 }
 
 CONFIG_TITLES = {
@@ -233,6 +237,7 @@ CONFIG_TITLES = {
     "P5": "order-5 exhaustive, 152 SNPs x 2,048 samples (1,024/1,024), top 100",
     "P6": "order-6 exhaustive, 76 SNPs x 2,048 samples (1,024/1,024), top 100",
     "Q4": "order-4 exhaustive, 600 SNPs x 512 samples (256/256), top 100",
+    "T4": "order-4 exhaustive, 2,409 SNPs x 2,048 samples (1,024/1,024), top 100",
 }
 
 

@@ -215,3 +215,25 @@ def test_batch_tc3_one_job_against_oracle(fc):
         return float(oracle.mi(oracle.tables(ds.genotypes, ph[1], 3, [c]), 3)[0])
     assert_topn_equal(idx[1, :cnt[1]], score[1, :cnt[1]], o_idx, o_s, score_of)
     fc.fc_free(h)
+
+
+def test_batch_tc3_several_table_sizes(fc, monkeypatch):
+    """One-accumulator data sets with 1,200, 3,000 and 6,000 samples: three
+    launches of the same kernel with x ln x tables of different sizes (the
+    largest with the short candidate buffer) in one graph."""
+    sets = [make_dataset("s0", seed=161, S=384, cases=600, controls=600, k=3, top_n=10),
+            make_dataset("s1", seed=162, S=390, cases=1400, controls=1600, k=3, top_n=10),
+            make_dataset("s2", seed=163, S=386, cases=3000, controls=3000, k=3, top_n=10)]
+    phs = [permuted_phenotypes(ds.phenotype, 2, seed=170 + i) for i, ds in enumerate(sets)]
+    gens = [ds.genotypes for ds in sets]
+    h = fc.fc_load_batch(gens, phs)
+    a = fc.fc_search_batch(h, 3, 10)
+    assert [fc.fc_batch_job_kind(h, j) for j in range(6)] == [8] * 6
+    monkeypatch.setenv("FC_BATCH_TC3", "0")
+    h2 = fc.fc_load_batch(gens, phs)
+    c = fc.fc_search_batch(h2, 3, 10)
+    assert [fc.fc_batch_job_kind(h2, j) for j in range(6)] == [6] * 6
+    assert np.array_equal(a[0], c[0]) and np.array_equal(a[2], c[2])
+    np.testing.assert_allclose(a[1], c[1], rtol=1e-12)
+    fc.fc_free(h)
+    fc.fc_free(h2)

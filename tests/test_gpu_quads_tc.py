@@ -36,13 +36,21 @@ def path(monkeypatch):
     return set_path
 
 
+@pytest.fixture(params=["1", "0"], ids=["one-accumulator", "per-class"])
+def form(request, monkeypatch):
+    """Form 1 (controls carry 64, one accumulator n_case + 4096 n_ctrl, two
+    right blocks per tile) where both classes allow it, or form 0."""
+    monkeypatch.setenv("FC_QUADS_ENC", request.param)
+    return int(request.param)
+
+
 def all_quads(S):
     return np.array(list(itertools.combinations(range(S), 4)), dtype=np.uint32)
 
 
 @pytest.mark.parametrize("S,cases,controls,seed", [(4, 40, 50, 1), (13, 700, 650, 2), (30, 129, 1000, 3),
                                                    (41, 1500, 2100, 4), (26, 1, 300, 5), (19, 300, 1, 6)])
-def test_dense_tables_exact(fc, S, cases, controls, seed):
+def test_dense_tables_exact(fc, form, S, cases, controls, seed):
     """Every combination's 81-cell table, for pair counts that leave partial
     blocks and ragged sample counts."""
     ds = make_dataset("q4", seed=800 + seed, S=S, cases=cases, controls=controls, k=4, top_n=5)
@@ -51,6 +59,17 @@ def test_dense_tables_exact(fc, S, cases, controls, seed):
     ref = oracle.tables(ds.genotypes, ds.phenotype, 4, all_quads(S))
     bad = np.nonzero(np.any(tab != ref, axis=(1, 2)))[0]
     assert len(bad) == 0, (len(bad), all_quads(S)[bad[:5]])
+
+
+@pytest.mark.parametrize("cases,controls", [(4000, 90), (90, 4000), (4096, 300)])
+def test_dense_tables_class_limits(fc, monkeypatch, cases, controls):
+    """Near the ends of the one-accumulator range (n_case + 4096 n_ctrl up to
+    about 1.6e7) and just past it (4,096 cases: the per-class form)."""
+    monkeypatch.setenv("FC_QUADS_ENC", "1")
+    ds = make_dataset("q4e", seed=840 + cases, S=14, cases=cases, controls=controls, k=4, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    _, tab = fc.fc_tuples_dense(h, 4, scores=False, tables=True)
+    assert np.array_equal(tab, oracle.tables(ds.genotypes, ds.phenotype, 4, all_quads(14)))
 
 
 def test_dense_scores_within_fp32_bound(fc):
@@ -62,7 +81,7 @@ def test_dense_scores_within_fp32_bound(fc):
 
 
 @pytest.mark.parametrize("S,cases,controls,top_n", [(40, 900, 1100, 100), (70, 2000, 1000, 60)])
-def test_search_tc_matches_oracle(fc, path, S, cases, controls, top_n):
+def test_search_tc_matches_oracle(fc, form, path, S, cases, controls, top_n):
     path("tc")
     ds = make_dataset("q4search", seed=840 + S, S=S, cases=cases, controls=controls, k=4, top_n=top_n,
                       planted=(3, S // 3, S // 2, S - 5))
@@ -118,7 +137,7 @@ def all_k(S, k):
 
 @pytest.mark.parametrize("k,S,cases,controls,seed", [(5, 5, 40, 50, 1), (5, 14, 700, 650, 2), (5, 29, 300, 290, 3),
                                                      (6, 6, 60, 41, 4), (6, 13, 129, 600, 5), (6, 20, 1, 333, 6)])
-def test_high_order_dense_tables_exact(fc, k, S, cases, controls, seed):
+def test_high_order_dense_tables_exact(fc, form, k, S, cases, controls, seed):
     ds = make_dataset("t56", seed=870 + seed, S=S, cases=cases, controls=controls, k=k, top_n=5)
     h = fc.fc_load(ds.genotypes, ds.phenotype)
     _, tab = fc.fc_tuples_dense(h, k, scores=False, tables=True)
@@ -137,7 +156,7 @@ def test_high_order_dense_scores_within_fp32_bound(fc, k, S):
 
 
 @pytest.mark.parametrize("k,S,planted", [(5, 30, (2, 9, 15, 22, 29)), (6, 22, (1, 5, 9, 13, 17, 21))])
-def test_high_order_search_tc_matches_oracle(fc, path, k, S, planted):
+def test_high_order_search_tc_matches_oracle(fc, form, path, k, S, planted):
     path("tc")
     ds = make_dataset("t56s", seed=900 + k, S=S, cases=1024, controls=1024, k=k, top_n=40, planted=planted)
     h = fc.fc_load(ds.genotypes, ds.phenotype)

@@ -100,6 +100,38 @@ def test_dense_tables_large_classes_one_accumulator(fc, cases, controls):
     assert np.array_equal(tab, oracle.tables(ds.genotypes, ds.phenotype, 3, all_triples(40)))
 
 
+def test_dense_tables_one_accumulator_above_4096_samples(fc):
+    """4,000 cases and 3,000 controls: both classes fit the one-accumulator
+    form although the x ln x table outgrows the default candidate buffer
+    (the kernel takes the shorter buffer instead)."""
+    ds = make_dataset("t3g", seed=727, S=40, cases=4000, controls=3000, k=3, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    assert fc.fc_triples_form(h) == 1
+    _, tab = fc.fc_triples_dense(h, scores=False, tables=True)
+    assert np.array_equal(tab, oracle.tables(ds.genotypes, ds.phenotype, 3, all_triples(40)))
+
+
+def test_search_short_buffer_and_long_lists_agree_with_sweep(fc, path):
+    """A search in the one-accumulator form with the short candidate buffer
+    (6,000 samples), and one whose list needs the per-class form (top 1,500:
+    the operands are rebuilt), return the sweep's lists."""
+    ds = make_dataset("t3h", seed=728, S=400, cases=3000, controls=3000, k=3, top_n=100,
+                      planted=(21, 222, 383))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    path("tc")
+    a = fc.fc_search(h, 3, 100)
+    assert fc.fc_last_search_kind(h) == 6
+    a2 = fc.fc_search(h, 3, 1500)
+    assert fc.fc_last_search_kind(h) == 6
+    path("popc")
+    b = fc.fc_search(h, 3, 100)
+    b2 = fc.fc_search(h, 3, 1500)
+    for x, y in ((a, b), (a2, b2)):
+        assert np.array_equal(x[0], y[0])
+        np.testing.assert_allclose(x[1], y[1], rtol=1e-12)
+    assert tuple(a[0][0]) == (21, 222, 383)
+
+
 def test_dense_tables_class_of_4096_takes_the_per_class_form(fc):
     big = make_dataset("t3f", seed=726, S=40, cases=4096, controls=100, k=3, top_n=5)
     hb = fc.fc_load(big.genotypes, big.phenotype)

@@ -10,57 +10,100 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 // Contingency table of one combination (Section "Computing the contingency
-// tables"): each cell is the AND of one genotype row per SNP, popcounted;
-// lanes split the 128-bit words and the warp reduces.  tab is [3^k][2],
-// column 0 = cases.  Cell digits follow the order of c[] (first SNP most
-// significant), as in Fig. 3.
-__device__ void warp_table(const uint4 *X, int64_t Sp, int W0, int Wt, int k, const uint32_t *c,
-                           uint32_t *tab)
+// tables"): each cell is the AND of one genotype row per SNP, popcounted.
+// Lane w takes the 128-bit words w, w + 32, ..; the 3k genotype rows of its
+// word are staged in the warp's shared-memory area rows[3k][32] (uint4), so
+// that every cell reads them from there instead of from memory, and the
+// warp reduces each cell.  The table goes to stab[3^k][2] (shared memory,
+// column 0 = cases) and, when tab is not null, to tab.  Cell digits follow
+// the order of c[] (first SNP most significant), as in Fig. 3.
+__device__ void warp_table(const uint4 *X, int64_t Sp, int W0, int Wt, int k, const uint32_t *c, uint4 *rows,
+                           uint32_t *stab, uint32_t *tab)
 {
     const int lane = threadIdx.x & 31;
     const int cells = pow3(k);
-    for (int cell = 0; cell < cells; ++cell) {
-        uint32_t s0 = 0, s1 = 0;
-        for (int w = lane; w < Wt; w += 32) {
+    for (int x = lane; x < 2 * cells; x += 32) stab[x] = 0;
+    __syncwarp();
+    for (int w0 = 0; w0 < Wt; w0 += 32) {
+        const int w = w0 + lane;
+        for (int r = 0; r < 3 * k; ++r) {   // row r = 3 t + g: genotype g of SNP c[t]
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (w < Wt) v = X[((size_t)w * 3 + r % 3) * Sp + c[r / 3]];
+            rows[r * 32 + lane] = v;
+        }
+        const bool cases = w < W0;
+        for (int cell = 0; cell < cells; ++cell) {
             uint4 v = make_uint4(~0u, ~0u, ~0u, ~0u);
             int rem = cell;
             for (int t = k - 1; t >= 0; --t) {
-                const int g = rem % 3;
+                const uint4 x = rows[(3 * t + rem % 3) * 32 + lane];
                 rem /= 3;
-                const uint4 x = X[((size_t)w * 3 + g) * Sp + c[t]];
                 v.x &= x.x; v.y &= x.y; v.z &= x.z; v.w &= x.w;
             }
             const uint32_t p = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-            if (w < W0) s0 += p; else s1 += p;
+            const uint32_t s0 = __reduce_add_sync(FULL, cases ? p : 0u);
+            const uint32_t s1 = __reduce_add_sync(FULL, cases ? 0u : p);
+            if (lane == 0) {
+                stab[2 * cell] += s0;
+                stab[2 * cell + 1] += s1;
+            }
         }
-        s0 = __reduce_add_sync(FULL, s0);
-        s1 = __reduce_add_sync(FULL, s1);
-        if (lane == 0) {
-            tab[2 * cell] = s0;
-            tab[2 * cell + 1] = s1;
-        }
+        __syncwarp();
     }
-    __syncwarp();
+    if (tab)
+        for (int x = lane; x < 2 * cells; x += 32) tab[x] = stab[x];
 }
 
-// MI(X;Y) = H(X) + H(Y) - H(X,Y), plug-in probabilities n/N, FP64, cell order.
-__device__ double mi_fp64(const uint32_t *tab, int cells)
+// Double-precision sum over the warp in a fixed order (a butterfly), the
+// same on every lane.
+__device__ double warp_sum64(double v)
 {
-    double n0 = 0.0, n1 = 0.0;
-    for (int x = 0; x < cells; ++x) { n0 += tab[2 * x]; n1 += tab[2 * x + 1]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// MI(X;Y) = H(X) + H(Y) - H(X,Y) of the table stab[cells][2], plug-in
+// probabilities n/N, FP64; lane x takes the cells x, x + 32, .. and the warp
+// sums the terms.  Every lane returns the value.
+__device__ double warp_mi_fp64(const uint32_t *stab, int cells)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t c0 = 0, c1 = 0;
+    for (int x = lane; x < cells; x += 32) { c0 += stab[2 * x]; c1 += stab[2 * x + 1]; }
+    const double n0 = (double)__reduce_add_sync(FULL, c0), n1 = (double)__reduce_add_sync(FULL, c1);
     const double N = n0 + n1;
     if (N <= 0.0) return 0.0;
-    double hx = 0.0, hxy = 0.0, hy = 0.0;
-    for (int x = 0; x < cells; ++x) {
-        const double a = tab[2 * x], b = tab[2 * x + 1];
+    double hx = 0.0, hxy = 0.0;
+    for (int x = lane; x < cells; x += 32) {
+        const double a = stab[2 * x], b = stab[2 * x + 1];
         const double nx = a + b;
         if (nx > 0.0) hx -= (nx / N) * log(nx / N);
         if (a > 0.0) hxy -= (a / N) * log(a / N);
         if (b > 0.0) hxy -= (b / N) * log(b / N);
     }
+    hx = warp_sum64(hx);
+    hxy = warp_sum64(hxy);
+    double hy = 0.0;
     if (n0 > 0.0) hy -= (n0 / N) * log(n0 / N);
     if (n1 > 0.0) hy -= (n1 / N) * log(n1 / N);
     return hx + hy - hxy;
+}
+
+// Shared memory of one warp of the table kernels: the staged rows and the
+// table.
+__host__ __device__ constexpr size_t warp_table_smem(int k)
+{
+    return (size_t)3 * k * 32 * 16 + ((size_t)pow3(k) * 8 + 15) / 16 * 16;
+}
+
+// This warp's area of the dynamic shared memory of a table kernel.
+__device__ __forceinline__ void warp_area(int k, uint4 *&rows, uint32_t *&stab)
+{
+    extern __shared__ uint4 smem_w[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(smem_w) + (size_t)(threadIdx.x >> 5) * warp_table_smem(k);
+    rows = reinterpret_cast<uint4 *>(base);
+    stab = reinterpret_cast<uint32_t *>(base + (size_t)3 * k * 32 * 16);
 }
 
 __global__ void k_rescore(RescoreArgs a)
@@ -84,10 +127,13 @@ __global__ void k_rescore(RescoreArgs a)
     }
     uint32_t c[KMAX_TABLES];
     unrank(a.S, a.k, r, c);
-    uint32_t *tab = a.res_tab + (size_t)i * cells * 2;
-    warp_table(a.X, a.S_pad, a.W0, a.Wt, a.k, c, tab);
+    uint4 *rows;
+    uint32_t *stab;
+    warp_area(a.k, rows, stab);
+    warp_table(a.X, a.S_pad, a.W0, a.Wt, a.k, c, rows, stab, a.res_tab ? a.res_tab + (size_t)i * cells * 2 : nullptr);
+    const double mi = warp_mi_fp64(stab, cells);
     if (lane == 0) {
-        a.res_s[i] = mi_fp64(tab, cells);
+        a.res_s[i] = mi;
         a.res_r[i] = r;
     }
 }
@@ -153,10 +199,14 @@ __global__ void k_rescore_batch(RescoreBatchArgs a)
     }
     uint32_t c[KMAX_TABLES];
     unrank(jd.S, a.k, r, c);
-    uint32_t *tab = a.res_tab + ((size_t)job * a.L + i) * cells * 2;
-    warp_table(jd.X, jd.S_pad, jd.W0, jd.Wt, a.k, c, tab);
+    uint4 *rows;
+    uint32_t *stab;
+    warp_area(a.k, rows, stab);
+    warp_table(jd.X, jd.S_pad, jd.W0, jd.Wt, a.k, c, rows, stab,
+               a.res_tab ? a.res_tab + ((size_t)job * a.L + i) * cells * 2 : nullptr);
+    const double mi = warp_mi_fp64(stab, cells);
     if (lane == 0) {
-        res_s[i] = mi_fp64(tab, cells);
+        res_s[i] = mi;
         res_r[i] = r;
     }
 }
@@ -207,15 +257,25 @@ __global__ void k_tables(TablesArgs a)
     if (i >= a.n) return;
     uint32_t c[KMAX_TABLES];
     for (int t = 0; t < a.k; ++t) c[t] = a.combos[i * a.k + t];
-    warp_table(a.X, a.S_pad, a.W0, a.Wt, a.k, c, a.out + (size_t)i * pow3(a.k) * 2);
+    uint4 *rows;
+    uint32_t *stab;
+    warp_area(a.k, rows, stab);
+    warp_table(a.X, a.S_pad, a.W0, a.Wt, a.k, c, rows, stab, a.out + (size_t)i * pow3(a.k) * 2);
 }
+
+// Warps per block of the table kernels: their shared memory stays within the
+// 48 KiB that needs no opt-in (4.7 KiB a warp at order 3, 14.7 KiB at order 6).
+int table_warps_per_block(int k) { return k <= 3 ? 8 : k <= 5 ? 4 : 3; }
+static_assert(8 * warp_table_smem(3) <= 48 * 1024 && 4 * warp_table_smem(5) <= 48 * 1024 &&
+                  3 * warp_table_smem(6) <= 48 * 1024,
+              "table kernels within the default shared memory");
 
 }  // namespace
 
 cudaError_t launch_rescore(const RescoreArgs &a, cudaStream_t st)
 {
-    const int wpb = 8;
-    k_rescore<<<(a.L + wpb - 1) / wpb, wpb * 32, 0, st>>>(a);
+    const int wpb = table_warps_per_block(a.k);
+    k_rescore<<<(a.L + wpb - 1) / wpb, wpb * 32, wpb * warp_table_smem(a.k), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -231,9 +291,9 @@ cudaError_t launch_final_sort(double *res_s, uint64_t *res_r, int L, int N, int 
 
 cudaError_t launch_rescore_batch(const RescoreBatchArgs &a, cudaStream_t st)
 {
-    const int wpb = 8;
+    const int wpb = table_warps_per_block(a.k);
     const int64_t warps = (int64_t)a.n_jobs * a.L;
-    k_rescore_batch<<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, 0, st>>>(a);
+    k_rescore_batch<<<(unsigned)((warps + wpb - 1) / wpb), wpb * 32, wpb * warp_table_smem(a.k), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -252,9 +312,9 @@ cudaError_t launch_final_sort_batch(const JobDesc *jobs, int n_jobs, double *res
 cudaError_t launch_tables(const TablesArgs &a, cudaStream_t st)
 {
     if (a.n == 0) return cudaSuccess;
-    const int wpb = 8;
+    const int wpb = table_warps_per_block(a.k);
     const int64_t blocks = (a.n + wpb - 1) / wpb;
-    k_tables<<<(unsigned)blocks, wpb * 32, 0, st>>>(a);
+    k_tables<<<(unsigned)blocks, wpb * 32, wpb * warp_table_smem(a.k), st>>>(a);
     return cudaGetLastError();
 }
 

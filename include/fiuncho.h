@@ -344,6 +344,18 @@ int fc_last_search_kind(const fc_handle *h);
  */
 int fc_sweep_tables(fc_handle *h, int k, uint64_t rank_begin, int64_t n, uint32_t *out);
 
+/*
+ * fc_log2_approx - the base-2 logarithm that the order-3 tensor-core
+ * epilogue takes for its n ln n terms (the hardware approximation), of
+ * max(n[i], 1) for count integers n[i] < 2^23 (host uint32 in, host float
+ * out), computed on the current device.  A parity hook: the epilogue's FP32
+ * error bound (Section "Background": the mutual information; see
+ * fc_search) assumes |result - log2(n)| <= 2^-21 for 1 <= n <= 2^17, which a
+ * test checks for every such n.  FC_EINVAL for count < 0 or NULL buffers;
+ * FC_ENOMEM / FC_ECUDA as the other calls.
+ */
+int fc_log2_approx(const uint32_t *n, int64_t count, float *out);
+
 /* fc_info - sizes of a loaded data set (any pointer may be NULL). */
 int fc_info(const fc_handle *h, int64_t *S, int64_t *M, int64_t *cases, int64_t *controls);
 

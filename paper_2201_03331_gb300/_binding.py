@@ -44,6 +44,7 @@ _SIGNATURES = {
     "fc_tables": ([P, i32, P, i64, P], i32),
     "fc_scores": ([P, i32, u64, i64, P], i32),
     "fc_info": ([P, P, P, P, P], i32),
+    "fc_log2_approx": ([P, i64, P], i32),
     "fc_pairs_dense": ([P, P, P], i32),
     "fc_triples_dense": ([P, P, P], i32),
     "fc_tuples_dense": ([P, i32, P, P], i32),
@@ -180,6 +181,14 @@ def fc_tables(h: Handle, k: int, combos) -> np.ndarray:
     c = np.ascontiguousarray(np.asarray(combos, dtype=np.uint32).reshape(-1, k))
     out = np.zeros((c.shape[0], 3 ** k, 2), dtype=np.uint32)
     _check(library().fc_tables(h.ptr, k, _ptr(c), c.shape[0], _ptr(out)), "fc_tables")
+    return out
+
+
+def fc_log2_approx(n) -> np.ndarray:
+    """The epilogue's hardware base-2 logarithm of ``max(n, 1)`` (float32)."""
+    a = np.ascontiguousarray(np.asarray(n, dtype=np.uint32).ravel())
+    out = np.zeros(a.shape[0], dtype=np.float32)
+    _check(library().fc_log2_approx(_ptr(a), a.shape[0], _ptr(out)), "fc_log2_approx")
     return out
 
 

@@ -319,7 +319,7 @@ struct TriplesArgs {
     const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
     const uint4 *PR;        // restricted pair table [S_pad][S_pad]
     const float *xlogx;     // x ln x for x = 0..M (FP64 rounded once to FP32)
-    int M;
+    int M;                  // extent of the kernel's x ln x table: at least every class count
     float hy, invN;
     uint64_t total;         // C(S, 3)
     uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count
@@ -336,6 +336,9 @@ struct TriplesArgs {
 };
 
 int triples_pairs_per_tile(int enc);
+// The base-2 logarithm the tensor-core epilogues take for n ln n, of
+// max(n & (2^23 - 1), 1), for n[0 .. count).
+cudaError_t launch_log2_approx(const uint32_t *n, int64_t count, float *out, cudaStream_t st);
 // Candidates one round of the kernel's epilogue may add to its buffer.
 int triples_round_candidates();
 size_t triples_smem_bytes(int enc, int M, int P2);

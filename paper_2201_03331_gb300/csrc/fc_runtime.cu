@@ -353,11 +353,16 @@ float score_error_bound(int k, int64_t M)
     // 2*3^k accumulations adds <= u N ln 2 (partial sums are bounded by
     // N H(Y|X) <= N ln 2); the final scaling and subtraction <= 3u ln 2.
     // Divided by N: |MI32 - MI| <= u (2 ln M + (2*3^k + 6) ln 2).  The
-    // tensor-core epilogues' x ln x form has the smaller bound
-    // u (3 ln M + (3^k + 4) ln 2) for every M used here.  Doubled for margin.
+    // orders 4-6 tensor-core epilogue's x ln x form has the smaller bound
+    // u (3 ln M + (3^k + 4) ln 2) for every M used here; the order-3 one,
+    // whose n ln n terms come from the hardware logarithm (relative error
+    // 2^-22 plus 2^-22 absolute), u (7 ln M + 35 ln 2).  The larger, doubled
+    // for margin.
     const double u = std::ldexp(1.0, -24);
     const double terms = 2.0 * pow3(k);
-    const double e = u * (2.0 * std::log((double)std::max<int64_t>(M, 2)) + (terms + 6.0) * std::log(2.0));
+    const double lm = std::log((double)std::max<int64_t>(M, 2));
+    double e = u * (2.0 * lm + (terms + 6.0) * std::log(2.0));
+    if (k == 3) e = std::max(e, u * (7.0 * lm + 35.0 * std::log(2.0)));
     return (float)(2.0 * e);
 }
 
@@ -746,7 +751,13 @@ int triples_list_fit(int enc, int64_t M, int L, int smem_cap)
     return -1;
 }
 
-int Dataset::triples_list_fit(int enc, int L) const { return fc::triples_list_fit(enc, M, L, max_smem_optin); }
+// The order-3 kernel's x ln x table needs the class counts only (n ln n of a
+// cell's total comes from the hardware logarithm), so its extent is the
+// larger class.
+int Dataset::triples_list_fit(int enc, int L) const
+{
+    return fc::triples_list_fit(enc, std::max(M1, M0), L, max_smem_optin);
+}
 
 bool Dataset::triples_tc_eligible(int L)
 {
@@ -776,7 +787,7 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.marg4 = reinterpret_cast<const uint4 *>(marg);
     ta.PR = PR;
     ta.xlogx = xlogx;
-    ta.M = (int)M;
+    ta.M = (int)std::max(M1, M0);   // table extent: the class counts
     ta.hy = hy;
     ta.invN = invN;
     ta.total = binom(S, 3);
@@ -2126,6 +2137,28 @@ int fc_sweep_tables(fc_handle *h, int k, uint64_t rank_begin, int64_t n, uint32_
             return set_error(FC_EINVAL, "rank range outside [0, C(S, k))");
         DeviceGuard g(h->ds.device);
         return h->ds.sweep_dump(k, MODE_TABLES, rank_begin, n, out);
+    });
+}
+
+int fc_log2_approx(const uint32_t *n, int64_t count, float *out)
+{
+    return guarded([&]() -> int {
+        if (count < 0 || (count > 0 && (!n || !out))) return set_error(FC_EINVAL, "bad buffers");
+        if (count == 0) return FC_OK;
+        uint32_t *dn = nullptr;
+        float *dout = nullptr;
+        cudaError_t e = dev_alloc((void **)&dn, sizeof(uint32_t) * (size_t)count);
+        if (e != cudaSuccess) return cuda_status(e, "alloc");
+        if ((e = dev_alloc((void **)&dout, sizeof(float) * (size_t)count)) != cudaSuccess) {
+            cudaFree(dn);
+            return cuda_status(e, "alloc");
+        }
+        if ((e = cudaMemcpy(dn, n, sizeof(uint32_t) * (size_t)count, cudaMemcpyHostToDevice)) == cudaSuccess &&
+            (e = launch_log2_approx(dn, count, dout, 0)) == cudaSuccess)
+            e = cudaMemcpy(out, dout, sizeof(float) * (size_t)count, cudaMemcpyDeviceToHost);
+        cudaFree(dn);
+        cudaFree(dout);
+        return e == cudaSuccess ? FC_OK : cuda_status(e, "log2 probe");
     });
 }
 

@@ -70,6 +70,22 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
+// The same test, letting the hardware suspend the thread until the phase
+// completes or about 20 us pass (a waiting warp then issues nothing, which
+// leaves the issue slots of its scheduler to the epilogue warps).
+__device__ __forceinline__ bool mbar_try_suspend(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase of the given parity.  On timeout it raises the
 // CTA abort flag and the device error word; every role then leaves its loop.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
@@ -77,7 +93,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try(bar, parity)) {
+    while (!mbar_try_suspend(bar, parity)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > budget) {
             *abort_flag = 1;

@@ -45,15 +45,21 @@
 // three load stages are owned by three producer warps that each issue the
 // copies of their own stage (fill f by warp f mod 3).
 //
-// The epilogue scores with a table of x ln x instead of ln x: per cell
-// t = (xl[n] - xl[a]) - xl[b] = a ln(n/a) + b ln(n/b), MI = H(Y) - sum t / N.
-// With each entry correctly rounded (relative error u = 2^-24), a cell errs
-// by at most u n (2 ln M) from the entries, u n ln M from the first
-// subtraction and u n ln 2 from the second; over the 27 cells (sum n = N),
-// the 27 accumulations (partial sums <= N ln 2) and the final scaling this
-// gives |MI32 - MI| <= u (3 ln M + 31 ln 2), within the sweep's bound
-// u (2 ln M + 60 ln 2) for every M < 2^29, so the same FP64 rescoring window
-// applies.
+// The epilogue scores each cell as t = n ln n - xl[a] - xl[b] = a ln(n/a) +
+// b ln(n/b) (a, b the class counts, n = a + b), MI = H(Y) - sum t / N, where
+// xl is a shared-memory table of x ln x over the class counts (entries
+// correctly rounded) and n ln n comes from the hardware base-2 logarithm:
+// n (ln 2 lg2~(n)), with |lg2~(n) - log2 n| <= 2^-22 (log2 n + 1) for every
+// integer 1 <= n <= 2^17 (checked exhaustively on the device by a test;
+// fc_log2_approx).  Moving one of the three lookups per cell to the XU pipe
+// relieves the shared-memory pipe.  With u = 2^-24 (so 2^-22 = 4u), a cell
+// errs by at most n (4u (ln M + ln 2) + u ln M) from the n ln n term,
+// u (a + b) ln M from the table entries, u n ln M from the fused
+// multiply-subtract and u n ln 2 from the last subtraction; over the 27 cells
+// (sum n = N), the 27 accumulations (partial sums <= N ln 2) and the final
+// scaling this gives |MI32 - MI| <= u (7 ln M + 35 ln 2), which the FP64
+// rescoring window of the library covers (twice the larger of this and the
+// sweep's bound).
 //
 // Roles (one persistent CTA per SM, 640 threads):
 //   warps 0-2  : producers (lane 0 issues the TMA copies of its stage)
@@ -92,8 +98,9 @@ struct T3Shape {
     static constexpr int ROUNDS = (QUADS + T3_PARTS - 1) / T3_PARTS;
 };
 
-// Entries of the shared-memory x ln x table: the power of two above M (the
-// entries beyond M are 0), so that a masked index never leaves it.
+// Entries of the shared-memory x ln x table: the power of two above its
+// extent M (the entries beyond M are 0), so that a masked index never leaves
+// it.
 __host__ __device__ inline int xl_table_size(int M)
 {
     int n = 4;
@@ -129,6 +136,23 @@ __device__ __forceinline__ uint32_t unpack_enc(uint32_t bits)
 {
     const uint32_t v = __float2uint_rz(__uint_as_float(bits));
     return v + (v >> 12) * 61440u;
+}
+
+constexpr float LN2F = 0.693147180559945309f;
+
+// Hardware base-2 logarithm (MUFU), flush-to-zero; x >= 1 here.
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// An integer below 2^23 as a float, exactly: its bits under the exponent of
+// 2^23, minus 2^23.
+__device__ __forceinline__ float u2f_small(uint32_t n)
+{
+    return __uint_as_float(n | 0x4B000000u) - 8388608.0f;
 }
 
 // BATCH: the items of several jobs (T3Job), job-major, in one launch; the
@@ -634,10 +658,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
 #pragma unroll
                         for (int x = 0; x < 27; ++x) {
                             // Masked so that no index can leave the table
-                            // (exact counts, a + b <= M, are below its size).
+                            // (exact class counts are below its size).
                             const uint32_t ca = T[x] & tmask, cb = (T[x] >> 16) & tmask;
-                            const uint32_t n = (ca + cb) & tmask;
-                            hs[x % 3] += (xltab[n] - xltab[ca]) - xltab[cb];
+                            const float nf = fmaxf(u2f_small(ca + cb), 1.0f);   // n ln n = 0 at n = 0, 1
+                            hs[x % 3] += fmaf(nf, LN2F * lg2_approx(nf), -xltab[ca]) - xltab[cb];
                         }
                         hsum = (hs[0] + hs[1]) + hs[2];
                     }
@@ -799,6 +823,21 @@ cudaError_t launch_fill_lists(float *s, uint64_t *r, size_t n, cudaStream_t st)
     if (n == 0) return cudaSuccess;
     const size_t blocks = std::min<size_t>((n + 255) / 256, 4096);
     k_fill_lists<<<(unsigned)blocks, 256, 0, st>>>(s, r, n);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_log2_approx(const uint32_t *n, int64_t count, float *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = lg2_approx(fmaxf(u2f_small(n[i] & 0x7fffffu), 1.0f));
+}
+}  // namespace
+
+cudaError_t launch_log2_approx(const uint32_t *n, int64_t count, float *out, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    k_log2_approx<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(n, count, out);
     return cudaGetLastError();
 }
 

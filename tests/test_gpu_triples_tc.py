@@ -15,8 +15,13 @@ pytestmark = pytest.mark.gpu
 
 
 def fp32_bound(k, M):
+    """The library's window: twice the larger of the sweep's bound and the
+    order-3 tensor-core epilogue's u (7 ln M + 35 ln 2), whose n ln n terms
+    come from the hardware logarithm."""
     u = 2.0 ** -24
-    return 2.0 * u * (2.0 * math.log(max(M, 2)) + (2.0 * 3 ** k + 6.0) * math.log(2.0))
+    lm = math.log(max(M, 2))
+    sweep = u * (2.0 * lm + (2.0 * 3 ** k + 6.0) * math.log(2.0))
+    return 2.0 * max(sweep, u * (7.0 * lm + 35.0 * math.log(2.0)))
 
 
 @pytest.fixture(scope="module")
@@ -224,3 +229,16 @@ def test_triples_dense_rejects_bad_inputs(fc):
     h1 = fc.fc_load(one.genotypes, one.phenotype)
     with pytest.raises(fc.FiunchoError):
         fc.fc_triples_dense(h1, scores=True)         # a single class
+
+
+def test_log2_approx_error_within_assumed_bound(fc):
+    # The epilogue's error bound takes n ln n from the hardware base-2
+    # logarithm with |lg2~(n) - log2 n| <= 2^-22 (log2 n + 1) for every
+    # integer count 1 <= n <= 2^17: checked here for all of them (n = 0 is
+    # taken as 1).
+    n = np.arange(0, 2 ** 17 + 1, dtype=np.uint32)
+    lg = fc.fc_log2_approx(n).astype(np.float64)
+    exact = np.log2(np.maximum(n, 1).astype(np.float64))
+    err = np.abs(lg - exact)
+    assert (err <= 2.0 ** -22 * (exact + 1.0)).all(), (err / (exact + 1.0)).max()
+    assert lg[0] == 0.0 and lg[1] == 0.0

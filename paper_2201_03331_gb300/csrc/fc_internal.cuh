@@ -373,14 +373,18 @@ constexpr int tc_left_size(int k) { return k == 6 ? 3 : 2; }
 constexpr int tc_tuples_per_block(int T) { return 4 * (27 / (T == 2 ? 9 : 27)); }
 constexpr uint64_t NO_TUPLE = ~0ull;
 struct QuadsArgs {
-    // Tiles (left block a, right block b) come in strips: item q of the
-    // launch is (group g, right block b = lo + q - item_first) of the group
-    // {g0, g1, lo, item_first} with the first item_first <= q, and its tiles
-    // are the left blocks a in [g0, min(g1, amax[b])) (those with include[a]
-    // set, if include is not null).  Within a group the right blocks stream
-    // while the group's left blocks stay in L2.
+    // Tiles (left block a, right block b) come in strips of at most `sub`
+    // left blocks: with r = q - item_first and n = ceil((g1 - g0) / sub),
+    // item q of the launch is (group g, right block b = lo + r / n, strip
+    // r % n) of the group {g0, g1, lo, item_first} with the first
+    // item_first <= q, and its tiles are the left blocks a in
+    // [g0 + sub (r % n), g0 + sub (r % n + 1)) below min(g1, amax[b]) (those
+    // with include[a] set, if include is not null).  Within a group the right
+    // blocks stream while the group's left blocks stay in L2; consecutive
+    // items share a right block, so the CTAs in flight hold few of them.
     const int4 *groups;     // by item_first (enc 1: right block pairs in place of right blocks)
     int ngroups;
+    int sub;
     int enc;                // 1: one accumulator n_case + 4096 n_ctrl, two right blocks per tile
     int n_items;
     const int *amax;        // [right blocks]: left blocks whose smallest last SNP is below the block's largest first SNP

@@ -408,13 +408,15 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1) k_pairs_tc(const __grid_cons
                     for (int q = 0; q < 8; ++q) {
                         const bool cand = val[q] && sc[q] >= gthr && better(sc[q], rk[q], thr_s, thr_r);
                         const unsigned m = __ballot_sync(FULL, cand);
-                        int base = 0;
-                        if (lane == 0 && m) base = atomicAdd(&buf_count, __popc(m));
-                        base = __shfl_sync(FULL, base, 0);
-                        if (cand) {
-                            const int slot = L + base + __popc(m & ((1u << lane) - 1u));
-                            lscore[slot] = sc[q];
-                            lrank[slot] = rk[q];
+                        if (m) {
+                            int base = 0;
+                            if (lane == 0) base = atomicAdd(&buf_count, __popc(m));
+                            base = __shfl_sync(FULL, base, 0);
+                            if (cand) {
+                                const int slot = L + base + __popc(m & ((1u << lane) - 1u));
+                                lscore[slot] = sc[q];
+                                lrank[slot] = rk[q];
+                            }
                         }
                     }
                 }

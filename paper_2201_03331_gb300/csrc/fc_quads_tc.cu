@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
             // The strip being handed out: right block s_b, left blocks
             // [s_a, s_aend); the group of the last item taken.
             int s_b = 0, s_a = 0, s_aend = 0;
-            int s_first = 0, s_end = 0, s_lo = 0, s_g0 = 0, s_g1 = 0;
+            int s_first = 0, s_end = 0, s_lo = 0, s_g0 = 0, s_g1 = 0, s_n = 1;
             auto next_tile = [&](int &ta, int &tb) -> bool {
                 for (;;) {
                     while (s_a < s_aend) {
@@ -272,10 +272,12 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                         s_lo = gr.z;
                         s_first = gr.w;
                         s_end = lo + 1 < a.ngroups ? a.groups[lo + 1].w : a.n_items;
+                        s_n = (s_g1 - s_g0 + a.sub - 1) / a.sub;
                     }
-                    s_b = s_lo + (q - s_first);
-                    s_a = s_g0;
-                    s_aend = min(s_g1, a.amax[s_b]);
+                    const int r = q - s_first;
+                    s_b = s_lo + r / s_n;
+                    s_a = s_g0 + (r % s_n) * a.sub;
+                    s_aend = min(min(s_a + a.sub, s_g1), a.amax[s_b]);
                 }
             };
             auto publish = [&](int k) -> bool {
@@ -473,13 +475,15 @@ __global__ void __launch_bounds__(TC_THREADS_MP, 1)
                     for (int q = 0; q < RPC; ++q) {
                         const bool cand = val[q] && sc[q] >= gthr && better(sc[q], rk[q], thr_s, thr_r);
                         const unsigned mk = __ballot_sync(FULL, cand);
-                        int base = 0;
-                        if (lane == 0 && mk) base = atomicAdd(&buf_count, __popc(mk));
-                        base = __shfl_sync(FULL, base, 0);
-                        if (cand) {
-                            const int s2 = L + base + __popc(mk & ((1u << lane) - 1u));
-                            lscore[s2] = sc[q];
-                            lrank[s2] = rk[q];
+                        if (mk) {
+                            int base = 0;
+                            if (lane == 0) base = atomicAdd(&buf_count, __popc(mk));
+                            base = __shfl_sync(FULL, base, 0);
+                            if (cand) {
+                                const int s2 = L + base + __popc(mk & ((1u << lane) - 1u));
+                                lscore[s2] = sc[q];
+                                lrank[s2] = rk[q];
+                            }
                         }
                     }
                 }

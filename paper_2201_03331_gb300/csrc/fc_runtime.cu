@@ -1077,6 +1077,28 @@ void enum_tuples(int64_t S, int T, bool left, int other, std::vector<uint64_t> &
 
 // Left blocks per group: ~48 MB of them, about a third of L2 (two dies share
 // the 129 MB), so that a group stays resident while the right blocks stream.
+// A scheduler item is a strip of at most `sub` of them against one right
+// block (form 1: block pair), so that the CTAs in flight share right blocks:
+// with one strip per (group, right block) the 152 CTAs each held their own
+// right block (117 MB of them at 6000 samples beside the group), and the
+// order-4 search read 2 TB from DRAM per launch instead of 35 GB.  Long
+// strips are otherwise better (a CTA keeps its right tuples' data in L1:
+// orders 5 and 6 at 2048 samples ran 10 % slower with one left block per
+// item), so `sub` is the largest power of two whose right blocks in flight,
+// about sms * sub / group of them, stay within 32 MB, and the smallest that
+// keeps the item count an int (FC_TUPLES_STRIP overrides it).
+int64_t tuple_strip(int64_t group, int64_t bl, int64_t br, int sms, double item_bytes)
+{
+    int64_t sub = 1;
+    while (2 * sub <= group && (double)sms * (double)(2 * sub) / (double)group * item_bytes <= 32.0 * 1048576.0)
+        sub *= 2;
+    if (const char *v = getenv("FC_TUPLES_STRIP")) sub = std::max<int64_t>(1, atol(v));
+    for (;; sub *= 2) {
+        const double items = (double)(bl / group + 1) * (double)br * (double)((group + sub - 1) / sub);
+        if (items < 2147483647.0 || sub >= group) return sub;
+    }
+}
+
 int64_t tuple_group_size(int Wt)
 {
     const uint64_t pitch = (uint64_t)Wt * 128 + 128;
@@ -1109,7 +1131,8 @@ bool Dataset::tuples_tc_eligible(int k, int L)
     // as in prepare_tuples).
     if (bl >= ((int64_t)1 << 31) / 128 || br >= ((int64_t)1 << 31) / 128) return false;
     const int64_t group = tuple_group_size(Wt);
-    if ((double)(bl / group + 1) * (double)br >= 2147483647.0) return false;
+    const int64_t sub = tuple_strip(group, bl, br, sms, 128.0 * ((double)Wt * 128 + 128));
+    if ((double)(bl / group + 1) * (double)br * (double)((group + sub - 1) / sub) >= 2147483647.0) return false;
     // Both slabs stay resident: at most 60 % of the free memory (FC_TUPLES_SLAB_MB caps it).
     const double slab = (double)(bl + br) * 128.0 * ((double)Wt * 128 + 128);
     size_t free_b = 0, total_b = 0;
@@ -1147,6 +1170,7 @@ QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)
     const TupleTC &u = tup[k - 4];
     QuadsArgs qa{};
     qa.groups = u.groups;
+    qa.sub = (int)u.sub;
     qa.ngroups = u.ngroups;
     qa.enc = u.enc;
     qa.n_items = (int)u.n_items;
@@ -1206,9 +1230,11 @@ void Dataset::release_tuples(int k)
 namespace {
 // Groups {g0, g1, lo, item_first} of `group` left blocks (those with some
 // include[a] set, if include is not null): lo is the first right block with
-// a tile in the group; the group's items are its right blocks lo .. br - 1.
-int64_t tuple_groups(int64_t group, int64_t bl, const std::vector<int> &amax, const std::vector<char> *include,
-                     std::vector<int4> &groups)
+// a tile in the group; the group's items are its right blocks lo .. br - 1,
+// each split into ceil((g1 - g0) / sub) strips of `sub` left blocks (a strip
+// beyond the right block's amax is empty).
+int64_t tuple_groups(int64_t group, int64_t sub, int64_t bl, const std::vector<int> &amax,
+                     const std::vector<char> *include, std::vector<int4> &groups)
 {
     groups.clear();
     const int64_t br = (int64_t)amax.size();
@@ -1224,7 +1250,8 @@ int64_t tuple_groups(int64_t group, int64_t bl, const std::vector<int> &amax, co
         const int64_t lo = std::upper_bound(amax.begin(), amax.end(), (int)g0) - amax.begin();
         if (lo >= br) continue;
         groups.push_back(make_int4((int)g0, (int)g1, (int)lo, (int)items));
-        items += br - lo;
+        items += (br - lo) * ((g1 - g0 + sub - 1) / sub);
+        if (items >= ((int64_t)1 << 31)) return items;
     }
     return items;
 }
@@ -1298,7 +1325,8 @@ int Dataset::prepare_tuples(int k)
         amax[(size_t)b] = (int)(std::lower_bound(u.lmin_host.begin(), u.lmin_host.end(), u.rmax_host[(size_t)rb]) -
                                 u.lmin_host.begin());
     }
-    u.n_items = tuple_groups(u.group, bl, amax, nullptr, u.groups_host);
+    u.sub = tuple_strip(u.group, bl, nb, sms, (u.enc ? 2.0 : 1.0) * 128.0 * (double)pitch);
+    u.n_items = tuple_groups(u.group, u.sub, bl, amax, nullptr, u.groups_host);
     if (u.n_items >= ((int64_t)1 << 31)) return set_error(FC_ERANGE, "tensor-core strip plan too large");
     u.ngroups = (int)u.groups_host.size();
     u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
@@ -1488,7 +1516,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                     const uint64_t first = rank_of(S, k, c);
                     if (first < r1 && first + count > r0) include[x / (size_t)LPB] = 1;
                 }
-                nt = tuple_groups(u.group, (int64_t)u.lmin_host.size(), u.amax_host, &include, range_groups4);
+                nt = tuple_groups(u.group, u.sub, (int64_t)u.lmin_host.size(), u.amax_host, &include,
+                                  range_groups4);
                 qa.n_items = (int)nt;
                 qa.ngroups = (int)range_groups4.size();
                 qa.rank_begin = r0;

@@ -134,7 +134,7 @@ struct Dataset {
         int4 *groups = nullptr;    // {g0, g1, lo, item_first} per group of left blocks
         int *amax = nullptr;       // [right blocks]
         int ngroups = 0;
-        int64_t n_items = 0;       // strips (group, right block)
+        int64_t n_items = 0;       // strips (group, right block, left sub-range)
         std::vector<int4> groups_host;
         std::vector<int> amax_host;
         CUtensorMap tmapL{}, tmapR{};
@@ -145,6 +145,7 @@ struct Dataset {
         std::vector<uint64_t> lt_host;
         std::vector<int64_t> lmin_host, rmax_host;
         int64_t group = 0;
+        int64_t sub = 1;           // left blocks per strip (scheduler item)
     };
     TupleTC tup[3];            // k = 4, 5, 6
     bool last_path_tc4 = false;

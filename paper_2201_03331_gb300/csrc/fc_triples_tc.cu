@@ -684,14 +684,16 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                     for (int m = 0; m < 2; ++m) {
                         const bool cand = val[m] && sc[m] >= gthr && better(sc[m], rk[m], thr_s, thr_r);
                         const unsigned mk = __ballot_sync(FULL, cand);
-                        int base = 0;
-                        if (lane == 0 && mk) base = atomicAdd(&buf_count, __popc(mk));
-                        base = __shfl_sync(FULL, base, 0);
-                        if (cand) {
-                            // The headroom keeps the slot inside the buffer.
-                            const int s2 = min(L + base + __popc(mk & ((1u << lane) - 1u)), a.P2 - 1);
-                            lscore[s2] = sc[m];
-                            lrank[s2] = rk[m];
+                        if (mk) {
+                            int base = 0;
+                            if (lane == 0) base = atomicAdd(&buf_count, __popc(mk));
+                            base = __shfl_sync(FULL, base, 0);
+                            if (cand) {
+                                // The headroom keeps the slot inside the buffer.
+                                const int s2 = min(L + base + __popc(mk & ((1u << lane) - 1u)), a.P2 - 1);
+                                lscore[s2] = sc[m];
+                                lrank[s2] = rk[m];
+                            }
                         }
                     }
                 }

@@ -39,7 +39,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5", "P5", "P6", "T4"])
+    p.add_argument("--workload", default="C2", choices=["C1", "C2", "C3", "C4", "C5", "P5", "P6", "T4", "T5", "T6"])
     p.add_argument("--c5-datasets", type=int, default=64)
     p.add_argument("--c5-replicates", type=int, default=20)
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -53,7 +53,8 @@ def parse_args():
                    help="keep only the workload's first N SNPs (smaller cases for profiler captures)")
     p.add_argument("--range", default=None, metavar="S/P",
                    help="search only rank range S of P equal ranges (the share of one of P GPUs); "
-                        "default for T4: 63/64")
+                        "default for T4: 63/64, for T5 and T6: 0/64 (the range whose tiles need every "
+                        "chunk of the right tuple rows)")
     return p.parse_args()
 
 
@@ -316,7 +317,7 @@ def run_ours(args):
     k, top_n = ds.k, ds.top_n
     total = math.comb(ds.S, k)
     from paper_2201_03331_gb300.shard import shard_ranges
-    part = args.range or ("63/64" if args.workload == "T4" else None)
+    part = args.range or {"T4": "63/64", "T5": "0/64", "T6": "0/64"}.get(args.workload)
     if shard:
         # This rank's share of the one search: a contiguous rank range.
         r0, r1 = shard_ranges(total, world)[rank]

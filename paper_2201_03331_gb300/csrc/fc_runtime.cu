@@ -1130,11 +1130,36 @@ bool Dataset::tuples_tc_eligible(int k, int L)
     // Block indices and strips (group, right block) are ints (the group size
     // as in prepare_tuples).
     if (bl >= ((int64_t)1 << 31) / 128 || br >= ((int64_t)1 << 31) / 128) return false;
-    const int64_t group = tuple_group_size(Wt);
-    const int64_t sub = tuple_strip(group, bl, br, sms, 128.0 * ((double)Wt * 128 + 128));
-    if ((double)(bl / group + 1) * (double)br * (double)((group + sub - 1) / sub) >= 2147483647.0) return false;
-    // Both slabs stay resident: at most 60 % of the free memory (FC_TUPLES_SLAB_MB caps it).
-    const double slab = (double)(bl + br) * 128.0 * ((double)Wt * 128 + 128);
+    if (!tup[k - 4].ready) {
+        // The left slab stays resident; the right one in chunks beside it.
+        const int64_t rchunk = tuple_right_chunk(k);
+        if (rchunk <= 0) return false;
+        const int64_t group = tuple_group_size(Wt);
+        const int64_t sub = tuple_strip(group, bl, rchunk, sms, 128.0 * ((double)Wt * 128 + 128));
+        if ((double)(bl / group + 1) * (double)rchunk * (double)((group + sub - 1) / sub) >= 2147483647.0)
+            return false;
+    }
+    const int Bcap = std::max(L, 1024);
+    const int P2 = pow2_at_least(L + Bcap);
+    return quads_smem_bytes(tuples_form(), 2, (int)M, P2) <= (size_t)max_smem_optin;
+}
+
+// Right items per chunk of the orders 4-6 right slab (items: right blocks,
+// block pairs in form 1): all of them when both slabs fit in 60 % of the
+// free memory (at most 192 GiB; FC_TUPLES_SLAB_MB caps it), else as many as
+// fit beside the left slab, which stays resident; 0 if not even one does.
+// The search then builds each chunk's right rows in turn and runs the
+// chunk's tiles (the paper's order-5 and order-6 runs on one node, 561 and
+// 223 variants, need 2 TB and 122 GB of right rows at 2048 samples).
+int64_t Dataset::tuple_right_chunk(int k) const
+{
+    const int LT = tc_left_size(k), RT = k - LT;
+    const int64_t nl = tuple_count(S, LT, RT), nr = tuple_count(S, RT, LT);
+    const int64_t bl = (nl + tc_tuples_per_block(LT) - 1) / tc_tuples_per_block(LT);
+    const int64_t br = (nr + tc_tuples_per_block(RT) - 1) / tc_tuples_per_block(RT);
+    const int rblk = tuples_form() ? 2 : 1;
+    const int64_t nb = (br + rblk - 1) / rblk;
+    const double blk = 128.0 * ((double)Wt * 128 + 128);
     size_t free_b = 0, total_b = 0;
     double cap = 192.0 * 1024 * 1024 * 1024;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) cap = std::min(cap, 0.6 * (double)free_b);
@@ -1142,10 +1167,44 @@ bool Dataset::tuples_tc_eligible(int k, int L)
         const long v = atol(mb);
         if (v > 0) cap = std::min(cap, (double)v * 1024 * 1024);
     }
-    if (!tup[k - 4].ready && slab > cap) return false;
-    const int Bcap = std::max(L, 1024);
-    const int P2 = pow2_at_least(L + Bcap);
-    return quads_smem_bytes(tuples_form(), 2, (int)M, P2) <= (size_t)max_smem_optin;
+    const double left = (double)bl * blk, item = rblk * blk;
+    if (left + (double)nb * item <= cap) return nb;
+    if (cap - left < item) return 0;
+    return std::min<int64_t>(nb, (int64_t)((cap - left) / item));
+}
+
+int Dataset::build_right_chunk(int k, int64_t c)
+{
+    TupleTC &u = tup[k - 4];
+    if (u.built == c) return FC_OK;
+    const int LT = tc_left_size(k), RT = k - LT;
+    const int64_t c0 = c * u.rchunk, c1 = std::min(u.nb, c0 + u.rchunk);
+    const int64_t RPB = tc_tuples_per_block(RT);
+    cudaError_t e;
+    u.built = -1;
+    if ((e = launch_gate()) != cudaSuccess ||
+        (e = launch_tuple_rows(RT, X, S_pad, W0, Wt, u.rt + c0 * u.rblk * RPB, (c1 - c0) * u.rblk,
+                               (int64_t)Wt * 128 + 128, u.enc ? 0x68 : 0x38, u.QR, stream)) != cudaSuccess)
+        return cuda_status(e, "tuple-row kernel");
+    note_launches(1);
+    u.built = c;
+    return FC_OK;
+}
+
+QuadsArgs Dataset::tuples_chunk_args(const QuadsArgs &base, int k, int64_t c, const int4 *groups,
+                                     const std::vector<int> &cg0, const std::vector<int64_t> &citems) const
+{
+    const TupleTC &u = tup[k - 4];
+    const int64_t c0 = c * u.rchunk;
+    const int64_t RPB = tc_tuples_per_block(k - tc_left_size(k));
+    QuadsArgs qa = base;
+    qa.groups = groups + cg0[(size_t)c];
+    qa.ngroups = cg0[(size_t)c + 1] - cg0[(size_t)c];
+    qa.n_items = (int)citems[(size_t)c];
+    qa.amax = u.amax + c0;
+    qa.rtup = u.rt + c0 * u.rblk * RPB;
+    qa.rrank = u.rr + c0 * u.rblk * RPB;
+    return qa;
 }
 
 // The orders 4-6 tensor-core form: 1 (one accumulator n_case + 4096 n_ctrl,
@@ -1257,6 +1316,29 @@ int64_t tuple_groups(int64_t group, int64_t sub, int64_t bl, const std::vector<i
 }
 }  // namespace
 
+// Groups of every right chunk of the plan of order k (those of left blocks
+// with include set, if include is not null), back to back: chunk c's are
+// groups[cg0[c] .. cg0[c + 1]), with citems[c] items.  FC_ERANGE if a
+// chunk's items overflow an int.
+int tuple_chunk_groups(const Dataset::TupleTC &u, int64_t bl, const std::vector<char> *include,
+                       std::vector<int4> &groups, std::vector<int> &cg0, std::vector<int64_t> &citems)
+{
+    groups.clear();
+    cg0.assign(1, 0);
+    citems.clear();
+    std::vector<int4> gc;
+    for (int64_t c = 0; c < u.nchunks(); ++c) {
+        const int64_t c0 = c * u.rchunk, c1 = std::min(u.nb, c0 + u.rchunk);
+        const std::vector<int> slice(u.amax_host.begin() + c0, u.amax_host.begin() + c1);
+        const int64_t items = tuple_groups(u.group, u.sub, bl, slice, include, gc);
+        if (items >= ((int64_t)1 << 31)) return set_error(FC_ERANGE, "tensor-core strip plan too large");
+        groups.insert(groups.end(), gc.begin(), gc.end());
+        cg0.push_back((int)groups.size());
+        citems.push_back(items);
+    }
+    return FC_OK;
+}
+
 int Dataset::prepare_tuples(int k)
 {
     TupleTC &u = tup[k - 4];
@@ -1319,18 +1401,24 @@ int Dataset::prepare_tuples(int k)
     // second block's, the larger; a padding block takes its partner's).
     std::vector<int> &amax = u.amax_host;
     const int64_t nb = u.enc ? br2 / 2 : br;
+    u.nb = nb;
+    u.rblk = u.enc ? 2 : 1;
+    u.rchunk = tuple_right_chunk(k);
+    if (u.rchunk <= 0) return set_error(FC_ENOMEM, "tuple-row slabs do not fit in device memory");
     amax.resize((size_t)nb);
     for (int64_t b = 0; b < nb; ++b) {
         const int64_t rb = u.enc ? std::min<int64_t>(2 * b + 1, br - 1) : b;
         amax[(size_t)b] = (int)(std::lower_bound(u.lmin_host.begin(), u.lmin_host.end(), u.rmax_host[(size_t)rb]) -
                                 u.lmin_host.begin());
     }
-    u.sub = tuple_strip(u.group, bl, nb, sms, (u.enc ? 2.0 : 1.0) * 128.0 * (double)pitch);
-    u.n_items = tuple_groups(u.group, u.sub, bl, amax, nullptr, u.groups_host);
-    if (u.n_items >= ((int64_t)1 << 31)) return set_error(FC_ERANGE, "tensor-core strip plan too large");
+    u.sub = tuple_strip(u.group, bl, u.rchunk, sms, (u.enc ? 2.0 : 1.0) * 128.0 * (double)pitch);
+    int rc = tuple_chunk_groups(u, bl, nullptr, u.groups_host, u.cg0, u.citems);
+    if (rc) return rc;
+    u.n_items = 0;
+    for (const int64_t n : u.citems) u.n_items += n;
     u.ngroups = (int)u.groups_host.size();
     u.ql_bytes = std::max<size_t>((size_t)bl * 128 * pitch, 1);
-    u.qr_bytes = std::max<size_t>((size_t)br2 * 128 * pitch, 1);
+    u.qr_bytes = std::max<size_t>((size_t)u.rchunk * u.rblk * 128 * pitch, 1);
     if ((e = dev_alloc_pooled((void **)&u.QL, u.ql_bytes, device)) != cudaSuccess ||
         (e = dev_alloc_pooled((void **)&u.QR, u.qr_bytes, device)) != cudaSuccess)
         return cuda_status(e, "tuple-row slab allocation");
@@ -1349,14 +1437,15 @@ int Dataset::prepare_tuples(int k)
     cudaMemcpyAsync(u.amax, amax.data(), sizeof(int) * amax.size(), cudaMemcpyHostToDevice, stream);
     if ((e = launch_gate()) != cudaSuccess ||
         (e = launch_tuple_rows(LT, X, S_pad, W0, Wt, u.lt, bl, (int64_t)pitch, u.enc ? 0x68 : 0x38, u.QL, stream)) !=
-            cudaSuccess ||
-        (e = launch_tuple_rows(RT, X, S_pad, W0, Wt, u.rt, br2, (int64_t)pitch, u.enc ? 0x68 : 0x38, u.QR, stream)) !=
             cudaSuccess)
         return cuda_status(e, "tuple-row kernel");
-    note_launches(2);
-    int rc;
+    note_launches(1);
+    // One chunk: the right rows are built once and kept.
+    u.built = -1;
+    if (u.nchunks() == 1 && (rc = build_right_chunk(k, 0)) != FC_OK) return rc;
     if ((rc = encode_tmap_u8(&u.tmapL, u.QL, kbytes, pitch, (uint64_t)bl * 128, 128, true)) != FC_OK) return rc;
-    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)br2 * 128, u.enc ? 256 : 128, true)) != FC_OK)
+    if ((rc = encode_tmap_u8(&u.tmapR, u.QR, kbytes, pitch, (uint64_t)u.rchunk * u.rblk * 128, u.enc ? 256 : 128,
+                             true)) != FC_OK)
         return rc;
     // Host vectors go out of scope: the copies must have landed.
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_status(e, "tuple operands");
@@ -1393,10 +1482,14 @@ int Dataset::tuples_dense(int k, float *scores, uint32_t *tables)
     if (ns) cudaMemsetAsync(qa.dump_scores, 0, ns, stream);
     if (nt) cudaMemsetAsync(qa.dump_tables, 0, nt, stream);
     const TupleTC &u = tup[k - 4];
-    if (u.n_items > 0) {
-        const int grid = (int)std::min<int64_t>(sms, u.n_items);
+    for (int64_t c = 0; c < u.nchunks(); ++c) {
+        if (u.citems[(size_t)c] == 0) continue;
+        if ((rc = build_right_chunk(k, c)) != FC_OK) return rc;
+        const QuadsArgs qc = tuples_chunk_args(qa, k, c, u.groups, u.cg0, u.citems);
+        const int grid = (int)std::min<int64_t>(sms, u.citems[(size_t)c]);
+        cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
         if ((e = launch_gate()) != cudaSuccess ||
-            (e = launch_quads_tc(k, MODE_DUMP, u.tmapL, u.tmapR, qa, grid, stream)) != cudaSuccess)
+            (e = launch_quads_tc(k, MODE_DUMP, u.tmapL, u.tmapR, qc, grid, stream)) != cudaSuccess)
             return cuda_status(e, "tensor-core tuple kernel");
         note_launches(1);
     }
@@ -1458,6 +1551,8 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
         // and the left blocks to take.
         std::vector<int4> range_groups4;
         std::vector<char> include4;
+        std::vector<int> cg0_4;
+        std::vector<int64_t> citems4, launches4;
         struct SlabLaunch { int si; int64_t t0, t1; };
         std::vector<SlabLaunch> launches3;
         int grid = 0;
@@ -1496,9 +1591,10 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             int rc = prepare_tuples(k);
             if (rc) return rc;
             qa = tuples_args(k, L, (float)hy, (float)(1.0 / Nd));
-            int64_t nt = tup[k - 4].n_items;
+            const TupleTC &u = tup[k - 4];
+            cg0_4 = u.cg0;
+            citems4 = u.citems;
             if (!whole) {
-                const TupleTC &u = tup[k - 4];
                 const int LT = tc_left_size(k), LPB = tc_tuples_per_block(LT);
                 std::vector<char> &include = include4;
                 include.assign(u.lmin_host.size(), 0);
@@ -1516,14 +1612,18 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                     const uint64_t first = rank_of(S, k, c);
                     if (first < r1 && first + count > r0) include[x / (size_t)LPB] = 1;
                 }
-                nt = tuple_groups(u.group, u.sub, (int64_t)u.lmin_host.size(), u.amax_host, &include,
-                                  range_groups4);
-                qa.n_items = (int)nt;
-                qa.ngroups = (int)range_groups4.size();
+                if ((rc = tuple_chunk_groups(u, (int64_t)u.lmin_host.size(), &include, range_groups4, cg0_4,
+                                             citems4)) != FC_OK)
+                    return rc;
                 qa.rank_begin = r0;
                 qa.rank_end = r1;
             }
-            grid = (int)std::max<int64_t>(1, std::min<int64_t>(sms, nt));
+            // One launch per right chunk with tiles (at least one, whose
+            // CTAs write the empty lists); each writes sms lists.
+            for (int64_t c = 0; c < u.nchunks(); ++c)
+                if (citems4[(size_t)c] > 0) launches4.push_back(c);
+            if (launches4.empty()) launches4.push_back(0);
+            grid = sms * (int)launches4.size();
         } else {
             cfg = pick_config(k, L, MODE_TOPN, no_alloc);
             if (cfg.var == VAR_IE) {
@@ -1603,11 +1703,11 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
             if ((e = launch_gate()) != cudaSuccess || (e = launch_pairs_tc(MODE_TOPN, tmap, pa, grid, stream)) != cudaSuccess)
                 return cuda_status(e, "tensor-core pairs kernel");
         } else if (tc4) {
-            qa.list_score = (float *)p[0];
-            qa.list_rank = (uint64_t *)p[1];
+            const TupleTC &u = tup[k - 4];
             qa.gthr = (int *)p[11];
             qa.tile_counter = (int *)p[11] + 1;
             qa.err = err;
+            const int4 *groups = u.groups;
             if (!whole) {
                 int4 *dg = (int4 *)p[12];
                 uint8_t *di = (uint8_t *)(dg + range_groups4.size());
@@ -1615,14 +1715,23 @@ int Dataset::search(int k, int64_t top_n, uint32_t *out_idx, double *out_score, 
                     cudaMemcpyAsync(dg, range_groups4.data(), sizeof(int4) * range_groups4.size(),
                                     cudaMemcpyHostToDevice, stream);
                 cudaMemcpyAsync(di, include4.data(), include4.size(), cudaMemcpyHostToDevice, stream);
-                qa.groups = dg;
+                groups = dg;
                 qa.include = di;
             }
             cudaMemsetAsync(p[11], 0x80, sizeof(int), stream);
-            cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
-            if ((e = launch_gate()) != cudaSuccess ||
-                (e = launch_quads_tc(k, MODE_TOPN, tup[k - 4].tmapL, tup[k - 4].tmapR, qa, grid, stream)) != cudaSuccess)
-                return cuda_status(e, "tensor-core tuple kernel");
+            for (size_t x = 0; x < launches4.size(); ++x) {
+                const int64_t c = launches4[x];
+                int rc = build_right_chunk(k, c);
+                if (rc) return rc;
+                QuadsArgs qc = tuples_chunk_args(qa, k, c, groups, cg0_4, citems4);
+                qc.list_score = (float *)p[0] + x * sms * L;
+                qc.list_rank = (uint64_t *)p[1] + x * sms * L;
+                cudaMemsetAsync(qa.tile_counter, 0, sizeof(int), stream);
+                if ((e = launch_gate()) != cudaSuccess ||
+                    (e = launch_quads_tc(k, MODE_TOPN, u.tmapL, u.tmapR, qc, sms, stream)) != cudaSuccess)
+                    return cuda_status(e, "tensor-core tuple kernel");
+                if (x > 0) note_launches(1);
+            }
         } else if (tc3) {
             ta.gthr = (int *)p[11];
             ta.tile_counter = (int *)p[11] + 1;

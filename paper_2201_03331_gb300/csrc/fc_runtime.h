@@ -146,6 +146,17 @@ struct Dataset {
         std::vector<int64_t> lmin_host, rmax_host;
         int64_t group = 0;
         int64_t sub = 1;           // left blocks per strip (scheduler item)
+        // The right operand in chunks when the whole right slab does not
+        // fit beside the left one: nb right items (blocks; block pairs in
+        // form 1) of rblk blocks, rchunk of them per chunk (nb: one chunk,
+        // built once and kept); chunk c's groups are groups_host[cg0[c] ..
+        // cg0[c + 1]) with citems[c] items; QR holds chunk `built`.
+        int64_t nb = 0, rchunk = 0;
+        int rblk = 1;
+        std::vector<int> cg0;
+        std::vector<int64_t> citems;
+        int64_t built = -1;
+        int64_t nchunks() const { return rchunk > 0 ? (nb + rchunk - 1) / rchunk : 0; }
     };
     TupleTC tup[3];            // k = 4, 5, 6
     bool last_path_tc4 = false;
@@ -200,6 +211,13 @@ struct Dataset {
     TriplesArgs triples_args(int L, float hy, float invN);
     int triples_dense(float *scores, uint32_t *tables);
     bool tuples_tc_eligible(int k, int L);
+    // Right items per chunk of the orders 4-6 right slab (0: does not fit).
+    int64_t tuple_right_chunk(int k) const;
+    int build_right_chunk(int k, int64_t c);
+    // Arguments of the launch over right chunk c (groups from `groups` with
+    // chunk offsets cg0, citems).
+    QuadsArgs tuples_chunk_args(const QuadsArgs &base, int k, int64_t c, const int4 *groups, const std::vector<int> &cg0,
+                                const std::vector<int64_t> &citems) const;
     int tuples_form() const;
     int prepare_tuples(int k);
     void release_tuples(int k);

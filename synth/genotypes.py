@@ -226,6 +226,12 @@ CONFIGS = {
     # 2,409 variants, 2,048 samples).
     "T4": dict(seed=9, S=2409, cases=1024, controls=1024, k=4, top_n=100,
                planted=(100, 900, 1700, 2300), maf_range=(0.05, 0.5)),
+    # Orders 5 and 6 at the sizes of the paper's single-node runs (Table 4:
+    # 561 and 223 variants, 2,048 samples).
+    "T5": dict(seed=10, S=561, cases=1024, controls=1024, k=5, top_n=100,
+               planted=(0, 120, 250, 400, 540), maf_range=(0.05, 0.5)),
+    "T6": dict(seed=11, S=223, cases=1024, controls=1024, k=6, top_n=100,
+               planted=(0, 40, 80, 120, 160, 200), maf_range=(0.05, 0.5)),
 }
 
 CONFIG_TITLES = {
@@ -238,6 +244,8 @@ CONFIG_TITLES = {
     "P6": "order-6 exhaustive, 76 SNPs x 2,048 samples (1,024/1,024), top 100",
     "Q4": "order-4 exhaustive, 600 SNPs x 512 samples (256/256), top 100",
     "T4": "order-4 exhaustive, 2,409 SNPs x 2,048 samples (1,024/1,024), top 100",
+    "T5": "order-5 exhaustive, 561 SNPs x 2,048 samples (1,024/1,024), top 100",
+    "T6": "order-6 exhaustive, 223 SNPs x 2,048 samples (1,024/1,024), top 100",
 }
 
 

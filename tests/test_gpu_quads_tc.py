@@ -184,3 +184,73 @@ def test_high_order_tc_and_sweep_agree(fc, path, name, S):
     assert fc.fc_last_search_kind(h) == 5
     assert np.array_equal(a[0], b[0])
     np.testing.assert_allclose(a[1], b[1], rtol=1e-12)
+
+
+# ---- right operand in chunks -------------------------------------------------
+# When the right tuple rows do not fit beside the left ones (the paper's
+# single-node order-5 and order-6 sizes), the search builds them chunk by
+# chunk and runs each chunk's tiles.  FC_TUPLES_SLAB_MB makes small cases
+# take that path.
+
+def _slab_mb(k, S, M1, M0, form, right_share):
+    """Memory cap (MB) that leaves about `right_share` of the right rows beside
+    the left ones: blocks of 128 rows of (words * 128 + 128) bytes, 12 left
+    pairs or 4 triples per block (one tuple of each genotype combination per
+    32-row quarter), right blocks in pairs in form 1."""
+    LT = 3 if k == 6 else 2
+    RT = k - LT
+    words = -(-M1 // 128) + -(-M0 // 128)
+    blk = 128 * (words * 128 + 128)
+    per = {2: 12, 3: 4}
+    bl = -(-math.comb(S - RT, LT) // per[LT])
+    br = -(-math.comb(S - LT, RT) // per[RT])
+    left, right = bl * blk, br * blk
+    return int(math.ceil((left + right_share * right) / 2 ** 20)), left + right
+
+
+@pytest.mark.parametrize("k,S,cases,controls,seed", [(4, 41, 1500, 2100, 11), (5, 29, 300, 290, 12),
+                                                     (6, 20, 1, 333, 13)])
+def test_dense_tables_exact_right_chunks(fc, form, monkeypatch, k, S, cases, controls, seed):
+    mb, total = _slab_mb(k, S, cases, controls, form, 0.25)
+    assert mb * 2 ** 20 < total            # the right rows cannot all stay
+    monkeypatch.setenv("FC_TUPLES_SLAB_MB", str(mb))
+    ds = make_dataset("q4chunk", seed=870 + seed, S=S, cases=cases, controls=controls, k=k, top_n=5)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    fc.fc_timing(h, 1)
+    _, tab = fc.fc_tuples_dense(h, k, scores=False, tables=True)
+    _, _, launches = fc.fc_timing(h, 0)
+    assert launches >= 2 + 2 * 3           # left rows + at least three (right chunk, kernel) launches
+    ref = oracle.tables(ds.genotypes, ds.phenotype, k, all_k(S, k))
+    bad = np.nonzero(np.any(tab != ref, axis=(1, 2)))[0]
+    assert len(bad) == 0, (len(bad), all_k(S, k)[bad[:5]])
+
+
+@pytest.mark.parametrize("k,S,cases,controls,top_n", [(5, 34, 500, 420, 60), (6, 24, 300, 333, 40)])
+def test_search_right_chunks_match_oracle(fc, form, path, monkeypatch, k, S, cases, controls, top_n):
+    path("tc")
+    mb, _ = _slab_mb(k, S, cases, controls, form, 0.2)
+    monkeypatch.setenv("FC_TUPLES_SLAB_MB", str(mb))
+    planted = tuple(sorted({2, S // 4, S // 3, S // 2, 2 * S // 3, S - 3}))[:k]
+    ds = make_dataset("q5chunk", seed=880 + k, S=S, cases=cases, controls=controls, k=k, top_n=top_n,
+                      planted=planted)
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    g_idx, g_s = fc.fc_search(h, k, top_n)
+    assert fc.fc_last_search_kind(h) == 7
+    o_idx, o_s, _ = oracle.search(ds.genotypes, ds.phenotype, k, top_n)
+
+    def score_of(c):
+        return float(oracle.mi(oracle.tables(ds.genotypes, ds.phenotype, k, [c]), k)[0])
+    assert_topn_equal(g_idx, g_s, o_idx, o_s, score_of)
+    # The same search again (the right rows of the last chunk are in place),
+    # and a rank range, against a handle whose right rows all fit.
+    again = fc.fc_search(h, k, top_n)
+    assert np.array_equal(again[0], g_idx)
+    monkeypatch.delenv("FC_TUPLES_SLAB_MB")
+    h1 = fc.fc_load(ds.genotypes, ds.phenotype)
+    total = math.comb(S, k)
+    r0, r1 = total // 3, total // 3 + total // 5
+    a = fc.fc_search_range(h, k, top_n, r0, r1)
+    b = fc.fc_search_range(h1, k, top_n, r0, r1)
+    assert fc.fc_last_search_kind(h1) == 7
+    assert np.array_equal(a[0], b[0])
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-12)

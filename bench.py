@@ -53,8 +53,7 @@ def parse_args():
                    help="keep only the workload's first N SNPs (smaller cases for profiler captures)")
     p.add_argument("--range", default=None, metavar="S/P",
                    help="search only rank range S of P equal ranges (the share of one of P GPUs); "
-                        "default for T4: 63/64, for T5 and T6: 0/64 (the range whose tiles need every "
-                        "chunk of the right tuple rows)")
+                        "default for T4, T5 and T6: 63/64")
     return p.parse_args()
 
 
@@ -317,7 +316,7 @@ def run_ours(args):
     k, top_n = ds.k, ds.top_n
     total = math.comb(ds.S, k)
     from paper_2201_03331_gb300.shard import shard_ranges
-    part = args.range or {"T4": "63/64", "T5": "0/64", "T6": "0/64"}.get(args.workload)
+    part = args.range or {"T4": "63/64", "T5": "63/64", "T6": "63/64"}.get(args.workload)
     if shard:
         # This rank's share of the one search: a contiguous rank range.
         r0, r1 = shard_ranges(total, world)[rank]

@@ -1208,20 +1208,19 @@ QuadsArgs Dataset::tuples_chunk_args(const QuadsArgs &base, int k, int64_t c, co
 }
 
 // The orders 4-6 tensor-core form: 1 (one accumulator n_case + 4096 n_ctrl,
-// two right blocks per tile) while both classes have at most 4095 samples
-// and four of its 48 KB stages fit beside the x ln x table and a list of
-// 2048 entries, else 0 (one accumulator per class, 32 KB stages).  The
-// copies in flight set the operand stream (measured: at 2048 samples form 1
-// with four stages is 1.3x form 0 with six; at 6000 samples form 1 with
-// three stages is 4 % slower than form 0 with six).  FC_QUADS_ENC=0 forces
-// form 0, FC_QUADS_ENC=1 form 1 where the classes allow it.
+// two right blocks per tile, which halves the left operand's bytes per
+// multiply-add) while both classes have at most 4095 samples, else 0 (one
+// accumulator per class, 32 KB stages).  Measured with the strip schedule:
+// at 2048 samples form 1 with four 48 KB stages is 1.3x form 0 with six; at
+// 6000 samples form 1 with three stages is 1.9x form 0 with six (162 against
+// 307 ms for 300 SNPs).  FC_QUADS_ENC=0 forces form 0, FC_QUADS_ENC=1 form 1
+// where the classes allow it.
 int Dataset::tuples_form() const
 {
     const char *f = getenv("FC_QUADS_ENC");
     if (f && strcmp(f, "0") == 0) return 0;
     if (M1 > 4095 || M0 > 4095) return 0;
-    if (f && strcmp(f, "1") == 0) return 1;
-    return quads_smem_bytes(1, 4, (int)M, 2048) <= (size_t)max_smem_optin ? 1 : 0;
+    return quads_smem_bytes(1, 3, (int)M, 2048) <= (size_t)max_smem_optin ? 1 : 0;
 }
 
 QuadsArgs Dataset::tuples_args(int k, int L, float hy, float invN)

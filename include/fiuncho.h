@@ -349,10 +349,11 @@ int fc_sweep_tables(fc_handle *h, int k, uint64_t rank_begin, int64_t n, uint32_
  * epilogue takes for its n ln n terms (the hardware approximation), of
  * max(n[i], 1) for count integers n[i] < 2^23 (host uint32 in, host float
  * out), computed on the current device.  A parity hook: the epilogue's FP32
- * error bound (Section "Background": the mutual information; see
- * fc_search) assumes |result - log2(n)| <= 2^-21 for 1 <= n <= 2^17, which a
- * test checks for every such n.  FC_EINVAL for count < 0 or NULL buffers;
- * FC_ENOMEM / FC_ECUDA as the other calls.
+ * error bound on the mutual information (Section "Mutual Information test";
+ * see fc_search) assumes |result - log2(n)| <= 2^-22 (log2(n) + 1) for
+ * 1 <= n <= 2^17, which a test checks for every such n.  The paper has no
+ * counterpart.  FC_EINVAL for count < 0 or NULL buffers; FC_ENOMEM /
+ * FC_ECUDA as the other calls.
  */
 int fc_log2_approx(const uint32_t *n, int64_t count, float *out);
 

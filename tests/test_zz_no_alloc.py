@@ -115,3 +115,23 @@ def test_static_search_allocates_nothing(fc):
         del os.environ["FC_FAULT_ALLOC_ALL"]
     torch.cuda.synchronize()
     assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_static_search_with_right_chunks_allocates_nothing(fc, monkeypatch):
+    """Orders 4-6 with the right tuple rows in chunks: once fc_search has
+    built the operands, the static search rebuilds each chunk's rows into
+    the kept buffer without allocating (every device allocation made to
+    fail), with fc_search's results."""
+    monkeypatch.setenv("FC_QUADS_PATH", "tc")
+    monkeypatch.setenv("FC_TUPLES_SLAB_MB", "6")
+    ds = make_dataset("na-chunks", seed=97, S=30, cases=300, controls=290, k=5, top_n=20,
+                      planted=(2, 8, 13, 20, 27))
+    h = fc.fc_load(ds.genotypes, ds.phenotype)
+    ref = fc.fc_search(h, 5, 20)
+    assert fc.fc_last_search_kind(h) == 7
+    monkeypatch.setenv("FC_FAULT_ALLOC_ALL", "1")
+    for _ in range(2):
+        idx, s = fc.fc_search_static(h, 5, 20)
+        assert fc.fc_last_search_kind(h) == 7
+        assert np.array_equal(idx, ref[0])
+        np.testing.assert_allclose(s, ref[1], rtol=SCORE_REL, atol=1e-12)

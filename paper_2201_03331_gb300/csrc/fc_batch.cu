@@ -168,20 +168,23 @@ int plan_tc3(fc_handle *h, int L, int64_t top_n, std::unique_ptr<Tc3Batch> &out)
     int64_t maxM = 0;
     for (int d = 0; d < B.n_data; ++d) {
         bool all = true, one_acc = true;
+        int64_t cls = 0;   // the largest class of any replicate
         for (int r = 0; r < R; ++r) {
             const Dataset &x = *h->jobs[(size_t)d * R + r];
             all = all && B.tc[(size_t)d * R + r];
             one_acc = one_acc && x.M1 <= 4095 && x.M0 <= 4095;
+            cls = std::max(cls, std::max(x.M1, x.M0));
         }
         if (!all) continue;
         const Dataset &d0 = *h->jobs[(size_t)d * R];
         Tc3Batch::Set st;
         st.first_job = d * R;
         // The kernel holds an x ln x table of the power of two above the
-        // launch's largest sample count: one accumulator where both classes
-        // of every replicate have at most 4095 samples and shared memory
-        // fits, else two.
-        if (one_acc && triples_list_fit(1, d0.M, L, lead.max_smem_optin) > 0) {
+        // launch's largest class count (the table serves the class counts;
+        // n ln n of a cell's total comes from the hardware logarithm): one
+        // accumulator where both classes of every replicate have at most
+        // 4095 samples and shared memory fits, else two.
+        if (one_acc && triples_list_fit(1, cls, L, lead.max_smem_optin) > 0) {
             st.enc = 1;
         } else {
             // Two accumulators over the chunks [0, split) and [split, Wt) of
@@ -197,11 +200,11 @@ int plan_tc3(fc_handle *h, int L, int64_t top_n, std::unique_ptr<Tc3Batch> &out)
                 split = c + 1;
             }
             if (split <= 0 || split >= d0.Wt || d0.M - pre > 4095) continue;
-            if (triples_list_fit(2, d0.M, L, lead.max_smem_optin) < 0) continue;
+            if (triples_list_fit(2, cls, L, lead.max_smem_optin) < 0) continue;
             st.enc = 2;
             st.split = split;
         }
-        st.M = d0.M;
+        st.M = cls;   // table extent
         st.NP = triples_pairs_per_tile(st.enc);
         st.pitch = (int64_t)d0.Wt * 128 + 128;
         st.rows = 2 * ((d0.S + 63) / 64 * 64);

@@ -173,9 +173,18 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        # nvidia-smi takes a moment to start: wait (up to 2 s) for its first
+        # sample, so that a short timed region is covered.
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 2.0 and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -335,15 +344,17 @@ def run_ours(args):
     fc.fc_set_stream(h, stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    # Clock samples from the warm-up (the same searches) through the timed
+    # steps, so that a short timed region still gets several.
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(3, args.warmup)):
         one_search(h)
     torch.cuda.synchronize()
 
     fc.fc_timing(h, 1)
-    clocks = ClockSampler(local)
     barrier(dist)
     torch.cuda.synchronize()
-    clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     with NvtxRange("timed"):

@@ -369,7 +369,7 @@ int plan_tc3(fc_handle *h, int L, int64_t top_n, std::unique_ptr<Tc3Batch> &out)
     cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(uint4) * tiles.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(T->rowbase, rowbase.data(), sizeof(int64_t) * rowbase.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(d_masks, masks.data(), sizeof(uint32_t) * masks.size(), cudaMemcpyHostToDevice, st);
-    if ((e = launch_gate()) != cudaSuccess || (e = launch_xlogx(T->xlogx, maxM, st)) != cudaSuccess)
+    if ((e = launch_gate()) != cudaSuccess || (e = launch_xlogx(T->xlogx, maxM, st, true)) != cudaSuccess)
         return cuda_status(e, "x ln x table");
     for (int si = 0; si < nsets; ++si) {
         const Tc3Batch::Set &ss = T->sets[(size_t)si];

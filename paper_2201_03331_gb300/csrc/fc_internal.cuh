@@ -107,7 +107,8 @@ struct PackArgs {
 cudaError_t launch_class_index(const PackArgs &a, cudaStream_t st);
 cudaError_t launch_pack(const PackArgs &a, int64_t M1, int64_t M0, cudaStream_t st);
 cudaError_t launch_logtab(float *logtab, int64_t M, cudaStream_t st);
-cudaError_t launch_xlogx(float *t, int64_t M, cudaStream_t st);
+// x ln x (base2: x log2 x) for x = 0..M, each the FP64 product rounded once.
+cudaError_t launch_xlogx(float *t, int64_t M, cudaStream_t st, bool base2 = false);
 
 struct SearchArgs {
     const uint4 *X;
@@ -318,8 +319,8 @@ struct TriplesArgs {
     int W0, Wt;             // 128-sample chunks: cases [0, W0), controls [W0, Wt)
     const uint4 *marg4;     // per-SNP genotype counts (one uint4 per SNP)
     const uint4 *PR;        // restricted pair table [S_pad][S_pad]
-    const float *xlogx;     // x ln x for x = 0..M (FP64 rounded once to FP32)
-    int M;                  // extent of the kernel's x ln x table: at least every class count
+    const float *xlogx;     // x log2 x for x = 0..M (FP64 rounded once to FP32)
+    int M;                  // extent of the kernel's x log2 x table: at least every class count
     float hy, invN;
     uint64_t total;         // C(S, 3)
     uint64_t rank_begin, rank_end;   // only combinations with ranks in [rank_begin, rank_end) count

@@ -101,18 +101,19 @@ __global__ void k_logtab(float *t, int64_t M)
     if (n <= M) t[n] = n == 0 ? 0.0f : (float)log((double)n);
 }
 
-// x ln x for x = 0..M (0 ln 0 := 0): the product in FP64 rounded once to FP32.
-__global__ void k_xlogx(float *t, int64_t M)
+// x ln x (base2: x log2 x) for x = 0..M (0 ln 0 := 0): the product in FP64
+// rounded once to FP32.
+__global__ void k_xlogx(float *t, int64_t M, bool base2)
 {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n <= M) t[n] = n == 0 ? 0.0f : (float)((double)n * log((double)n));
+    if (n <= M) t[n] = n == 0 ? 0.0f : (float)((double)n * (base2 ? log2((double)n) : log((double)n)));
 }
 
 }  // namespace
 
-cudaError_t launch_xlogx(float *t, int64_t M, cudaStream_t st)
+cudaError_t launch_xlogx(float *t, int64_t M, cudaStream_t st, bool base2)
 {
-    k_xlogx<<<(unsigned)((M + 1 + 255) / 256), 256, 0, st>>>(t, M);
+    k_xlogx<<<(unsigned)((M + 1 + 255) / 256), 256, 0, st>>>(t, M, base2);
     return cudaGetLastError();
 }
 

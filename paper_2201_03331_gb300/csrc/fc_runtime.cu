@@ -325,6 +325,7 @@ Dataset::~Dataset()
     dev_free_pooled(tiles, tiles_bytes, device);
     cudaFree(PR);
     cudaFree(xlogx);
+    cudaFree(xlog2x);
     for (int k = 4; k <= 6; ++k) release_tuples(k);
     dev_free_pooled(tiles3, tiles3_bytes, device);
     dev_free_pooled(rowbase3, rowbase3_bytes, device);
@@ -355,14 +356,14 @@ float score_error_bound(int k, int64_t M)
     // Divided by N: |MI32 - MI| <= u (2 ln M + (2*3^k + 6) ln 2).  The
     // orders 4-6 tensor-core epilogue's x ln x form has the smaller bound
     // u (3 ln M + (3^k + 4) ln 2) for every M used here; the order-3 one,
-    // whose n ln n terms come from the hardware logarithm (relative error
-    // 2^-22 plus 2^-22 absolute), u (7 ln M + 35 ln 2).  The larger, doubled
+    // whose n log2 n terms come from the hardware logarithm (relative error
+    // 2^-22 plus 2^-22 absolute), u (7 ln M + 37 ln 2).  The larger, doubled
     // for margin.
     const double u = std::ldexp(1.0, -24);
     const double terms = 2.0 * pow3(k);
     const double lm = std::log((double)std::max<int64_t>(M, 2));
     double e = u * (2.0 * lm + (terms + 6.0) * std::log(2.0));
-    if (k == 3) e = std::max(e, u * (7.0 * lm + 35.0 * std::log(2.0)));
+    if (k == 3) e = std::max(e, u * (7.0 * lm + 37.0 * std::log(2.0)));
     return (float)(2.0 * e);
 }
 
@@ -786,7 +787,7 @@ TriplesArgs Dataset::triples_args(int L, float hy, float invN)
     ta.Wt = Wt;
     ta.marg4 = reinterpret_cast<const uint4 *>(marg);
     ta.PR = PR;
-    ta.xlogx = xlogx;
+    ta.xlogx = xlog2x;
     ta.M = (int)std::max(M1, M0);   // table extent: the class counts
     ta.hy = hy;
     ta.invN = invN;
@@ -885,11 +886,11 @@ int Dataset::prepare_triples(int L)
     if (rc) return rc;
     if ((rc = prepare_ie(3)) != FC_OK) return rc;
     cudaError_t e;
-    if (!xlogx) {
-        if ((e = dev_alloc((void **)&xlogx, sizeof(float) * (size_t)(M + 1))) != cudaSuccess)
-            return cuda_status(e, "x ln x table allocation");
-        if ((e = launch_gate()) != cudaSuccess || (e = launch_xlogx(xlogx, M, stream)) != cudaSuccess)
-            return cuda_status(e, "x ln x table");
+    if (!xlog2x) {
+        if ((e = dev_alloc((void **)&xlog2x, sizeof(float) * (size_t)(M + 1))) != cudaSuccess)
+            return cuda_status(e, "x log2 x table allocation");
+        if ((e = launch_gate()) != cudaSuccess || (e = launch_xlogx(xlog2x, M, stream, true)) != cudaSuccess)
+            return cuda_status(e, "x log2 x table");
         note_launches(1);
     }
     const int64_t S64 = (S + 63) / 64 * 64;

@@ -101,7 +101,8 @@ struct Dataset {
     };
     std::vector<TripleSlab> slabs3;
     std::vector<int64_t> first_tile3;   // [S + 1] first tile of each first SNP
-    float *xlogx = nullptr;   // x ln x, x = 0..M (the order-3 epilogue's MI table)
+    float *xlogx = nullptr;   // x ln x, x = 0..M (the orders 4-6 epilogue's MI table)
+    float *xlog2x = nullptr;  // x log2 x, x = 0..M (the order-3 epilogue's)
     uint8_t *P3 = nullptr;
     size_t p3_bytes = 0;
     uint4 *tiles3 = nullptr;

@@ -45,19 +45,21 @@
 // three load stages are owned by three producer warps that each issue the
 // copies of their own stage (fill f by warp f mod 3).
 //
-// The epilogue scores each cell as t = n ln n - xl[a] - xl[b] = a ln(n/a) +
-// b ln(n/b) (a, b the class counts, n = a + b), MI = H(Y) - sum t / N, where
-// xl is a shared-memory table of x ln x over the class counts (entries
-// correctly rounded) and n ln n comes from the hardware base-2 logarithm:
-// n (ln 2 lg2~(n)), with |lg2~(n) - log2 n| <= 2^-22 (log2 n + 1) for every
-// integer 1 <= n <= 2^17 (checked exhaustively on the device by a test;
-// fc_log2_approx).  Moving one of the three lookups per cell to the XU pipe
-// relieves the shared-memory pipe.  With u = 2^-24 (so 2^-22 = 4u), a cell
-// errs by at most n (4u (ln M + ln 2) + u ln M) from the n ln n term,
-// u (a + b) ln M from the table entries, u n ln M from the fused
-// multiply-subtract and u n ln 2 from the last subtraction; over the 27 cells
-// (sum n = N), the 27 accumulations (partial sums <= N ln 2) and the final
-// scaling this gives |MI32 - MI| <= u (7 ln M + 35 ln 2), which the FP64
+// The epilogue scores each cell, in bits, as t = n log2 n - xl[a] - xl[b] =
+// a log2(n/a) + b log2(n/b) (a, b the class counts, n = a + b), and
+// MI = H(Y) - ln 2 sum t / N, where xl is a shared-memory table of x log2 x
+// over the class counts (entries correctly rounded) and n log2 n comes from
+// the hardware base-2 logarithm, n lg2~(n), with |lg2~(n) - log2 n| <=
+// 2^-22 (log2 n + 1) for every integer 1 <= n <= 2^17 (checked exhaustively
+// on the device by a test; fc_log2_approx).  Moving one of the three lookups
+// per cell to the XU pipe relieves the shared-memory pipe, and the sum in
+// bits leaves one multiplication by ln 2 per combination.  With u = 2^-24
+// (so 2^-22 = 4u) and in bits, a cell errs by at most n 4u (log2 M + 1) from
+// the n log2 n term, u (a + b) log2 M from the table entries, u n log2 M from
+// the fused multiply-subtract and u n from the last subtraction (t <= n);
+// over the 27 cells (sum n = N), the 27 accumulations (partial sums <= N),
+// the product with ln 2 and the final scaling this gives, in nats,
+// |MI32 - MI| <= u (6 ln M + 37 ln 2) <= u (7 ln M + 37 ln 2), which the FP64
 // rescoring window of the library covers (twice the larger of this and the
 // sweep's bound).
 //
@@ -660,10 +662,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                             // Masked so that no index can leave the table
                             // (exact class counts are below its size).
                             const uint32_t ca = T[x] & tmask, cb = (T[x] >> 16) & tmask;
-                            const float nf = fmaxf(u2f_small(ca + cb), 1.0f);   // n ln n = 0 at n = 0, 1
-                            hs[x % 3] += fmaf(nf, LN2F * lg2_approx(nf), -xltab[ca]) - xltab[cb];
+                            const float nf = fmaxf(u2f_small(ca + cb), 1.0f);   // n log2 n = 0 at n = 0, 1
+                            hs[x % 3] += fmaf(nf, lg2_approx(nf), -xltab[ca]) - xltab[cb];
                         }
-                        hsum = (hs[0] + hs[1]) + hs[2];
+                        hsum = LN2F * ((hs[0] + hs[1]) + hs[2]);
                     }
                     const float score = fmaf(-hsum, invN, hy);
                     const uint64_t rank = valid ? rank0 : NO_RANK;

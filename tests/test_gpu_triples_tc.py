@@ -16,12 +16,12 @@ pytestmark = pytest.mark.gpu
 
 def fp32_bound(k, M):
     """The library's window: twice the larger of the sweep's bound and the
-    order-3 tensor-core epilogue's u (7 ln M + 35 ln 2), whose n ln n terms
+    order-3 tensor-core epilogue's u (7 ln M + 37 ln 2), whose n log2 n terms
     come from the hardware logarithm."""
     u = 2.0 ** -24
     lm = math.log(max(M, 2))
     sweep = u * (2.0 * lm + (2.0 * 3 ** k + 6.0) * math.log(2.0))
-    return 2.0 * max(sweep, u * (7.0 * lm + 35.0 * math.log(2.0)))
+    return 2.0 * max(sweep, u * (7.0 * lm + 37.0 * math.log(2.0)))
 
 
 @pytest.fixture(scope="module")

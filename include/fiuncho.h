@@ -113,6 +113,10 @@ int fc_set_stream(fc_handle *h, void *cuda_stream);
  * Results are ordered by (score descending, index tuple ascending).  The
  * tables are exact; scores are computed in FP32 during the sweep and the
  * candidates within the FP32 error bound of the cut are rescored in FP64.
+ * Operands derived for the tensor-core paths are built by the first search
+ * of an order and kept in the handle (orders 4-6: when the right tuple rows
+ * do not fit beside the left ones in 60 % of the free device memory, every
+ * search rebuilds them chunk by chunk into one kept buffer).
  */
 int fc_search(fc_handle *h, int k, int64_t top_n, uint32_t *out_idx, double *out_score,
               int64_t *out_count);

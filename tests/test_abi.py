@@ -112,6 +112,20 @@ def test_load_without_gpu_fails_cleanly(lib):
     assert ei.value.status == fc.FC_ENODEV
 
 
+def test_log2_probe_without_gpu_or_buffers_fails_cleanly(lib):
+    import ctypes
+    import torch
+    import paper_2201_03331_gb300 as fc
+    assert lib.fc_log2_approx(None, 4, None) == fc.FC_EINVAL
+    assert lib.fc_log2_approx(None, -1, None) == fc.FC_EINVAL
+    assert lib.fc_log2_approx(None, 0, None) == fc.FC_OK
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    n = (ctypes.c_uint32 * 4)(1, 2, 3, 4)
+    out = (ctypes.c_float * 4)()
+    assert lib.fc_log2_approx(n, 4, out) in (fc.FC_ENODEV, fc.FC_ECUDA)
+
+
 def test_null_arguments_are_rejected(lib):
     import ctypes
     assert lib.fc_load(None, 1, 1, None, None) == -1
